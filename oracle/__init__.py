@@ -1,0 +1,192 @@
+"""Python face of the CPU oracle (plain C, FP64, unfused loop nests).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+benchmark's CPU-baseline leg may import this package; the library's product
+path never does.
+
+Matrices are numpy arrays of shape (ld, n) in Fortran (column-major) order;
+the leading dimension is taken from the array (ld >= m, rows m..ld-1 are
+never read or written).  Vectors are contiguous float64 arrays.  Every
+function allocates and returns its outputs.
+"""
+import ctypes
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.c_int64
+
+
+def lib(path=None):
+    """Load (building first if needed) the oracle library; `path` loads another build."""
+    global _lib
+    if path is not None:
+        return _bind(ctypes.CDLL(path))
+    if _lib is None:
+        _lib = _bind(ctypes.CDLL(_build.build()))
+    return _lib
+
+
+def _bind(L):
+    d, i = ctypes.c_double, _I
+    sig = {
+        "oracle_bicgk": [i, i, _D, i, _D, _D, _D, _D],
+        "oracle_atax": [i, i, d, _D, i, _D, _D],
+        "oracle_gemver": [i, i, d, d, _D, i, _D, _D, _D, _D, _D, _D, _D, i, _D, _D],
+        "oracle_gesummv": [i, i, d, _D, i, d, _D, i, _D, _D],
+        "oracle_dgemv": [i, i, d, _D, i, _D, d, _D, _D],
+        "oracle_dgemvt": [i, i, d, d, _D, i, _D, _D, _D, _D],
+        "oracle_axpydot": [i, d, _D, _D, _D, _D, _D],
+        "oracle_axpydot_dot2": [i, d, _D, _D, _D, _D, _D],
+        "oracle_waxpby": [i, d, _D, d, _D, _D],
+        "oracle_vadd": [i, _D, _D, _D, _D],
+        "oracle_dot2": [i, _D, _D],
+        "oracle_bicgk_mrhs": [i, i, i, _D, i, _D, i, _D, i, _D, i, _D, i],
+        "oracle_row_dot": [i, _D, _D],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int if name in (
+            "oracle_atax", "oracle_gemver", "oracle_gesummv", "oracle_dgemv",
+            "oracle_dgemvt") else (ctypes.c_double if name in ("oracle_dot2", "oracle_row_dot") else None)
+    return L
+
+
+def _p(a):
+    if a.size == 0:
+        # A valid pointer for zero-length arrays (never dereferenced).
+        a = np.zeros(1, dtype=np.float64)
+        _p._keep.append(a)
+    return a.ctypes.data_as(_D)
+
+
+_p._keep = []
+
+
+def _vec(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    assert x.ndim == 1
+    return x
+
+
+def _mat(A, m):
+    A = np.asfortranarray(A, dtype=np.float64)
+    assert A.ndim == 2
+    ld = max(1, A.shape[0])
+    assert A.shape[0] >= m or A.size == 0
+    return A, ld
+
+
+def _chk(rc):
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+
+
+def bicgk(m, n, A, p, r, L=None):
+    L = L or lib()
+    A, lda = _mat(A, m)
+    p, r = _vec(p), _vec(r)
+    q, s = np.empty(m), np.empty(n)
+    L.oracle_bicgk(m, n, _p(A), lda, _p(p), _p(r), _p(q), _p(s))
+    return q, s
+
+
+def atax(m, n, beta, A, x, L=None):
+    L = L or lib()
+    A, lda = _mat(A, m)
+    x = _vec(x)
+    y = np.empty(n)
+    _chk(L.oracle_atax(m, n, beta, _p(A), lda, _p(x), _p(y)))
+    return y
+
+
+def gemver(m, n, alpha, beta, A, u1, v1, u2, v2, y, z, L=None):
+    L = L or lib()
+    A, lda = _mat(A, m)
+    u1, v1, u2, v2, y, z = map(_vec, (u1, v1, u2, v2, y, z))
+    B = np.zeros((max(1, m), n), order="F")
+    x, w = np.empty(n), np.empty(m)
+    _chk(L.oracle_gemver(m, n, alpha, beta, _p(A), lda, _p(u1), _p(v1), _p(u2), _p(v2),
+                         _p(y), _p(z), _p(B), max(1, m), _p(x), _p(w)))
+    return B[:m], x, w
+
+
+def gesummv(m, n, alpha, A, beta, B, x, L=None):
+    L = L or lib()
+    A, lda = _mat(A, m)
+    B, ldb = _mat(B, m)
+    x = _vec(x)
+    y = np.empty(m)
+    _chk(L.oracle_gesummv(m, n, alpha, _p(A), lda, beta, _p(B), ldb, _p(x), _p(y)))
+    return y
+
+
+def dgemv(m, n, alpha, A, x, beta, y, L=None):
+    L = L or lib()
+    A, lda = _mat(A, m)
+    x, y = _vec(x), _vec(y)
+    z = np.empty(m)
+    _chk(L.oracle_dgemv(m, n, alpha, _p(A), lda, _p(x), beta, _p(y), _p(z)))
+    return z
+
+
+def dgemvt(m, n, alpha, beta, A, y, z, L=None):
+    L = L or lib()
+    A, lda = _mat(A, m)
+    y, z = _vec(y), _vec(z)
+    x, w = np.empty(n), np.empty(m)
+    _chk(L.oracle_dgemvt(m, n, alpha, beta, _p(A), lda, _p(y), _p(z), _p(x), _p(w)))
+    return x, w
+
+
+def axpydot(n, alpha, w, v, u, compensated=False, L=None):
+    L = L or lib()
+    w, v, u = map(_vec, (w, v, u))
+    z = np.empty(n)
+    r = ctypes.c_double(0.0)
+    f = L.oracle_axpydot_dot2 if compensated else L.oracle_axpydot
+    f(n, alpha, _p(w), _p(v), _p(u), _p(z), ctypes.byref(r))
+    return z, r.value
+
+
+def waxpby(n, alpha, x, beta, y, L=None):
+    L = L or lib()
+    x, y = _vec(x), _vec(y)
+    w = np.empty(n)
+    L.oracle_waxpby(n, alpha, _p(x), beta, _p(y), _p(w))
+    return w
+
+
+def vadd(n, w, y, z, L=None):
+    L = L or lib()
+    w, y, z = map(_vec, (w, y, z))
+    x = np.empty(n)
+    L.oracle_vadd(n, _p(w), _p(y), _p(z), _p(x))
+    return x
+
+
+def dot2(x, y, L=None):
+    L = L or lib()
+    x, y = _vec(x), _vec(y)
+    return L.oracle_dot2(len(x), _p(x), _p(y))
+
+
+def row_dot(row, p, L=None):
+    L = L or lib()
+    row, p = _vec(row), _vec(p)
+    return L.oracle_row_dot(len(row), _p(row), _p(p))
+
+
+def bicgk_mrhs(m, n, k, A, P, R, L=None):
+    L = L or lib()
+    A, lda = _mat(A, m)
+    P = np.asfortranarray(P, dtype=np.float64)
+    R = np.asfortranarray(R, dtype=np.float64)
+    Q = np.zeros((max(1, m), k), order="F")
+    S = np.zeros((max(1, n), k), order="F")
+    L.oracle_bicgk_mrhs(m, n, k, _p(A), lda, _p(P), max(1, P.shape[0]), _p(R),
+                        max(1, R.shape[0]), _p(Q), max(1, m), _p(S), max(1, n))
+    return Q[:m], S[:n]

@@ -1,0 +1,487 @@
+"""Benchmark: the FP64 kernel suite at n = 16384 (fused), beside its unfused
+form, the end-to-end path from pinned host memory, and the oracle on the
+host's cores.
+
+One step runs every fused Table I kernel once on resident synthetic inputs:
+BICGK, ATAX, GESUMMV, GEMVER, DGEMV and DGEMVT on 16384 x 16384 FP64
+column-major matrices (2 GiB each), and AXPYDOT, WAXPBY and VADD on 2^26
+element vectors.  `value` is the suite's effective bandwidth: the sum of
+each kernel's compulsory bytes (every input read once, every output written
+once, GEMVER's B written once and read back once) divided by the step time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own replica of the workload (the kernels
+do not shard); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_MAT = 16384
+N_VEC = 1 << 26
+SEED = 1
+ALPHA, BETA = 1.5, 1.2
+FP64_FLOP_PER_CLK_PER_SM = 4.0   # 2 FP64 FMA per clock per SM (measured: 2.05)
+
+KERNELS = ["bicgk", "atax", "gesummv", "gemver", "dgemv", "dgemvt", "axpydot", "waxpby", "vadd"]
+# Launches of our kernels per call (panel pass(es) + combine(s); ATAX is one cooperative kernel).
+LAUNCHES = {"bicgk": 2, "atax": 1, "gesummv": 2, "gemver": 4, "dgemv": 2, "dgemvt": 4,
+            "axpydot": 2, "waxpby": 1, "vadd": 1}
+UNFUSED_LAUNCHES = {"bicgk": 4, "atax": 5, "gesummv": 4, "gemver": 8, "dgemv": 3, "dgemvt": 5,
+                    "axpydot": 4, "waxpby": 3, "vadd": 3}
+
+
+def compulsory_bytes(k, m, n, N):
+    e = 8
+    return {
+        "bicgk": e * m * n + e * (2 * m + 2 * n),
+        "atax": e * m * n + e * 2 * n,
+        "gesummv": 2 * e * m * n + e * (n + m),
+        "gemver": 3 * e * m * n + e * (4 * m + 4 * n),
+        "dgemv": e * m * n + e * (n + 2 * m),
+        "dgemvt": 2 * e * m * n + e * (2 * m + 2 * n),
+        "axpydot": 4 * e * N + e,
+        "waxpby": 3 * e * N,
+        "vadd": 4 * e * N,
+    }[k]
+
+
+def unfused_bytes(k, m, n, N):
+    # Bytes the one-kernel-per-BLAS-call form moves (its own traffic).
+    e = 8
+    return {
+        "bicgk": 2 * e * m * n + e * (2 * m + 2 * n),
+        "atax": 2 * e * m * n + e * (2 * m + 4 * n),
+        "gesummv": 2 * e * m * n + e * (3 * m + 2 * n),
+        "gemver": 8 * e * m * n + e * (6 * m + 6 * n),
+        "dgemv": e * m * n + e * (n + 4 * m),
+        "dgemvt": 2 * e * m * n + e * (4 * n + 3 * m),
+        "axpydot": 7 * e * N + e,
+        "waxpby": 7 * e * N,
+        "vadd": 8 * e * N,
+    }[k]
+
+
+def flops(k, m, n, N):
+    return {"bicgk": 4 * m * n, "atax": 4 * m * n, "gesummv": 4 * m * n, "gemver": 8 * m * n,
+            "dgemv": 2 * m * n, "dgemvt": 4 * m * n, "axpydot": 4 * N, "waxpby": 3 * N,
+            "vadd": 2 * N}[k]
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+class Suite:
+    """Device buffers and one call per fused (or unfused) kernel."""
+
+    def __init__(self, torch, bto, m=N_MAT, n=N_MAT, N=N_VEC):
+        import synth
+        self.torch, self.bto = torch, bto
+        self.m, self.n, self.N = m, n, N
+        f64 = dict(dtype=torch.float64, device="cuda")
+        self.A = torch.empty(m * n, **f64)
+        self.B2 = torch.empty(m * n, **f64)       # GESUMMV's second matrix
+        self.Bout = torch.empty(m * n, **f64)     # GEMVER's B
+        bto.bto_fill_f64(SEED, 0, 0, m, n, 0, self.A, m, None)
+        bto.bto_fill_f64(SEED, 1, 0, m, n, 0, self.B2, m, None)
+        self.vec = {}
+        for k, ln, aid in [("p", n, 1), ("r", m, 2), ("x", n, 3), ("ym", m, 4), ("zn", n, 5),
+                           ("u1", m, 11), ("v1", n, 12), ("u2", m, 13), ("v2", n, 14),
+                           ("gy", m, 15), ("gz", n, 16)]:
+            self.vec[k] = torch.empty(ln, **f64)
+            bto.bto_fill_f64(SEED, aid, 0, ln, 1, 0, self.vec[k], ln, None)
+        for k, ln in [("q", m), ("s", n), ("y_atax", n), ("y_ges", m), ("gx", n), ("gw", m),
+                      ("z_dgemv", m), ("tx", n), ("tw", m)]:
+            self.vec[k] = torch.empty(ln, **f64)
+        self.big = {}
+        for k, aid in [("w", 20), ("v", 21), ("u", 22), ("xx", 23), ("yy", 24), ("zz", 25)]:
+            self.big[k] = torch.empty(N, **f64)
+            bto.bto_fill_f64(SEED, aid, 0, N, 1, 0, self.big[k], N, None)
+        for k in ("z_ax", "w_wx", "x_va"):
+            self.big[k] = torch.empty(N, **f64)
+        self.r = torch.empty(1, **f64)
+        self.ws = {}
+        for form in (0, 1):
+            size = max(bto.bto_workspace_bytes(k, form, m if k in KERNELS[:6] else 0,
+                                               n if k in KERNELS[:6] else N) for k in KERNELS)
+            self.ws[form] = (torch.empty(size, dtype=torch.uint8, device="cuda"), size)
+        torch.cuda.synchronize()
+
+    def call(self, k, form=0):
+        b, v, g, m, n, N = self.bto, self.vec, self.big, self.m, self.n, self.N
+        ws, wb = self.ws[form]
+        u = form == 1
+        if k == "bicgk":
+            (b.bto_unfused_bicgk if u else b.bto_bicgk)(m, n, self.A, m, v["p"], v["r"], v["q"], v["s"], ws, wb, None)
+        elif k == "atax":
+            (b.bto_unfused_atax if u else b.bto_atax)(m, n, BETA, self.A, m, v["x"], v["y_atax"], ws, wb, None)
+        elif k == "gesummv":
+            (b.bto_unfused_gesummv if u else b.bto_gesummv)(m, n, ALPHA, self.A, m, -0.75, self.B2, m, v["x"],
+                                                            v["y_ges"], ws, wb, None)
+        elif k == "gemver":
+            (b.bto_unfused_gemver if u else b.bto_gemver)(m, n, ALPHA, BETA, self.A, m, v["u1"], v["v1"], v["u2"],
+                                                          v["v2"], v["gy"], v["gz"], self.Bout, m, v["gx"],
+                                                          v["gw"], ws, wb, None)
+        elif k == "dgemv":
+            (b.bto_unfused_dgemv if u else b.bto_dgemv)(m, n, ALPHA, self.A, m, v["x"], -0.5, v["ym"],
+                                                        v["z_dgemv"], ws, wb, None)
+        elif k == "dgemvt":
+            (b.bto_unfused_dgemvt if u else b.bto_dgemvt)(m, n, ALPHA, BETA, self.A, m, v["ym"], v["zn"],
+                                                          v["tx"], v["tw"], ws, wb, None)
+        elif k == "axpydot":
+            (b.bto_unfused_axpydot if u else b.bto_axpydot)(N, 0.75, g["w"], g["v"], g["u"], g["z_ax"], self.r,
+                                                            ws, wb, None)
+        elif k == "waxpby":
+            (b.bto_unfused_waxpby if u else b.bto_waxpby)(N, ALPHA, g["xx"], -0.25, g["yy"], g["w_wx"], None)
+        elif k == "vadd":
+            (b.bto_unfused_vadd if u else b.bto_vadd)(N, g["w"], g["yy"], g["zz"], g["x_va"], None)
+
+
+def timed_steps(torch, suite, steps, warmup, form, dist, per_kernel=True):
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        for k in KERNELS:
+            suite.call(k, form)
+    ev = {k: [] for k in KERNELS}
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    for _ in range(steps):
+        for k in KERNELS:
+            if per_kernel:
+                a = torch.cuda.Event(enable_timing=True)
+                a.record(st)
+            suite.call(k, form)
+            if per_kernel:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(st)
+                ev[k].append((a, e))
+    t1.record(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total = t0.elapsed_time(t1)
+    kern = {k: (sum(a.elapsed_time(e) for a, e in ev[k]) / len(ev[k]) if ev[k] else None) for k in KERNELS}
+    return total / steps, kern
+
+
+def e2e_steps(torch, bto, steps, warmup, m, n, N):
+    """Same suite through the public API from pinned host buffers: every step
+    copies its inputs host->device, runs the fused kernels and reads every
+    output back."""
+    import synth
+    pin = dict(dtype=torch.float64, pin_memory=True)
+    hA = torch.empty(m * n, **pin)
+    hB = torch.empty(m * n, **pin)
+    # host inputs (generated once on the device, then copied into pinned memory)
+    tmp = torch.empty(m * n, dtype=torch.float64, device="cuda")
+    bto.bto_fill_f64(SEED, 0, 0, m, n, 0, tmp, m, None); hA.copy_(tmp)
+    bto.bto_fill_f64(SEED, 1, 0, m, n, 0, tmp, m, None); hB.copy_(tmp)
+    del tmp
+    hv = {k: torch.from_numpy(synth.vector(SEED, 30 + i, ln)).pin_memory()
+          for i, (k, ln) in enumerate([("p", n), ("r", m), ("x", n), ("ym", m), ("zn", n), ("u1", m),
+                                       ("v1", n), ("u2", m), ("v2", n), ("gy", m), ("gz", n)])}
+    hbig = {}
+    for i, k in enumerate(("w", "v", "u", "xx", "yy", "zz")):
+        t = torch.empty(N, dtype=torch.float64, device="cuda")
+        bto.bto_fill_f64(SEED, 40 + i, 0, N, 1, 0, t, N, None)
+        hbig[k] = torch.empty(N, **pin)
+        hbig[k].copy_(t)
+        del t
+    outs_h = {k: torch.empty(ln, **pin) for k, ln in [("q", m), ("s", n), ("y_atax", n), ("y_ges", m),
+                                                       ("gx", n), ("gw", m), ("z_dgemv", m), ("tx", n),
+                                                       ("tw", m), ("r", 1)]}
+    outs_big_h = {k: torch.empty(N, **pin) for k in ("z_ax", "w_wx", "x_va")}
+    hBout = torch.empty(m * n, **pin)
+    suite = Suite.__new__(Suite)
+    suite.torch, suite.bto, suite.m, suite.n, suite.N = torch, bto, m, n, N
+    f64 = dict(dtype=torch.float64, device="cuda")
+    suite.A, suite.B2, suite.Bout = (torch.empty(m * n, **f64) for _ in range(3))
+    suite.vec = {k: torch.empty(t.numel(), **f64) for k, t in hv.items()}
+    suite.vec.update({k: torch.empty(t.numel(), **f64) for k, t in outs_h.items() if k != "r"})
+    suite.big = {k: torch.empty(N, **f64) for k in list(hbig) + list(outs_big_h)}
+    suite.r = torch.empty(1, **f64)
+    suite.ws = {}
+    size = max(bto.bto_workspace_bytes(k, 0, m if k in KERNELS[:6] else 0, n if k in KERNELS[:6] else N)
+               for k in KERNELS)
+    suite.ws[0] = (torch.empty(size, dtype=torch.uint8, device="cuda"), size)
+    h2d = hA.numel() * 8 + hB.numel() * 8 + sum(t.numel() * 8 for t in hv.values()) + \
+        sum(t.numel() * 8 for t in hbig.values())
+    d2h = sum(t.numel() * 8 for t in outs_h.values()) + sum(t.numel() * 8 for t in outs_big_h.values()) + \
+        hBout.numel() * 8
+
+    def step():
+        suite.A.copy_(hA, non_blocking=True)
+        suite.B2.copy_(hB, non_blocking=True)
+        for k, t in hv.items():
+            suite.vec[k].copy_(t, non_blocking=True)
+        for k, t in hbig.items():
+            suite.big[k].copy_(t, non_blocking=True)
+        for k in KERNELS:
+            suite.call(k, 0)
+        for k, t in outs_h.items():
+            t.copy_(suite.r if k == "r" else suite.vec[k], non_blocking=True)
+        for k, t in outs_big_h.items():
+            t.copy_(suite.big[k], non_blocking=True)
+        hBout.copy_(suite.Bout, non_blocking=True)
+
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(st)
+    for _ in range(steps):
+        step()
+    t1.record(st)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / steps, h2d, d2h
+
+
+def suite_bytes(m, n, N, fn=compulsory_bytes):
+    return sum(fn(k, m, n, N) for k in KERNELS)
+
+
+def oracle_sample(n_mat, n_vec, reps=1):
+    """The oracle suite on the host: returns (seconds, compulsory bytes)."""
+    import oracle as O
+    import synth
+    m = n = n_mat
+    A = synth.matrix(SEED, 0, m, n)
+    B = synth.matrix(SEED, 1, m, n)
+    v = {k: synth.vector(SEED, i, n) for i, k in enumerate(["p", "r", "x", "y", "z", "u1", "v1", "u2", "v2"])}
+    big = {k: synth.vector(SEED, 20 + i, n_vec) for i, k in enumerate(["w", "v", "u"])}
+    L = O.lib()
+    t = time.perf_counter()
+    for _ in range(reps):
+        O.bicgk(m, n, A, v["p"], v["r"], L=L)
+        O.atax(m, n, BETA, A, v["x"], L=L)
+        O.gesummv(m, n, ALPHA, A, -0.75, B, v["x"], L=L)
+        O.gemver(m, n, ALPHA, BETA, A, v["u1"], v["v1"], v["u2"], v["v2"], v["y"], v["z"], L=L)
+        O.dgemv(m, n, ALPHA, A, v["x"], -0.5, v["y"], L=L)
+        O.dgemvt(m, n, ALPHA, BETA, A, v["y"], v["z"], L=L)
+        O.axpydot(n_vec, 0.75, big["w"], big["v"], big["u"], L=L)
+        O.waxpby(n_vec, ALPHA, big["w"], -0.25, big["v"], L=L)
+        O.vadd(n_vec, big["w"], big["v"], big["u"], L=L)
+    return time.perf_counter() - t, reps * suite_bytes(m, n, n_vec)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ns, nv = 2048, 1 << 22
+    for _ in range(args.warmup):
+        oracle_sample(ns, nv)
+    secs, nbytes = 0.0, 0
+    for _ in range(args.steps):
+        s, b = oracle_sample(ns, nv)
+        secs += s
+        nbytes += b
+    value = nbytes / secs / 1e9
+    sample = ("per step: the oracle (plain C, FP64, 1 thread) on the suite at n=%d matrices and "
+              "%d-element vectors, a bounded sample of the n=16384 / 2^26 workload" % (ns, nv))
+    print(json.dumps({
+        "impl": "reference", "metric": "fused FP64 kernel-suite effective HBM bandwidth",
+        "value": round(value, 4), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * secs / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (SplitMix64 uniform[-1,1), seed 1)",
+        "config": {"workload": "FP64 suite n=16384, vectors 2^26 (bounded host sample)"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-unfused", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+    from paper_1205_1098_gb300 import build
+    build.build()
+    import paper_1205_1098_gb300 as bto
+
+    m = n = N_MAT
+    N = N_VEC
+    hbm, sm_max, peak_src = load_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp64_peak = FP64_FLOP_PER_CLK_PER_SM * sms * sm_max * 1e6 / 1e12   # TFLOP/s
+
+    suite = Suite(torch, bto, m, n, N)
+    with Clocks(local) as clk:
+        ms, kern = timed_steps(torch, suite, args.steps, args.warmup, 0, dist)
+    clocks = clk.summary()
+    # max over ranks
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    step_bytes = suite_bytes(m, n, N)
+    value = world * step_bytes / (ms * 1e-3) / 1e9
+
+    per = {}
+    for k in KERNELS:
+        t = kern[k] * 1e-3
+        gbs = compulsory_bytes(k, m, n, N) / t / 1e9
+        tf = flops(k, m, n, N) / t / 1e12
+        per[k] = {"ms": round(kern[k], 4), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3),
+                  "fp64_tflops": round(tf, 4), "fp64_frac": round(tf / fp64_peak, 3),
+                  "bound": "alu" if tf / fp64_peak > gbs / hbm else "hbm"}
+
+    unfused = None
+    if not args.no_unfused:
+        ums, ukern = timed_steps(torch, suite, args.steps, max(3, args.warmup // 2), 1, dist)
+        unfused = {"ms_per_step": round(ums, 3), "value": round(step_bytes / (ums * 1e-3) / 1e9, 1),
+                   "unit": "GB/s of fused compulsory bytes", "speedup_fused": round(ums / ms, 3)}
+        for k in KERNELS:
+            per[k]["unfused_ms"] = round(ukern[k], 4)
+            per[k]["unfused_own_gbs"] = round(unfused_bytes(k, m, n, N) / (ukern[k] * 1e-3) / 1e9, 1)
+            per[k]["fused_speedup"] = round(ukern[k] / kern[k], 3)
+            per[k]["byte_ratio"] = round(unfused_bytes(k, m, n, N) / compulsory_bytes(k, m, n, N), 3)
+
+    # Roofline of the dominant kernel (largest share of the step).
+    dom = max(KERNELS, key=lambda k: kern[k])
+    d = per[dom]
+    if d["bound"] == "alu":
+        roof = {"kernel": "bto_%s (all launches of one call)" % dom, "bound": "alu",
+                "achieved": d["fp64_tflops"], "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                "frac": d["fp64_frac"], "traffic": None,
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x %d SMs x %.0f MHz" % (sms, sm_max),
+                "hbm_frac_of_%s" % peak_src: d["hbm_frac"]}
+    else:
+        roof = {"kernel": "bto_%s (all launches of one call)" % dom, "bound": "hbm",
+                "achieved": d["gbs"], "peak": hbm, "unit": "GB/s", "frac": d["hbm_frac"],
+                "traffic": None, "peak_source": peak_src}
+
+    e2e = None
+    if not args.no_e2e:
+        del suite
+        torch.cuda.empty_cache()
+        ems, h2d, d2h = e2e_steps(torch, bto, max(2, args.steps // 3), 1, m, n, N)
+        if dist:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": round(world * step_bytes / (ems * 1e-3) / 1e9, 2), "unit": "GB/s",
+               "ms_per_step": round(ems, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        ns, nv = 8192, 1 << 25
+        secs, nbytes = oracle_sample(ns, nv)
+        cpu = {"value": round(nbytes / secs / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "the oracle (plain C, FP64, 1 thread) on the same suite at n=%d matrices and "
+                         "%d-element vectors (%.1f s), bytes scaled the same way" % (ns, nv, secs)}
+
+    launches = args.steps * sum(LAUNCHES.values())
+    if rank == 0:
+        print(json.dumps({
+            "metric": "fused FP64 kernel-suite effective HBM bandwidth (GEMVER/BiCGK/ATAX/GESUMMV/"
+                      "DGEMV/DGEMVT at n=16384, AXPYDOT/WAXPBY/VADD at 2^26) vs unfused",
+            "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (SplitMix64 uniform[-1,1), seed 1), generated on the device",
+            "config": {"workload": "FP64 kernel suite: 16384x16384 column-major matrices, 2^26-element "
+                                   "vectors (configs[1])", "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "every input is larger than L2 (2 GiB matrices, 512 MiB vectors); no flush"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches, "kernels": per, "unfused": unfused,
+            "peaks": {"hbm_gbs": hbm, "hbm_source": peak_src, "fp64_tflops": round(fp64_peak, 4)},
+        }))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,257 @@
+/*
+ * bto.h -- C ABI of the fused BLAS-1/2 sequence library for GB300 (sm_103a).
+ *
+ * The operations are the kernels of Table I (Section V-A, "Test Environment
+ * and Kernels") of "Reliable Generation of High-Performance Matrix Algebra"
+ * (Belter, Jessup, Nelson, Norris, Siek; the Build to Order BLAS).  Each
+ * sequence runs with loop fusion and array contraction (Sections I and III):
+ * a matrix is streamed from device memory the fewest times the data
+ * dependences allow, and temporary vectors stay on chip.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers are DEVICE pointers unless a comment says otherwise.  The
+ *    caller owns all memory; the library never allocates, frees or
+ *    synchronizes (bto_device_status is the one call that waits, on request).
+ *  - Matrices are column-major: element (i, j) of A is A[i + j*lda], with
+ *    lda >= max(1, m).  Rows m..lda-1 are never read or written.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream) and returns before it finishes.  The returned status covers
+ *    argument validation and launch errors; faults inside a kernel surface at
+ *    the caller's next synchronization, as for any CUDA launch.
+ *  - m = 0 or n = 0 is valid; an empty sum is 0 (so GEMVER with m = 0 gives
+ *    x = beta*0 + z).
+ *  - Arithmetic is IEEE with no BLAS-style shortcut for zero scalars: alpha*s
+ *    is always evaluated, so a NaN or Inf in an operand propagates even when
+ *    its scalar is 0.  Kernels may contract a*b + c into one fused
+ *    multiply-add and sum in any fixed order; the order depends only on the
+ *    sizes and the device's SM count, so repeated calls are bitwise equal.
+ *  - Outputs may not overlap inputs, except where an entry point documents an
+ *    in-place form.  Violations are rejected with BTO_ERR_INVALID_VALUE.
+ *  - Workspace `ws` (device memory, at least bto_workspace_bytes() bytes,
+ *    256-byte aligned) holds split partial sums; its contents on entry are
+ *    ignored and on exit unspecified.  Calls that share a workspace must be
+ *    ordered (same stream or events).
+ *  - On an invalid argument nothing is launched, the call returns
+ *    BTO_ERR_INVALID_VALUE (or BTO_ERR_WORKSPACE for a short workspace) and
+ *    bto_last_invalid_arg() gives the 1-based position of the argument.
+ */
+#ifndef BTO_H
+#define BTO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t (struct CUstream_st *); no CUDA header needed. */
+typedef struct CUstream_st *bto_stream_t;
+
+typedef enum {
+    BTO_OK = 0,
+    BTO_ERR_INVALID_VALUE = 1, /* bad size, pointer, alignment or aliasing      */
+    BTO_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement   */
+    BTO_ERR_WORKSPACE = 3,     /* ws NULL or smaller than bto_workspace_bytes() */
+    BTO_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed          */
+    BTO_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired            */
+    BTO_ERR_BUDGET = 6         /* a request exceeds a configured memory budget  */
+} bto_status;
+
+typedef enum { BTO_F64 = 0, BTO_F32 = 1, BTO_BF16 = 2 } bto_dtype;
+
+typedef enum {
+    BTO_OP_BICGK = 0,
+    BTO_OP_ATAX = 1,
+    BTO_OP_GEMVER = 2,
+    BTO_OP_GESUMMV = 3,
+    BTO_OP_DGEMV = 4,
+    BTO_OP_DGEMVT = 5,
+    BTO_OP_AXPYDOT = 6,
+    BTO_OP_WAXPBY = 7,
+    BTO_OP_VADD = 8
+} bto_op;
+
+/* Form selector for bto_workspace_bytes: the fused kernels or the unfused
+ * one-kernel-per-BLAS-call sequences (bto_unfused_*). */
+#define BTO_FORM_FUSED 0
+#define BTO_FORM_UNFUSED 1
+
+/* ---------------------------------------------------------------- utilities */
+
+/* Library version, major*10000 + minor*100 + patch. */
+int bto_version(void);
+
+/* Static, NUL-terminated description of a status code (never NULL). */
+const char *bto_status_string(int status);
+
+/* 1-based position of the argument rejected by the calling thread's most
+ * recent failing call (0 if none). Thread-local. */
+int bto_last_invalid_arg(void);
+
+/* Bytes of workspace that `op` in `form` needs for an m x n problem (vector
+ * kernels: n elements, m ignored) with matrix storage type `a_type`, on the
+ * CURRENT device (the split of the matrix follows its SM count).  Writes the
+ * size to *bytes.  Returns BTO_ERR_INVALID_VALUE for a negative size or an
+ * unknown op/form/type, BTO_ERR_CUDA if the device cannot be queried. */
+bto_status bto_workspace_bytes(int op, int form, int64_t m, int64_t n, int a_type,
+                               size_t *bytes);
+
+/* Waits for `stream`, then reads the device status word that the kernels
+ * with bounded inter-block waits (bto_atax) leave at the start of `ws`:
+ * BTO_OK, or BTO_ERR_TIMEOUT if a wait expired (the outputs are then
+ * unspecified).  *status receives the value. */
+bto_status bto_device_status(const void *ws, bto_stream_t stream, int *status);
+
+/* --------------------------------------------------- fused FP64 sequences */
+
+/* BICGK (Table I): q <- A p ; s <- A^T r.
+ * A: m x n (lda); p: n; r: m; q: m (output); s: n (output).
+ * One pass over A produces both products (the two dgemv calls of the BICGK
+ * BLAS listing in Section V-A, fused). */
+bto_status bto_bicgk(int64_t m, int64_t n, const double *A, int64_t lda,
+                     const double *p, const double *r, double *q, double *s,
+                     void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* ATAX (Table I, y <- A^T A x) generalised to BATAX (Section II, Fig. 1:
+ * y <- beta A^T (A x)); beta = 1 is ATAX.  A: m x n (lda); x: n; y: n (output).
+ * The temporary t = A x (length m) is contracted: it never reaches device
+ * memory as a vector; A is read from device memory once.  Uses bounded waits
+ * between blocks; a timeout is reported through bto_device_status. */
+bto_status bto_atax(int64_t m, int64_t n, double beta, const double *A, int64_t lda,
+                    const double *x, double *y, void *ws, size_t ws_bytes,
+                    bto_stream_t stream);
+
+/* GEMVER (Table I): B <- A + u1 v1^T + u2 v2^T ; x <- beta B^T y + z ;
+ * w <- alpha B x  (x uses the new B, w the new x).
+ * A: m x n (lda); u1, u2, y: m; v1, v2, z: n; B: m x n (ldb, output);
+ * x: n (output); w: m (output).  In place: B == A with ldb == lda, and
+ * x == z, are allowed.  B is written once and read back once (w needs the
+ * complete x, so a second pass over B is unavoidable). */
+bto_status bto_gemver(int64_t m, int64_t n, double alpha, double beta,
+                      const double *A, int64_t lda, const double *u1, const double *v1,
+                      const double *u2, const double *v2, const double *y, const double *z,
+                      double *B, int64_t ldb, double *x, double *w,
+                      void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* GESUMMV (Table I): y <- alpha A x + beta B x.
+ * A: m x n (lda); B: m x n (ldb); x: n; y: m (output). */
+bto_status bto_gesummv(int64_t m, int64_t n, double alpha, const double *A, int64_t lda,
+                       double beta, const double *B, int64_t ldb, const double *x,
+                       double *y, void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* DGEMV (Table I): z <- alpha A x + beta y.
+ * A: m x n (lda); x: n; y: m; z: m (output; z == y allowed). */
+bto_status bto_dgemv(int64_t m, int64_t n, double alpha, const double *A, int64_t lda,
+                     const double *x, double beta, const double *y, double *z,
+                     void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* DGEMVT (Table I): x <- beta A^T y + z ; w <- alpha A x (with the new x).
+ * A: m x n (lda); y: m; z: n; x: n (output; x == z allowed); w: m (output). */
+bto_status bto_dgemvt(int64_t m, int64_t n, double alpha, double beta,
+                      const double *A, int64_t lda, const double *y, const double *z,
+                      double *x, double *w, void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* AXPYDOT (Table I): z <- w - alpha v ; r <- z^T u.  (Table I names the
+ * output scalar beta.)  w, v, u: n; z: n (output; z == w allowed);
+ * r: one double in device memory (output). */
+bto_status bto_axpydot(int64_t n, double alpha, const double *w, const double *v,
+                       const double *u, double *z, double *r,
+                       void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* WAXPBY (Table I): w <- alpha x + beta y.  x, y: n; w: n (output). */
+bto_status bto_waxpby(int64_t n, double alpha, const double *x, double beta,
+                      const double *y, double *w, bto_stream_t stream);
+
+/* VADD (Table I): x <- w + y + z, evaluated as (w + y) + z.
+ * w, y, z: n; x: n (output). */
+bto_status bto_vadd(int64_t n, const double *w, const double *y, const double *z,
+                    double *x, bto_stream_t stream);
+
+/* ------------------------------------------- unfused comparison sequences
+ * Same operations, arguments and results as the fused entry points above,
+ * computed as one GPU kernel per BLAS call, the way a program built from
+ * separately tuned BLAS routines would (the BICGK listing of Section V-A;
+ * the other kernels by the same translation): temporaries and intermediate
+ * results round-trip through device memory.
+ *   BICGK:   dgemv N (q = A p); dgemv T (s = A^T r)
+ *   ATAX:    dgemv N (t = A x, t in ws); dgemv T (y = A^T t); dscal (y = beta y)
+ *   GEMVER:  dcopy (B = A); dger (B += u1 v1^T); dger (B += u2 v2^T);
+ *            dcopy (x = z); dgemv T (x = beta B^T y + x); dgemv N (w = alpha B x)
+ *   GESUMMV: dgemv N (y = alpha A x); dgemv N (y = beta B x + y)
+ *   DGEMV:   dgemv N (z = alpha A x + beta y)
+ *   DGEMVT:  dcopy (x = z); dgemv T (x = beta A^T y + x); dgemv N (w = alpha A x)
+ *   AXPYDOT: dcopy (z = w); daxpy (z = -alpha v + z); ddot (r = z^T u)
+ *   WAXPBY:  dcopy (w = y); dscal (w = beta w); daxpy (w = alpha x + w)
+ *   VADD:    dcopy (x = w); daxpy (x = y + x); daxpy (x = z + x)
+ * In-place forms are not accepted here.  Results agree with the fused forms
+ * to rounding (the association of some sums differs). */
+bto_status bto_unfused_bicgk(int64_t m, int64_t n, const double *A, int64_t lda,
+                             const double *p, const double *r, double *q, double *s,
+                             void *ws, size_t ws_bytes, bto_stream_t stream);
+bto_status bto_unfused_atax(int64_t m, int64_t n, double beta, const double *A, int64_t lda,
+                            const double *x, double *y, void *ws, size_t ws_bytes,
+                            bto_stream_t stream);
+bto_status bto_unfused_gemver(int64_t m, int64_t n, double alpha, double beta,
+                              const double *A, int64_t lda, const double *u1,
+                              const double *v1, const double *u2, const double *v2,
+                              const double *y, const double *z, double *B, int64_t ldb,
+                              double *x, double *w, void *ws, size_t ws_bytes,
+                              bto_stream_t stream);
+bto_status bto_unfused_gesummv(int64_t m, int64_t n, double alpha, const double *A,
+                               int64_t lda, double beta, const double *B, int64_t ldb,
+                               const double *x, double *y, void *ws, size_t ws_bytes,
+                               bto_stream_t stream);
+bto_status bto_unfused_dgemv(int64_t m, int64_t n, double alpha, const double *A, int64_t lda,
+                             const double *x, double beta, const double *y, double *z,
+                             void *ws, size_t ws_bytes, bto_stream_t stream);
+bto_status bto_unfused_dgemvt(int64_t m, int64_t n, double alpha, double beta,
+                              const double *A, int64_t lda, const double *y,
+                              const double *z, double *x, double *w,
+                              void *ws, size_t ws_bytes, bto_stream_t stream);
+bto_status bto_unfused_axpydot(int64_t n, double alpha, const double *w, const double *v,
+                               const double *u, double *z, double *r,
+                               void *ws, size_t ws_bytes, bto_stream_t stream);
+bto_status bto_unfused_waxpby(int64_t n, double alpha, const double *x, double beta,
+                              const double *y, double *w, bto_stream_t stream);
+bto_status bto_unfused_vadd(int64_t n, const double *w, const double *y, const double *z,
+                            double *x, bto_stream_t stream);
+
+/* ------------------------------------------------ synthetic input fills
+ * Not part of any Table I operation: device-side generation of the seeded
+ * test and benchmark inputs, so that matrices of several GiB need no host
+ * copy.  Element (i, j) of an m x n array receives value(seed, aid, i + j*m)
+ * (multiplied by colscale[j] when colscale is non-NULL), where value() is
+ * the SplitMix64 counter stream of Steele, Lea and Flood (OOPSLA 2014):
+ *   key = fmix(seed * 2^32 + aid); u = fmix(key + (k + 1) * 0x9E3779B97F4A7C15)
+ *   kind 0: 2 * ((u >> 11) * 2^-53) - 1   (uniform in [-1, 1))
+ *   kind 1: ((u >> 11) mod 17) - 8         (integers in [-8, 8])
+ * `out` is column-major with leading dimension ld >= max(1, m); padding rows
+ * are left untouched.  The f32/bf16 forms round the FP64 value to nearest
+ * even (one rounding).  colscale, when given, is a device vector of n doubles. */
+bto_status bto_fill_f64(uint64_t seed, uint64_t aid, int kind, int64_t m, int64_t n,
+                        const double *colscale, double *out, int64_t ld, bto_stream_t stream);
+bto_status bto_fill_f32(uint64_t seed, uint64_t aid, int kind, int64_t m, int64_t n,
+                        const double *colscale, float *out, int64_t ld, bto_stream_t stream);
+bto_status bto_fill_bf16(uint64_t seed, uint64_t aid, int kind, int64_t m, int64_t n,
+                         const double *colscale, uint16_t *out, int64_t ld,
+                         bto_stream_t stream);
+
+/* ------------------------------------------------------------ testing
+ * Fault injection for the bounded inter-block waits of bto_atax (no
+ * counterpart in the paper).  Runs bto_atax, except that the ready flag of
+ * row band `stall_band` (bands are the kernel's internal row groups; 0 is
+ * the first) is never published, so every wait for it expires after
+ * `timeout_ms` (1..10000) milliseconds instead of about two seconds.  The
+ * kernel then returns early, y is unspecified, and bto_device_status reads
+ * BTO_ERR_TIMEOUT.  No fault is raised on the device.  With stall_band < 0
+ * the call is bto_atax with a shorter wait limit. */
+bto_status bto_debug_atax_stall(int64_t m, int64_t n, double beta, const double *A, int64_t lda,
+                                const double *x, double *y, void *ws, size_t ws_bytes,
+                                int64_t stall_band, int timeout_ms, bto_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTO_H */

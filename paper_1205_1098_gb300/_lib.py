@@ -1,0 +1,180 @@
+"""ctypes binding of libbto.so: the C entry points under the same names.
+
+Argument marshalling only.  Pointer arguments accept a torch tensor (its
+data_ptr() is passed), an int address, or None (NULL).  Stream arguments
+accept a torch.cuda.Stream, an int handle, or None (the current torch
+stream of the current device).  A non-zero status raises BtoError.  There
+is no fallback: if the library is not built, loading it raises.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+_c_i64, _c_u64, _c_f64, _c_int = ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int
+_c_ptr, _c_size = ctypes.c_void_p, ctypes.c_size_t
+
+# Argument kinds: i = int64, u = uint64, d = double, p = pointer, z = size_t,
+# s = stream, k = int
+SIGNATURES = {
+    "bto_bicgk": "iipipppppzs",
+    "bto_atax": "iidpipppzs",
+    "bto_gemver": "iiddpipppppppipppzs",
+    "bto_gesummv": "iidpidpipppzs",
+    "bto_dgemv": "iidpipdpppzs",
+    "bto_dgemvt": "iiddpipppppzs",
+    "bto_axpydot": "idppppppzs",
+    "bto_waxpby": "idpdpps",
+    "bto_vadd": "ipppps",
+    "bto_unfused_bicgk": "iipipppppzs",
+    "bto_unfused_atax": "iidpipppzs",
+    "bto_unfused_gemver": "iiddpipppppppipppzs",
+    "bto_unfused_gesummv": "iidpidpipppzs",
+    "bto_unfused_dgemv": "iidpipdpppzs",
+    "bto_unfused_dgemvt": "iiddpipppppzs",
+    "bto_unfused_axpydot": "idppppppzs",
+    "bto_unfused_waxpby": "idpdpps",
+    "bto_unfused_vadd": "ipppps",
+    "bto_fill_f64": "uukiippis",
+    "bto_fill_f32": "uukiippis",
+    "bto_fill_bf16": "uukiippis",
+    "bto_debug_atax_stall": "iidpipppziks",
+}
+_KIND = {"i": _c_i64, "u": _c_u64, "d": _c_f64, "p": _c_ptr, "z": _c_size, "s": _c_ptr, "k": _c_int}
+
+BTO_OK, BTO_ERR_INVALID_VALUE, BTO_ERR_UNSUPPORTED, BTO_ERR_WORKSPACE = 0, 1, 2, 3
+BTO_ERR_CUDA, BTO_ERR_TIMEOUT, BTO_ERR_BUDGET = 4, 5, 6
+BTO_F64, BTO_F32, BTO_BF16 = 0, 1, 2
+BTO_FORM_FUSED, BTO_FORM_UNFUSED = 0, 1
+OPS = {"bicgk": 0, "atax": 1, "gemver": 2, "gesummv": 3, "dgemv": 4, "dgemvt": 5,
+       "axpydot": 6, "waxpby": 7, "vadd": 8}
+
+
+class BtoError(RuntimeError):
+    def __init__(self, func, status, arg):
+        self.status, self.arg = status, arg
+        msg = "%s failed: %s" % (func, _status_string(status))
+        if arg:
+            msg += " (argument %d)" % arg
+        super().__init__(msg)
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded libbto.so; raises if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libbto.so is not built (%s); run paper_1205_1098_gb300.build.build() "
+                               "or __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, sig in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = [_KIND[c] for c in sig]
+            f.restype = _c_int
+        L.bto_version.restype = _c_int
+        L.bto_status_string.argtypes = [_c_int]
+        L.bto_status_string.restype = ctypes.c_char_p
+        L.bto_last_invalid_arg.restype = _c_int
+        L.bto_workspace_bytes.argtypes = [_c_int, _c_int, _c_i64, _c_i64, _c_int, ctypes.POINTER(_c_size)]
+        L.bto_workspace_bytes.restype = _c_int
+        L.bto_device_status.argtypes = [_c_ptr, _c_ptr, ctypes.POINTER(_c_int)]
+        L.bto_device_status.restype = _c_int
+        _LIB = L
+    return _LIB
+
+
+def _status_string(s):
+    return lib().bto_status_string(int(s)).decode()
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _conv(kind, v):
+    if kind == "p":
+        return _ptr(v)
+    if kind == "s":
+        return _stream(v)
+    if kind == "d":
+        return float(v)
+    return int(v)
+
+
+def _make(name):
+    sig = SIGNATURES[name]
+
+    def call(*args):
+        if len(args) == len(sig) - 1 and sig[-1] == "s":
+            args = args + (None,)
+        if len(args) != len(sig):
+            raise TypeError("%s takes %d arguments (%d given)" % (name, len(sig), len(args)))
+        L = lib()
+        st = getattr(L, name)(*[_conv(k, a) for k, a in zip(sig, args)])
+        if st != BTO_OK:
+            raise BtoError(name, st, L.bto_last_invalid_arg())
+        return st
+
+    call.__name__ = name
+    call.__doc__ = "C entry point %s (see include/bto.h); argument kinds %s." % (name, sig)
+    return call
+
+
+for _name in SIGNATURES:
+    globals()[_name] = _make(_name)
+
+
+def bto_version():
+    return lib().bto_version()
+
+
+def bto_status_string(status):
+    return _status_string(status)
+
+
+def bto_last_invalid_arg():
+    return lib().bto_last_invalid_arg()
+
+
+def bto_workspace_bytes(op, form, m, n, a_type=BTO_F64):
+    """Workspace size in bytes; `op` may be a bto_op value or a name such as 'bicgk'."""
+    if isinstance(op, str):
+        op = OPS[op]
+    out = _c_size(0)
+    L = lib()
+    st = L.bto_workspace_bytes(int(op), int(form), int(m), int(n), int(a_type), ctypes.byref(out))
+    if st != BTO_OK:
+        raise BtoError("bto_workspace_bytes", st, L.bto_last_invalid_arg())
+    return out.value
+
+
+def bto_device_status(ws, stream=None):
+    out = _c_int(0)
+    L = lib()
+    st = L.bto_device_status(_ptr(ws), _stream(stream), ctypes.byref(out))
+    if st != BTO_OK:
+        raise BtoError("bto_device_status", st, L.bto_last_invalid_arg())
+    return out.value
+
+
+def exported_symbols():
+    """Names the binding expects libbto.so to export."""
+    return sorted(list(SIGNATURES) + ["bto_version", "bto_status_string", "bto_last_invalid_arg",
+                                      "bto_workspace_bytes", "bto_device_status"])

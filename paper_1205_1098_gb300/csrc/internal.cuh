@@ -1,0 +1,123 @@
+// Internal declarations shared by the translation units of libbto.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include "bto.h"
+
+namespace bto {
+
+// ------------------------------------------------------------ host helpers
+void set_invalid_arg(int pos);
+void clear_invalid_arg();
+int last_invalid_arg();
+
+// Device facts, cached per device.
+struct DeviceInfo {
+    int sms = 0;
+    int max_smem_optin = 0;
+    bool coop = false;
+};
+bool device_info(DeviceInfo* out);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Byte extent touched by an m x n column-major matrix with leading dimension ld.
+inline size_t mat_extent_bytes(int64_t m, int64_t n, int64_t ld, size_t esz) {
+    if (m <= 0 || n <= 0) return 0;
+    return ((size_t)(n - 1) * (size_t)ld + (size_t)m) * esz;
+}
+inline bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    if (!na || !nb) return false;
+    uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
+
+// Workspace header: the first 256 bytes hold the device status word and,
+// for kernels with inter-block waits, nothing else (counters follow in
+// their own region).
+constexpr size_t WS_HEADER = 256;
+
+// Launch status -> bto_status.
+inline bto_status launch_status() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BTO_OK : BTO_ERR_CUDA;
+}
+
+// ------------------------------------------------------------ panel engine
+// The matrix is cut into NR row blocks x NC column panels; tile (rb, cb)
+// leaves row-vector partials in qpart[cb][.] and column-vector partials in
+// spart[rb][.]; a combine kernel adds them in a fixed order.
+enum PanelMode { PM_QS = 0, PM_Q = 1, PM_S = 2, PM_G1 = 3, PM_Q2 = 4 };
+
+struct PanelPlan {
+    int NR = 0, NC = 0;
+    int64_t TCmax = 0;     // widest column panel
+    int64_t ntiles = 0;
+    int grid = 0;
+    int64_t ldq = 0, lds = 0;  // leading dims of the partial arrays
+};
+PanelPlan panel_plan(int64_t m, int64_t n, int sms);
+size_t panel_smem_bytes(int mode, const PanelPlan& pl);
+
+struct PanelArgs {
+    int64_t m, n;
+    const double* A; int64_t lda;
+    const double* B; int64_t ldb;    // second input matrix (PM_Q2)
+    double* Bout;                    // output matrix (PM_G1), may equal A
+    const double* p;                 // column-indexed vector (PM_QS, PM_Q, PM_Q2)
+    const double* r;                 // row-indexed vector (PM_QS, PM_S, PM_G1: y)
+    const double* u1; const double* v1; const double* u2; const double* v2;   // PM_G1
+    double* qpart; double* qpart2; double* spart;
+    int64_t ldq, lds;
+    int NR, NC; int64_t ntiles; int reverse;
+};
+bto_status launch_panel(int mode, const PanelArgs& a, const PanelPlan& pl, cudaStream_t st);
+
+// out[i] = a1 * sum_k P1[k*ld1 + i] (+ a2 * sum_k P2[k*ld2 + i]) (+ b * v[i])
+struct CombineJob {
+    double* out; int64_t len;
+    const double* P1; int64_t ld1; int K1; double a1;
+    const double* P2; int64_t ld2; int K2; double a2;
+    const double* v; double b;
+};
+bto_status launch_combine(const CombineJob* jobs, int njobs, cudaStream_t st);
+
+// ------------------------------------------------------------ ATAX wavefront
+// Rows are cut into bands of TB rows; block c of a cooperative grid of G
+// blocks owns a fixed slice of columns (so it owns those entries of y).
+struct AtaxPlan {
+    int G = 0;          // blocks (one per SM)
+    int TB = 0;         // band height (rows)
+    int nbuf = 0;       // band slices resident in shared memory
+    int64_t nb = 0;     // number of bands
+    int64_t cmax = 0;   // widest column slice
+    size_t smem = 0;    // dynamic shared memory per block
+    bool fused = false; // false: the slices do not fit; the two-pass form runs
+};
+AtaxPlan atax_plan(int64_t m, int64_t n, const DeviceInfo& d);
+
+// ------------------------------------------------------------ workspace
+struct WsLayout {
+    size_t total = 0;
+    size_t off[6] = {0, 0, 0, 0, 0, 0};
+};
+bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type,
+                     const DeviceInfo& d, WsLayout* out);
+// Validates ws against the layout; sets the invalid-arg position on failure.
+bto_status check_ws(const void* ws, size_t ws_bytes, const WsLayout& L, int pos_ws);
+
+// ------------------------------------------------------------ vector helpers
+int vector_grid(int sms);                     // blocks of the reduction kernels
+bto_status launch_dot_partials(int64_t n, double alpha, const double* w, const double* v,
+                               const double* u, double* z, double* partials, int grid,
+                               int mode, cudaStream_t st);   // mode 0: axpydot, 1: plain dot of w,u
+bto_status launch_dot_final(const double* partials, int grid, double* r, cudaStream_t st);
+bto_status launch_waxpby(int64_t n, double alpha, const double* x, double beta, const double* y,
+                         double* w, int sms, cudaStream_t st);
+bto_status launch_vadd(int64_t n, const double* w, const double* y, const double* z, double* x,
+                       int sms, cudaStream_t st);
+
+}  // namespace bto

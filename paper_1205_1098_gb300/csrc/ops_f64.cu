@@ -1,0 +1,267 @@
+// Fused FP64 entry points built on the panel engine (BICGK, GEMVER, GESUMMV,
+// DGEMV, DGEMVT) and the workspace layouts of every entry point.
+#include "check.cuh"
+
+namespace bto {
+
+namespace {
+
+size_t region(size_t& cur, size_t bytes) {
+    size_t at = cur;
+    cur += round_up((int64_t)bytes, 256);
+    return at;
+}
+
+}  // namespace
+
+bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type, const DeviceInfo& d,
+                     WsLayout* out) {
+    if (a_type != BTO_F64) return BTO_ERR_UNSUPPORTED;
+    WsLayout L;
+    size_t cur = WS_HEADER;
+    const PanelPlan pl = panel_plan(m, n, d.sms);
+    const size_t qp = (size_t)pl.NC * pl.ldq * sizeof(double);
+    const size_t sp = (size_t)pl.NR * pl.lds * sizeof(double);
+    switch (op) {
+        case BTO_OP_BICGK:
+        case BTO_OP_GEMVER:
+        case BTO_OP_DGEMVT:
+            L.off[0] = region(cur, qp);
+            L.off[1] = region(cur, sp);
+            break;
+        case BTO_OP_DGEMV:
+            L.off[0] = region(cur, qp);
+            break;
+        case BTO_OP_GESUMMV:
+            L.off[0] = region(cur, qp);
+            if (form == BTO_FORM_FUSED) L.off[1] = region(cur, qp);
+            break;
+        case BTO_OP_ATAX:
+            if (form == BTO_FORM_FUSED) {
+                const AtaxPlan ap = atax_plan(m, n, d);
+                if (ap.fused) {
+                    L.off[0] = region(cur, (size_t)2 * ap.nb * sizeof(unsigned));          // counters, flags
+                    L.off[1] = region(cur, (size_t)ap.nb * ap.G * ap.TB * sizeof(double)); // block partials of t
+                    L.off[2] = region(cur, (size_t)ap.nb * ap.TB * sizeof(double));        // t per band
+                    break;
+                }
+            }
+            L.off[0] = region(cur, (size_t)std::max<int64_t>(m, 1) * sizeof(double));    // t = A x
+            L.off[1] = region(cur, qp);
+            L.off[2] = region(cur, sp);
+            break;
+        case BTO_OP_AXPYDOT:
+            L.off[0] = region(cur, (size_t)vector_grid(d.sms) * sizeof(double));
+            break;
+        case BTO_OP_WAXPBY:
+        case BTO_OP_VADD:
+            cur = 0;
+            break;
+        default:
+            return BTO_ERR_INVALID_VALUE;
+    }
+    L.total = cur;
+    *out = L;
+    return BTO_OK;
+}
+
+}  // namespace bto
+
+using namespace bto;
+
+namespace {
+
+// Shared preamble: device facts and the workspace layout of op.
+bool prepare(int op, int form, int64_t m, int64_t n, DeviceInfo* d, WsLayout* L) {
+    if (!device_info(d)) return false;
+    return ws_layout(op, form, m, n, BTO_F64, *d, L) == BTO_OK;
+}
+
+double* wsd(void* ws, size_t off) { return reinterpret_cast<double*>(static_cast<char*>(ws) + off); }
+
+}  // namespace
+
+extern "C" bto_status bto_bicgk(int64_t m, int64_t n, const double* A, int64_t lda,
+                                const double* p, const double* r, double* q, double* s,
+                                void* ws, size_t ws_bytes, bto_stream_t stream) {
+    clear_invalid_arg();
+    Check c;
+    c.size(1, m); c.size(2, n);
+    if (!c.ok()) return c.finish();
+    const size_t Ab = mat_extent_bytes(m, n, lda, 8);
+    c.ptr(3, A, m > 0 && n > 0); c.ld(4, lda, m);
+    c.ptr(5, p, n > 0); c.ptr(6, r, m > 0); c.ptr(7, q, m > 0); c.ptr(8, s, n > 0);
+    c.disjoint(7, q, vbytes(m), A, Ab); c.disjoint(7, q, vbytes(m), p, vbytes(n));
+    c.disjoint(7, q, vbytes(m), r, vbytes(m)); c.disjoint(7, q, vbytes(m), s, vbytes(n));
+    c.disjoint(8, s, vbytes(n), A, Ab); c.disjoint(8, s, vbytes(n), p, vbytes(n));
+    c.disjoint(8, s, vbytes(n), r, vbytes(m));
+    DeviceInfo d; WsLayout L;
+    if (c.ok() && !prepare(BTO_OP_BICGK, BTO_FORM_FUSED, m, n, &d, &L)) return BTO_ERR_CUDA;
+    if (c.ok()) c.ws(9, ws, ws_bytes, L);
+    if (!c.ok()) return c.finish();
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const PanelPlan pl = panel_plan(m, n, d.sms);
+    PanelArgs a{};
+    a.m = m; a.n = n; a.A = A; a.lda = lda; a.p = p; a.r = r;
+    a.qpart = wsd(ws, L.off[0]); a.spart = wsd(ws, L.off[1]);
+    a.ldq = pl.ldq; a.lds = pl.lds; a.NR = pl.NR; a.NC = pl.NC; a.ntiles = pl.ntiles;
+    bto_status e = launch_panel(PM_QS, a, pl, st);
+    if (e != BTO_OK) return e;
+    CombineJob j[2] = {};
+    j[0] = {q, m, a.qpart, pl.ldq, pl.NC, 1.0, nullptr, 0, 0, 0.0, nullptr, 0.0};
+    j[1] = {s, n, a.spart, pl.lds, pl.NR, 1.0, nullptr, 0, 0, 0.0, nullptr, 0.0};
+    return launch_combine(j, 2, st);
+}
+
+extern "C" bto_status bto_dgemv(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                                const double* x, double beta, const double* y, double* z,
+                                void* ws, size_t ws_bytes, bto_stream_t stream) {
+    clear_invalid_arg();
+    Check c;
+    c.size(1, m); c.size(2, n);
+    if (!c.ok()) return c.finish();
+    const size_t Ab = mat_extent_bytes(m, n, lda, 8);
+    c.ptr(4, A, m > 0 && n > 0); c.ld(5, lda, m);
+    c.ptr(6, x, n > 0); c.ptr(8, y, m > 0); c.ptr(9, z, m > 0);
+    c.disjoint(9, z, vbytes(m), A, Ab); c.disjoint(9, z, vbytes(m), x, vbytes(n));
+    if (z != y) c.disjoint(9, z, vbytes(m), y, vbytes(m));
+    DeviceInfo d; WsLayout L;
+    if (c.ok() && !prepare(BTO_OP_DGEMV, BTO_FORM_FUSED, m, n, &d, &L)) return BTO_ERR_CUDA;
+    if (c.ok()) c.ws(10, ws, ws_bytes, L);
+    if (!c.ok()) return c.finish();
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const PanelPlan pl = panel_plan(m, n, d.sms);
+    PanelArgs a{};
+    a.m = m; a.n = n; a.A = A; a.lda = lda; a.p = x;
+    a.qpart = wsd(ws, L.off[0]);
+    a.ldq = pl.ldq; a.lds = pl.lds; a.NR = pl.NR; a.NC = pl.NC; a.ntiles = pl.ntiles;
+    bto_status e = launch_panel(PM_Q, a, pl, st);
+    if (e != BTO_OK) return e;
+    CombineJob j = {z, m, a.qpart, pl.ldq, pl.NC, alpha, nullptr, 0, 0, 0.0, y, beta};
+    return launch_combine(&j, 1, st);
+}
+
+extern "C" bto_status bto_gesummv(int64_t m, int64_t n, double alpha, const double* A,
+                                  int64_t lda, double beta, const double* B, int64_t ldb,
+                                  const double* x, double* y, void* ws, size_t ws_bytes,
+                                  bto_stream_t stream) {
+    clear_invalid_arg();
+    Check c;
+    c.size(1, m); c.size(2, n);
+    if (!c.ok()) return c.finish();
+    const size_t Ab = mat_extent_bytes(m, n, lda, 8), Bb = mat_extent_bytes(m, n, ldb, 8);
+    c.ptr(4, A, m > 0 && n > 0); c.ld(5, lda, m);
+    c.ptr(7, B, m > 0 && n > 0); c.ld(8, ldb, m);
+    c.ptr(9, x, n > 0); c.ptr(10, y, m > 0);
+    c.disjoint(10, y, vbytes(m), A, Ab); c.disjoint(10, y, vbytes(m), B, Bb);
+    c.disjoint(10, y, vbytes(m), x, vbytes(n));
+    DeviceInfo d; WsLayout L;
+    if (c.ok() && !prepare(BTO_OP_GESUMMV, BTO_FORM_FUSED, m, n, &d, &L)) return BTO_ERR_CUDA;
+    if (c.ok()) c.ws(11, ws, ws_bytes, L);
+    if (!c.ok()) return c.finish();
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const PanelPlan pl = panel_plan(m, n, d.sms);
+    PanelArgs a{};
+    a.m = m; a.n = n; a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.p = x;
+    a.qpart = wsd(ws, L.off[0]); a.qpart2 = wsd(ws, L.off[1]);
+    a.ldq = pl.ldq; a.lds = pl.lds; a.NR = pl.NR; a.NC = pl.NC; a.ntiles = pl.ntiles;
+    bto_status e = launch_panel(PM_Q2, a, pl, st);
+    if (e != BTO_OK) return e;
+    CombineJob j = {y, m, a.qpart, pl.ldq, pl.NC, alpha, a.qpart2, pl.ldq, pl.NC, beta, nullptr, 0.0};
+    return launch_combine(&j, 1, st);
+}
+
+extern "C" bto_status bto_dgemvt(int64_t m, int64_t n, double alpha, double beta,
+                                 const double* A, int64_t lda, const double* y, const double* z,
+                                 double* x, double* w, void* ws, size_t ws_bytes,
+                                 bto_stream_t stream) {
+    clear_invalid_arg();
+    Check c;
+    c.size(1, m); c.size(2, n);
+    if (!c.ok()) return c.finish();
+    const size_t Ab = mat_extent_bytes(m, n, lda, 8);
+    c.ptr(5, A, m > 0 && n > 0); c.ld(6, lda, m);
+    c.ptr(7, y, m > 0); c.ptr(8, z, n > 0); c.ptr(9, x, n > 0); c.ptr(10, w, m > 0);
+    c.disjoint(9, x, vbytes(n), A, Ab); c.disjoint(9, x, vbytes(n), y, vbytes(m));
+    if (x != z) c.disjoint(9, x, vbytes(n), z, vbytes(n));
+    c.disjoint(10, w, vbytes(m), A, Ab); c.disjoint(10, w, vbytes(m), y, vbytes(m));
+    c.disjoint(10, w, vbytes(m), z, vbytes(n)); c.disjoint(10, w, vbytes(m), x, vbytes(n));
+    DeviceInfo d; WsLayout L;
+    if (c.ok() && !prepare(BTO_OP_DGEMVT, BTO_FORM_FUSED, m, n, &d, &L)) return BTO_ERR_CUDA;
+    if (c.ok()) c.ws(11, ws, ws_bytes, L);
+    if (!c.ok()) return c.finish();
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const PanelPlan pl = panel_plan(m, n, d.sms);
+    PanelArgs a{};
+    a.m = m; a.n = n; a.A = A; a.lda = lda; a.r = y;
+    a.qpart = wsd(ws, L.off[0]); a.spart = wsd(ws, L.off[1]);
+    a.ldq = pl.ldq; a.lds = pl.lds; a.NR = pl.NR; a.NC = pl.NC; a.ntiles = pl.ntiles;
+    // Pass 1: x = beta A^T y + z (column sums).  Pass 2 needs the complete x.
+    bto_status e = launch_panel(PM_S, a, pl, st);
+    if (e != BTO_OK) return e;
+    CombineJob jx = {x, n, a.spart, pl.lds, pl.NR, beta, nullptr, 0, 0, 0.0, z, 1.0};
+    if ((e = launch_combine(&jx, 1, st)) != BTO_OK) return e;
+    // Pass 2: w = alpha A x, panels in reverse so the tail still in L2 is read first.
+    a.p = x; a.r = nullptr; a.reverse = 1;
+    if ((e = launch_panel(PM_Q, a, pl, st)) != BTO_OK) return e;
+    CombineJob jw = {w, m, a.qpart, pl.ldq, pl.NC, alpha, nullptr, 0, 0, 0.0, nullptr, 0.0};
+    return launch_combine(&jw, 1, st);
+}
+
+extern "C" bto_status bto_gemver(int64_t m, int64_t n, double alpha, double beta,
+                                 const double* A, int64_t lda, const double* u1,
+                                 const double* v1, const double* u2, const double* v2,
+                                 const double* y, const double* z, double* B, int64_t ldb,
+                                 double* x, double* w, void* ws, size_t ws_bytes,
+                                 bto_stream_t stream) {
+    clear_invalid_arg();
+    Check c;
+    c.size(1, m); c.size(2, n);
+    if (!c.ok()) return c.finish();
+    const size_t Ab = mat_extent_bytes(m, n, lda, 8), Bb = mat_extent_bytes(m, n, ldb, 8);
+    c.ptr(5, A, m > 0 && n > 0); c.ld(6, lda, m);
+    c.ptr(7, u1, m > 0); c.ptr(8, v1, n > 0); c.ptr(9, u2, m > 0); c.ptr(10, v2, n > 0);
+    c.ptr(11, y, m > 0); c.ptr(12, z, n > 0);
+    c.ptr(13, B, m > 0 && n > 0); c.ld(14, ldb, m);
+    c.ptr(15, x, n > 0); c.ptr(16, w, m > 0);
+    const void* ins[7] = {u1, v1, u2, v2, y, z, nullptr};
+    const size_t inb[7] = {vbytes(m), vbytes(n), vbytes(m), vbytes(n), vbytes(m), vbytes(n), 0};
+    if (!(B == A && ldb == lda)) c.disjoint(13, B, Bb, A, Ab);
+    for (int k = 0; k < 6; k++) c.disjoint(13, B, Bb, ins[k], inb[k]);
+    c.disjoint(15, x, vbytes(n), A, Ab); c.disjoint(15, x, vbytes(n), B, Bb);
+    for (int k = 0; k < 5; k++) c.disjoint(15, x, vbytes(n), ins[k], inb[k]);
+    if (x != z) c.disjoint(15, x, vbytes(n), z, vbytes(n));
+    c.disjoint(16, w, vbytes(m), A, Ab); c.disjoint(16, w, vbytes(m), B, Bb);
+    for (int k = 0; k < 6; k++) c.disjoint(16, w, vbytes(m), ins[k], inb[k]);
+    c.disjoint(16, w, vbytes(m), x, vbytes(n));
+    DeviceInfo d; WsLayout L;
+    if (c.ok() && !prepare(BTO_OP_GEMVER, BTO_FORM_FUSED, m, n, &d, &L)) return BTO_ERR_CUDA;
+    if (c.ok()) c.ws(17, ws, ws_bytes, L);
+    if (!c.ok()) return c.finish();
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const PanelPlan pl = panel_plan(m, n, d.sms);
+    PanelArgs a{};
+    a.m = m; a.n = n; a.A = A; a.lda = lda; a.Bout = B; a.ldb = ldb;
+    a.u1 = u1; a.v1 = v1; a.u2 = u2; a.v2 = v2; a.r = y;
+    a.qpart = wsd(ws, L.off[0]); a.spart = wsd(ws, L.off[1]);
+    a.ldq = pl.ldq; a.lds = pl.lds; a.NR = pl.NR; a.NC = pl.NC; a.ntiles = pl.ntiles;
+    // Pass 1: B = A + u1 v1^T + u2 v2^T written once, with x = beta B^T y + z
+    // fused into the same sweep (column sums of the new B).
+    bto_status e = launch_panel(PM_G1, a, pl, st);
+    if (e != BTO_OK) return e;
+    CombineJob jx = {x, n, a.spart, pl.lds, pl.NR, beta, nullptr, 0, 0, 0.0, z, 1.0};
+    if ((e = launch_combine(&jx, 1, st)) != BTO_OK) return e;
+    // Pass 2: w = alpha B x over the new B, last-written panels first (L2 reuse).
+    PanelArgs b{};
+    b.m = m; b.n = n; b.A = B; b.lda = ldb; b.p = x;
+    b.qpart = a.qpart; b.ldq = pl.ldq; b.lds = pl.lds; b.NR = pl.NR; b.NC = pl.NC;
+    b.ntiles = pl.ntiles; b.reverse = 1;
+    if ((e = launch_panel(PM_Q, b, pl, st)) != BTO_OK) return e;
+    CombineJob jw = {w, m, b.qpart, pl.ldq, pl.NC, alpha, nullptr, 0, 0, 0.0, nullptr, 0.0};
+    return launch_combine(&jw, 1, st);
+}

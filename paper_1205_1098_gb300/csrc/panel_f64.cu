@@ -1,0 +1,366 @@
+// Panel engine: one pass over a column-major FP64 matrix that evaluates the
+// fused statements of a Table I kernel tile by tile.
+//
+// The matrix is cut into NR row blocks x NC column panels (NR = 1 for wide
+// matrices, so a panel spans every row).  A block of 8 warps takes a tile
+// and walks it in row chunks of 2048 rows; within a chunk each lane owns 8
+// rows of every column (four 16-byte loads per column in the aligned form),
+// so a warp's loads of one column are 512 contiguous bytes.  For every
+// column the lane
+//   - adds A(i,j) * p_j into its row accumulators (the non-transposed
+//     product, "A p": rows are independent, no reduction inside the tile),
+//   - forms sum_i A(i,j) * r_i over its 8 rows (the transposed product,
+//     "A^T r": a reduction over rows).
+// After a group of 32 columns the 32 lanes hold 32 column partials each; a
+// transposing butterfly (5 rounds of shuffles, 31 adds per lane) leaves lane
+// l with the warp's sum for column l of the group, so the transposed product
+// costs about one extra add per column per lane instead of a shuffle tree
+// per column.  Warps then add their column sums into per-warp shared-memory
+// rows, which the block sums in warp order at the end of the tile.
+//
+// This is the GPU form of the paper's fused partitioned loop nests
+// (Section III-C fuse sets; Section III-D partition compatibility): both
+// products read each A(i,j) once, and the "reduction at the parallel level"
+// that a column partition of the non-transposed product introduces is a
+// per-panel partial vector that a second kernel adds up in panel order.
+// All sums run in a fixed order, so results are bitwise reproducible.
+#include "internal.cuh"
+#include <algorithm>
+
+namespace bto {
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kRPT = 8;                           // rows per lane per column
+constexpr int kRowsPerWarp = 32 * kRPT;           // 256
+constexpr int kChunk = kWarps * kRowsPerWarp;     // 2048 rows per chunk
+constexpr int64_t kMaxPanel = 512;                // widest column panel
+
+// Lane l ends with sum over the warp's lanes of v[l] (v is destroyed).
+__device__ __forceinline__ double transpose_reduce32(double (&v)[32], int lane) {
+#pragma unroll
+    for (int half = 16; half >= 1; half >>= 1) {
+        const bool upper = (lane & half) != 0;
+#pragma unroll
+        for (int k = 0; k < half; k++) {
+            double send = upper ? v[k] : v[k + half];
+            double keep = upper ? v[k + half] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+        }
+    }
+    return v[0];
+}
+
+// Row offset (within a chunk) of the lane's k-th element.
+template <int VEC>
+__device__ __forceinline__ int row_of(int warp, int lane, int k) {
+    if (VEC == 2) return warp * kRowsPerWarp + (k >> 1) * 64 + 2 * lane + (k & 1);
+    return warp * kRowsPerWarp + k * 32 + lane;
+}
+
+// Loads the lane's 8 elements of one column segment; rows >= rend read as 0.
+template <int VEC>
+__device__ __forceinline__ void load_col(const double* __restrict__ col, int64_t R0, int64_t rend,
+                                         int warp, int lane, double (&a)[kRPT]) {
+    if (VEC == 2) {
+#pragma unroll
+        for (int h = 0; h < kRPT / 2; h++) {
+            int64_t i = R0 + row_of<2>(warp, lane, 2 * h);
+            if (i + 1 < rend) {
+                double2 t = __ldg(reinterpret_cast<const double2*>(col + i));
+                a[2 * h] = t.x; a[2 * h + 1] = t.y;
+            } else if (i < rend) {
+                a[2 * h] = __ldg(col + i); a[2 * h + 1] = 0.0;
+            } else {
+                a[2 * h] = 0.0; a[2 * h + 1] = 0.0;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kRPT; k++) {
+            int64_t i = R0 + row_of<1>(warp, lane, k);
+            a[k] = (i < rend) ? __ldg(col + i) : 0.0;
+        }
+    }
+}
+
+// Plain (coherent) loads, for the GEMVER pass that may write B over A.
+template <int VEC>
+__device__ __forceinline__ void load_col_rw(const double* col, int64_t R0, int64_t rend,
+                                            int warp, int lane, double (&a)[kRPT]) {
+    if (VEC == 2) {
+#pragma unroll
+        for (int h = 0; h < kRPT / 2; h++) {
+            int64_t i = R0 + row_of<2>(warp, lane, 2 * h);
+            if (i + 1 < rend) {
+                double2 t = *reinterpret_cast<const double2*>(col + i);
+                a[2 * h] = t.x; a[2 * h + 1] = t.y;
+            } else if (i < rend) {
+                a[2 * h] = col[i]; a[2 * h + 1] = 0.0;
+            } else {
+                a[2 * h] = 0.0; a[2 * h + 1] = 0.0;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kRPT; k++) {
+            int64_t i = R0 + row_of<1>(warp, lane, k);
+            a[k] = (i < rend) ? col[i] : 0.0;
+        }
+    }
+}
+
+template <int VEC>
+__device__ __forceinline__ void store_col(double* col, int64_t R0, int64_t rend, int warp, int lane,
+                                          const double (&b)[kRPT]) {
+    if (VEC == 2) {
+#pragma unroll
+        for (int h = 0; h < kRPT / 2; h++) {
+            int64_t i = R0 + row_of<2>(warp, lane, 2 * h);
+            if (i + 1 < rend) {
+                *reinterpret_cast<double2*>(col + i) = make_double2(b[2 * h], b[2 * h + 1]);
+            } else if (i < rend) {
+                col[i] = b[2 * h];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kRPT; k++) {
+            int64_t i = R0 + row_of<1>(warp, lane, k);
+            if (i < rend) col[i] = b[k];
+        }
+    }
+}
+
+template <int VEC>
+__device__ __forceinline__ void load_vec_rows(const double* __restrict__ v, int64_t R0, int64_t rend,
+                                              int warp, int lane, double (&o)[kRPT]) {
+#pragma unroll
+    for (int k = 0; k < kRPT; k++) {
+        int64_t i = R0 + row_of<VEC>(warp, lane, k);
+        o[k] = (i < rend) ? __ldg(v + i) : 0.0;
+    }
+}
+
+template <int VEC>
+__device__ __forceinline__ void store_vec_rows(double* v, int64_t R0, int64_t rend, int warp,
+                                               int lane, const double (&o)[kRPT]) {
+#pragma unroll
+    for (int k = 0; k < kRPT; k++) {
+        int64_t i = R0 + row_of<VEC>(warp, lane, k);
+        if (i < rend) v[i] = o[k];
+    }
+}
+
+// Balanced split of [0, n) into parts pieces; piece b starts at b*n/parts.
+__device__ __host__ __forceinline__ int64_t split_at(int64_t n, int64_t parts, int64_t b) {
+    return (n / parts) * b + ((n % parts) * b) / parts;   // floor(n*b/parts) without overflow
+}
+// Row blocks start on multiples of 64 rows so 16-byte row pairs stay aligned.
+__device__ __host__ __forceinline__ int64_t row_split_at(int64_t m, int64_t parts, int64_t b) {
+    if (b >= parts) return m;
+    return (split_at(m, parts, b) / 64) * 64;
+}
+
+template <int MODE, int VEC>
+__global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelArgs a) {
+    constexpr bool HAS_Q = (MODE == PM_QS || MODE == PM_Q || MODE == PM_Q2);
+    constexpr bool HAS_S = (MODE == PM_QS || MODE == PM_S || MODE == PM_G1);
+    extern __shared__ double sw[];   // [kWarps][TCmax] per-warp column sums
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tcmax = (a.n + a.NC - 1) / a.NC;
+
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const int64_t tt = a.reverse ? (a.ntiles - 1 - t) : t;
+        const int64_t cb = tt / a.NR, rb = tt % a.NR;
+        const int64_t c0 = split_at(a.n, a.NC, cb), c1 = split_at(a.n, a.NC, cb + 1);
+        const int64_t r0 = row_split_at(a.m, a.NR, rb), r1 = row_split_at(a.m, a.NR, rb + 1);
+        const int ncols = (int)(c1 - c0);
+
+        if (HAS_S) {
+            for (int k = threadIdx.x; k < kWarps * tcmax; k += kThreads) sw[k] = 0.0;
+            __syncthreads();
+        }
+
+        for (int64_t R0 = r0; R0 < r1; R0 += kChunk) {
+            double rv[kRPT], qacc[kRPT], qacc2[kRPT], u1r[kRPT], u2r[kRPT];
+            if (HAS_S) load_vec_rows<VEC>(a.r, R0, r1, warp, lane, rv);
+            if (MODE == PM_G1) {
+                load_vec_rows<VEC>(a.u1, R0, r1, warp, lane, u1r);
+                load_vec_rows<VEC>(a.u2, R0, r1, warp, lane, u2r);
+            }
+#pragma unroll
+            for (int k = 0; k < kRPT; k++) { qacc[k] = 0.0; qacc2[k] = 0.0; }
+
+            for (int64_t g0 = c0; g0 < c1; g0 += 32) {
+                const int nc = (int)((c1 - g0) < 32 ? (c1 - g0) : 32);
+                double sl[32];
+#pragma unroll
+                for (int jj = 0; jj < 32; jj++) {
+                    if (jj < nc) {
+                        const int64_t j = g0 + jj;
+                        double av[kRPT];
+                        if (MODE == PM_G1)
+                            load_col_rw<VEC>(a.A + j * a.lda, R0, r1, warp, lane, av);
+                        else
+                            load_col<VEC>(a.A + j * a.lda, R0, r1, warp, lane, av);
+                        if (MODE == PM_Q2) {
+                            double bv[kRPT];
+                            load_col<VEC>(a.B + j * a.ldb, R0, r1, warp, lane, bv);
+                            const double pj = __ldg(a.p + j);
+#pragma unroll
+                            for (int k = 0; k < kRPT; k++) {
+                                qacc[k] = fma(av[k], pj, qacc[k]);
+                                qacc2[k] = fma(bv[k], pj, qacc2[k]);
+                            }
+                        } else if (MODE == PM_G1) {
+                            const double v1j = __ldg(a.v1 + j), v2j = __ldg(a.v2 + j);
+                            double bv[kRPT];
+#pragma unroll
+                            for (int k = 0; k < kRPT; k++)
+                                bv[k] = fma(u2r[k], v2j, fma(u1r[k], v1j, av[k]));
+                            store_col<VEC>(a.Bout + j * a.ldb, R0, r1, warp, lane, bv);
+                            double acc = bv[0] * rv[0];
+#pragma unroll
+                            for (int k = 1; k < kRPT; k++) acc = fma(bv[k], rv[k], acc);
+                            sl[jj] = acc;
+                        } else {
+                            if (HAS_Q) {
+                                const double pj = __ldg(a.p + j);
+#pragma unroll
+                                for (int k = 0; k < kRPT; k++) qacc[k] = fma(av[k], pj, qacc[k]);
+                            }
+                            if (HAS_S) {
+                                double acc = av[0] * rv[0];
+#pragma unroll
+                                for (int k = 1; k < kRPT; k++) acc = fma(av[k], rv[k], acc);
+                                sl[jj] = acc;
+                            }
+                        }
+                    } else if (HAS_S) {
+                        sl[jj] = 0.0;
+                    }
+                }
+                if (HAS_S) {
+                    const double cs = transpose_reduce32(sl, lane);
+                    if (lane < nc) sw[warp * tcmax + (g0 - c0) + lane] += cs;
+                }
+            }
+            if (HAS_Q) {
+                store_vec_rows<VEC>(a.qpart + cb * a.ldq, R0, r1, warp, lane, qacc);
+                if (MODE == PM_Q2) store_vec_rows<VEC>(a.qpart2 + cb * a.ldq, R0, r1, warp, lane, qacc2);
+            }
+        }
+
+        if (HAS_S) {
+            __syncthreads();
+            for (int k = threadIdx.x; k < ncols; k += kThreads) {
+                double s = sw[k];
+#pragma unroll
+                for (int w = 1; w < kWarps; w++) s += sw[w * tcmax + k];
+                a.spart[rb * a.lds + c0 + k] = s;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void combine_kernel(const CombineJob j0, const CombineJob j1, int njobs) {
+    const int64_t tot = j0.len + (njobs > 1 ? j1.len : 0);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const CombineJob& J = (g < j0.len) ? j0 : j1;
+        const int64_t i = (g < j0.len) ? g : g - j0.len;
+        double s1 = 0.0;
+        for (int k = 0; k < J.K1; k++) s1 += __ldg(J.P1 + k * J.ld1 + i);
+        double o = J.a1 * s1;
+        if (J.P2) {
+            double s2 = 0.0;
+            for (int k = 0; k < J.K2; k++) s2 += __ldg(J.P2 + k * J.ld2 + i);
+            o = fma(J.a2, s2, o);
+        }
+        if (J.v) o = fma(J.b, J.v[i], o);
+        J.out[i] = o;
+    }
+}
+
+template <int MODE>
+bto_status launch_mode(const PanelArgs& a, const PanelPlan& pl, bool vec2, cudaStream_t st) {
+    const size_t smem = panel_smem_bytes(MODE, pl);
+    if (vec2) {
+        auto k = panel_kernel<MODE, 2>;
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return BTO_ERR_CUDA;
+        k<<<pl.grid, kThreads, smem, st>>>(a);
+    } else {
+        auto k = panel_kernel<MODE, 1>;
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return BTO_ERR_CUDA;
+        k<<<pl.grid, kThreads, smem, st>>>(a);
+    }
+    return launch_status();
+}
+
+}  // namespace
+
+PanelPlan panel_plan(int64_t m, int64_t n, int sms) {
+    PanelPlan pl;
+    pl.ldq = round_up(m > 0 ? m : 1, 32);
+    pl.lds = round_up(n > 0 ? n : 1, 32);
+    if (m <= 0 || n <= 0) return pl;
+    const int64_t G = sms;
+    int64_t NC = ceil_div(n, ceil_div(n, G));           // balanced panels, about G of them
+    if (ceil_div(n, NC) > kMaxPanel) NC = ceil_div(n, kMaxPanel);
+    int64_t NR = 1;
+    if (NC < G) {   // few columns: split the rows too, in blocks of >= 256 rows
+        NR = std::max<int64_t>(1, std::min<int64_t>(G / NC, ceil_div(m, 256)));
+    }
+    // Row blocks start on multiples of 64: drop blocks that would be empty.
+    while (NR > 1 && row_split_at(m, NR, 1) == 0) NR--;
+    pl.NR = (int)NR;
+    pl.NC = (int)NC;
+    pl.TCmax = ceil_div(n, NC);
+    pl.ntiles = NR * NC;
+    pl.grid = (int)std::min<int64_t>(pl.ntiles, G);
+    return pl;
+}
+
+size_t panel_smem_bytes(int mode, const PanelPlan& pl) {
+    const bool has_s = (mode == PM_QS || mode == PM_S || mode == PM_G1);
+    return has_s ? (size_t)kWarps * (size_t)pl.TCmax * sizeof(double) : 0;
+}
+
+bto_status launch_panel(int mode, const PanelArgs& a, const PanelPlan& pl, cudaStream_t st) {
+    if (pl.ntiles == 0) return BTO_OK;
+    // 16-byte loads need 16-byte aligned columns: every matrix base and an
+    // even leading dimension (rows pair up from even offsets).
+    bool vec2 = aligned16(a.A) && (a.lda % 2 == 0);
+    if (mode == PM_Q2) vec2 = vec2 && aligned16(a.B) && (a.ldb % 2 == 0);
+    if (mode == PM_G1) vec2 = vec2 && aligned16(a.Bout) && (a.ldb % 2 == 0);
+    switch (mode) {
+        case PM_QS: return launch_mode<PM_QS>(a, pl, vec2, st);
+        case PM_Q: return launch_mode<PM_Q>(a, pl, vec2, st);
+        case PM_S: return launch_mode<PM_S>(a, pl, vec2, st);
+        case PM_G1: return launch_mode<PM_G1>(a, pl, vec2, st);
+        case PM_Q2: return launch_mode<PM_Q2>(a, pl, vec2, st);
+    }
+    return BTO_ERR_INVALID_VALUE;
+}
+
+bto_status launch_combine(const CombineJob* jobs, int njobs, cudaStream_t st) {
+    int64_t tot = 0;
+    for (int i = 0; i < njobs; i++) tot += jobs[i].len;
+    if (tot == 0) return BTO_OK;
+    DeviceInfo d;
+    if (!device_info(&d)) return BTO_ERR_CUDA;
+    const int64_t blocks = std::min<int64_t>(ceil_div(tot, 256), (int64_t)d.sms * 8);
+    CombineJob j1 = njobs > 1 ? jobs[1] : jobs[0];
+    combine_kernel<<<(int)blocks, 256, 0, st>>>(jobs[0], j1, njobs);
+    return launch_status();
+}
+
+}  // namespace bto

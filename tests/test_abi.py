@@ -1,0 +1,91 @@
+"""The C ABI: the library builds, loads and exports every symbol include/bto.h
+declares, the binding's argument kinds match the header, and argument
+validation rejects bad calls before anything touches a GPU (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1205_1098_gb300 as bto
+from paper_1205_1098_gb300 import _lib, build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "bto.h")
+
+
+def _decls():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return re.findall(r"(?:bto_status|int|const char\s*\*)\s*(bto_\w+)\s*\(([^;]*)\);", src)
+
+
+def _kind(a):
+    if "*" in a:
+        return "p"
+    if "size_t" in a:
+        return "z"
+    if "uint64_t" in a:
+        return "u"
+    if "int64_t" in a:
+        return "i"
+    if "double" in a:
+        return "d"
+    if "bto_stream_t" in a:
+        return "s"
+    if "void" == a.strip():
+        return ""
+    if "int" in a:
+        return "k"
+    return "?"
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return bto.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = [n for n, _ in _decls()]
+    assert len(names) >= 27
+    for n in names:
+        assert hasattr(L, n), "libbto.so does not export " + n
+
+
+def test_binding_kinds_match_header():
+    for name, args in _decls():
+        if name in _lib.SIGNATURES:
+            got = "".join(_kind(a) for a in args.split(","))
+            assert got == _lib.SIGNATURES[name], name
+
+
+def test_status_strings(L):
+    assert bto.bto_version() >= 100
+    for s in range(7):
+        assert bto.bto_status_string(s).startswith("BTO_")
+
+
+def test_validation_without_gpu(L):
+    # Negative sizes, short leading dimensions and NULL operands are rejected
+    # before any CUDA call.
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_bicgk(-1, 4, 0, 1, 0, 0, 0, 0, 0, 0, 0)
+    assert e.value.status == _lib.BTO_ERR_INVALID_VALUE and e.value.arg == 1
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_bicgk(8, 4, 4096, 7, 4096, 8192, 12288, 16384, 0, 0, 0)
+    assert e.value.arg == 4   # lda < m
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_gemver(8, 4, 1.0, 1.0, 0, 8, 64, 128, 192, 256, 320, 384, 448, 8, 512, 576, 0, 0, 0)
+    assert e.value.arg == 5   # A NULL with m*n > 0
+    with pytest.raises(bto.BtoError) as e:   # output overlaps an input
+        bto.bto_vadd(16, 4096, 8192, 12288, 4096 + 64, 0)
+    assert e.value.arg == 5
+    with pytest.raises(bto.BtoError) as e:   # misaligned double pointer
+        bto.bto_waxpby(4, 1.0, 4097, 1.0, 8192, 12288, 0)
+    assert e.value.arg == 3
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_workspace_bytes(99, 0, 1, 1)
+    assert e.value.arg == 1
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_fill_f64(0, 0, 7, 4, 4, 0, 4096, 4, 0)
+    assert e.value.arg == 3

@@ -168,6 +168,34 @@ bto_status bto_waxpby(int64_t n, double alpha, const double *x, double beta,
 bto_status bto_vadd(int64_t n, const double *w, const double *y, const double *z,
                     double *x, bto_stream_t stream);
 
+/* BICGK without a workspace argument (the paper has no counterpart; this is
+ * a convenience of this library).  Some callers cannot call cudaMalloc: a
+ * plugin whose host application owns all device memory through its own
+ * allocator, code that must keep a device-memory footprint fixed when the
+ * library loads, and latency-critical loops, since cudaMalloc and cudaFree
+ * may synchronize the device.  This entry point computes exactly what
+ * bto_bicgk computes (same kernels, bitwise equal results) but keeps the
+ * split partial sums in a file-scope device array of
+ * BTO_NOALLOC_SCRATCH_BYTES (4 MiB) inside the library, which every GPU that
+ * loads the library holds until the process exits.  It allocates nothing.
+ *  - Size limit: the call is accepted when
+ *    bto_workspace_bytes(BTO_OP_BICGK, BTO_FORM_FUSED, m, n, BTO_F64) is at
+ *    most BTO_NOALLOC_SCRATCH_BYTES (for square FP64 problems on a 152-SM
+ *    GB300, up to about n = 3400); larger problems return BTO_ERR_WORKSPACE
+ *    with bto_last_invalid_arg() naming m (1) or n (2), and nothing runs.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array, and it keeps the last call's contents;
+ *    no part of it needs to start at zero.  Calls whose kernels overlap on
+ *    the GPU (different streams, no ordering between them) race on the
+ *    array and give undefined results: order them.
+ * Arguments, layout and errors are otherwise those of bto_bicgk. */
+#define BTO_NOALLOC_SCRATCH_BYTES ((size_t)4 << 20)
+bto_status bto_bicgk_noalloc(int64_t m, int64_t n, const double *A, int64_t lda,
+                             const double *p, const double *r, double *q, double *s,
+                             bto_stream_t stream);
+
 /* ------------------------------------------- unfused comparison sequences
  * Same operations, arguments and results as the fused entry points above,
  * computed as one GPU kernel per BLAS call, the way a program built from

@@ -39,6 +39,7 @@ SIGNATURES = {
     "bto_fill_f32": "uukiippis",
     "bto_fill_bf16": "uukiippis",
     "bto_debug_atax_stall": "iidpipppziks",
+    "bto_bicgk_noalloc": "iipipppps",
 }
 _KIND = {"i": _c_i64, "u": _c_u64, "d": _c_f64, "p": _c_ptr, "z": _c_size, "s": _c_ptr, "k": _c_int}
 

@@ -34,6 +34,7 @@ ALPHA, BETA = 1.5, 1.2
 FP64_FLOP_PER_CLK_PER_SM = 4.0   # 2 FP64 FMA per clock per SM (measured: 2.05)
 
 KERNELS = ["bicgk", "atax", "gesummv", "gemver", "dgemv", "dgemvt", "axpydot", "waxpby", "vadd"]
+MATRIX_KERNELS = KERNELS[:6]
 # Launches of our kernels per call (panel pass(es) + combine(s); ATAX is one cooperative kernel).
 LAUNCHES = {"bicgk": 2, "atax": 1, "gesummv": 2, "gemver": 4, "dgemv": 2, "dgemvt": 4,
             "axpydot": 2, "waxpby": 1, "vadd": 1}
@@ -167,8 +168,8 @@ class Suite:
         self.r = torch.empty(1, **f64)
         self.ws = {}
         for form in (0, 1):
-            size = max(bto.bto_workspace_bytes(k, form, m if k in KERNELS[:6] else 0,
-                                               n if k in KERNELS[:6] else N) for k in KERNELS)
+            size = max(bto.bto_workspace_bytes(k, form, m if k in MATRIX_KERNELS else 0,
+                                               n if k in MATRIX_KERNELS else N) for k in KERNELS)
             self.ws[form] = (torch.empty(size, dtype=torch.uint8, device="cuda"), size)
         torch.cuda.synchronize()
 
@@ -270,7 +271,7 @@ def e2e_steps(torch, bto, steps, warmup, m, n, N):
     suite.big = {k: torch.empty(N, **f64) for k in list(hbig) + list(outs_big_h)}
     suite.r = torch.empty(1, **f64)
     suite.ws = {}
-    size = max(bto.bto_workspace_bytes(k, 0, m if k in KERNELS[:6] else 0, n if k in KERNELS[:6] else N)
+    size = max(bto.bto_workspace_bytes(k, 0, m if k in MATRIX_KERNELS else 0, n if k in MATRIX_KERNELS else N)
                for k in KERNELS)
     suite.ws[0] = (torch.empty(size, dtype=torch.uint8, device="cuda"), size)
     h2d = hA.numel() * 8 + hB.numel() * 8 + sum(t.numel() * 8 for t in hv.values()) + \
@@ -365,13 +366,19 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
+    ap.add_argument("--only", default=None, help="comma-separated kernels (profiling runs)")
+    ap.add_argument("--n", type=int, default=N_MAT, help="matrix size (profiling runs)")
+    ap.add_argument("--nvec", type=int, default=N_VEC, help="vector length (profiling runs)")
     args = ap.parse_args()
+    if args.only:
+        global KERNELS
+        KERNELS = [k for k in KERNELS if k in args.only.split(",")]
     if args.impl == "reference":
         run_reference(args)
         return
@@ -390,8 +397,8 @@ def main():
     build.build()
     import paper_1205_1098_gb300 as bto
 
-    m = n = N_MAT
-    N = N_VEC
+    m = n = args.n
+    N = args.nvec
     hbm, sm_max, peak_src = load_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     fp64_peak = FP64_FLOP_PER_CLK_PER_SM * sms * sm_max * 1e6 / 1e12   # TFLOP/s
@@ -462,7 +469,7 @@ def main():
                "sample": "the oracle (plain C, FP64, 1 thread) on the same suite at n=%d matrices and "
                          "%d-element vectors (%.1f s), bytes scaled the same way" % (ns, nv, secs)}
 
-    launches = args.steps * sum(LAUNCHES.values())
+    launches = args.steps * sum(LAUNCHES[k] for k in KERNELS)
     if rank == 0:
         print(json.dumps({
             "metric": "fused FP64 kernel-suite effective HBM bandwidth (GEMVER/BiCGK/ATAX/GESUMMV/"

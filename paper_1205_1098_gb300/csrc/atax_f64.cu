@@ -36,6 +36,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int64_t kMaxSlice = 512;        // widest column slice per block
 constexpr int kYPerThread = kMaxSlice / kThreads;
+constexpr int kBatch = 8;             // column segments in flight per warp in phase 1
 
 struct AtaxArgs {
     int64_t m, n;
@@ -103,27 +104,44 @@ __global__ void __launch_bounds__(kThreads, 1) atax_kernel(const AtaxArgs a) {
             double tp[RPL];
 #pragma unroll
             for (int k = 0; k < RPL; k++) tp[k] = 0.0;
-            for (int jl = warp; jl < nc; jl += kWarps) {
-                const double* col = a.A + (c0 + jl) * a.lda;
-                const double xj = __ldg(a.x + c0 + jl);
-                double v[RPL];
-                if (RPL == 2) {
-                    const int64_t i = R0 + 2 * lane;
-                    if (VEC2 && i + 1 < rend) {
-                        double2 t = __ldg(reinterpret_cast<const double2*>(col + i));
-                        v[0] = t.x; v[RPL - 1] = t.y;
-                    } else {
-                        v[0] = (i < rend) ? __ldg(col + i) : 0.0;
-                        v[RPL - 1] = (i + 1 < rend) ? __ldg(col + i + 1) : 0.0;
+            // Columns jl = warp + kWarps*u, in batches of kBatch per warp, so each
+            // warp has kBatch column segments in flight before it consumes any.
+            for (int jb = warp; jb < nc; jb += kWarps * kBatch) {
+                double v[kBatch][RPL], xj[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; u++) {
+                    const int jl = jb + u * kWarps;
+                    xj[u] = 0.0;
+#pragma unroll
+                    for (int k = 0; k < RPL; k++) v[u][k] = 0.0;
+                    if (jl < nc) {
+                        const double* col = a.A + (c0 + jl) * a.lda;
+                        xj[u] = __ldg(a.x + c0 + jl);
+                        if (RPL == 2) {
+                            const int64_t i = R0 + 2 * lane;
+                            if (VEC2 && i + 1 < rend) {
+                                double2 t = __ldg(reinterpret_cast<const double2*>(col + i));
+                                v[u][0] = t.x; v[u][RPL - 1] = t.y;
+                            } else {
+                                if (i < rend) v[u][0] = __ldg(col + i);
+                                if (i + 1 < rend) v[u][RPL - 1] = __ldg(col + i + 1);
+                            }
+                        } else {
+                            const int64_t i = R0 + lane;
+                            if (i < rend) v[u][0] = __ldg(col + i);
+                        }
                     }
-                } else {
-                    const int64_t i = R0 + lane;
-                    v[0] = (i < rend) ? __ldg(col + i) : 0.0;
                 }
 #pragma unroll
-                for (int k = 0; k < RPL; k++) {
-                    tp[k] = fma(v[k], xj, tp[k]);
-                    buf[jl * a.cstride + RPL * lane + k] = v[k];
+                for (int u = 0; u < kBatch; u++) {
+                    const int jl = jb + u * kWarps;
+                    if (jl < nc) {
+#pragma unroll
+                        for (int k = 0; k < RPL; k++) {
+                            tp[k] = fma(v[u][k], xj[u], tp[k]);
+                            buf[jl * a.cstride + RPL * lane + k] = v[u][k];
+                        }
+                    }
                 }
             }
 #pragma unroll
@@ -134,10 +152,12 @@ __global__ void __launch_bounds__(kThreads, 1) atax_kernel(const AtaxArgs a) {
 #pragma unroll
                 for (int w = 1; w < kWarps; w++) s += tred[w * TB + threadIdx.x];
                 a.tpart[(b * G + c) * TB + threadIdx.x] = s;
-                __threadfence();
             }
             __syncthreads();
             if (threadIdx.x == 0) {
+                // The barrier orders the block's partial stores before this
+                // fence; fence + atomic form the release of this band's partial.
+                __threadfence();
                 const unsigned old = atomicAdd(a.cnt + b, 1u);
                 s_last = (old == (unsigned)(G - 1));
             }
@@ -149,19 +169,27 @@ __global__ void __launch_bounds__(kThreads, 1) atax_kernel(const AtaxArgs a) {
                 __threadfence();
                 constexpr int P = kThreads / TB;
                 const int row = threadIdx.x % TB, part = threadIdx.x / TB;
-                double s = 0.0;
-                for (int cc = part; cc < G; cc += P) s += __ldcg(a.tpart + (b * G + cc) * TB + row);
-                rsum[threadIdx.x] = s;
+                // Eight independent accumulators keep eight loads in flight.
+                double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                int cc = part;
+                for (; cc + 7 * P < G; cc += 8 * P) {
+#pragma unroll
+                    for (int u = 0; u < 8; u++) acc[u] += __ldcg(a.tpart + (b * G + cc + u * P) * TB + row);
+                }
+                for (int u = 0; cc < G; cc += P, u++) acc[u] += __ldcg(a.tpart + (b * G + cc) * TB + row);
+                rsum[threadIdx.x] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
                 __syncthreads();
                 if (threadIdx.x < TB) {
                     double t = rsum[threadIdx.x];
 #pragma unroll
                     for (int p = 1; p < P; p++) t += rsum[p * TB + threadIdx.x];
                     a.tfull[b * TB + threadIdx.x] = t;
-                    __threadfence();
                 }
                 __syncthreads();
-                if (threadIdx.x == 0 && b != a.stall_band) st_release(a.flag + b, 1u);
+                if (threadIdx.x == 0 && b != a.stall_band) {
+                    __threadfence();
+                    st_release(a.flag + b, 1u);
+                }
             }
         }
         // ---------------- phase 2: y += A_band^T t_band for band b - D
@@ -189,11 +217,15 @@ __global__ void __launch_bounds__(kThreads, 1) atax_kernel(const AtaxArgs a) {
             for (int k = 0; k < kYPerThread; k++) {
                 const int jl = threadIdx.x + k * kThreads;
                 if (jl < nc) {
-                    double acc = yacc[k];
+                    // Two interleaved chains (even and odd rows), added in a fixed order.
+                    double e0 = 0.0, e1 = 0.0;
                     const double* colbuf = buf + jl * a.cstride;
 #pragma unroll 16
-                    for (int i = 0; i < TB; i++) acc = fma(colbuf[i], ts[i], acc);
-                    yacc[k] = acc;
+                    for (int i = 0; i < TB; i += 2) {
+                        e0 = fma(colbuf[i], ts[i], e0);
+                        e1 = fma(colbuf[i + 1], ts[i + 1], e1);
+                    }
+                    yacc[k] += e0 + e1;
                 }
             }
             __syncthreads();
@@ -219,14 +251,27 @@ AtaxPlan atax_plan(int64_t m, int64_t n, const DeviceInfo& d) {
     AtaxPlan p;
     p.G = d.sms;
     if (m <= 0 || n <= 0) { p.fused = true; return p; }
-    p.cmax = ceil_div(n, p.G);
-    if (p.cmax > kMaxSlice || !d.coop) return p;
-    const size_t limit = (size_t)d.max_smem_optin - 2048;
+    if (!d.coop) return p;
+    // One block per SM: more blocks per band multiply the partials the last
+    // arrival must add, which costs more than the overlap they bring.
     const int cand[4][2] = {{64, 3}, {64, 2}, {32, 3}, {32, 2}};
-    for (auto& cd : cand) {
-        const size_t s = atax_smem(cd[0], cd[1], p.cmax);
-        if (s <= limit) {
-            p.TB = cd[0]; p.nbuf = cd[1]; p.smem = s;
+    for (int per_sm = 1; per_sm >= 1; per_sm--) {
+        const int64_t G = (int64_t)d.sms * per_sm;
+        const int64_t cmax = ceil_div(n, G);
+        if (cmax > kMaxSlice) continue;
+        const size_t limit = ((size_t)d.max_smem_optin - 2048) / per_sm;
+        for (auto& cd : cand) {
+            const size_t sz = atax_smem(cd[0], cd[1], cmax);
+            if (sz > limit) continue;
+            void* fn = cd[0] == 64 ? atax_fn<64, true>() : atax_fn<32, false>();
+            int occ = 0;
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, sz) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (occ < per_sm) continue;
+            p.G = (int)G; p.cmax = cmax; p.TB = cd[0]; p.nbuf = cd[1]; p.smem = sz;
             p.nb = ceil_div(m, p.TB);
             p.fused = true;
             return p;
@@ -306,7 +351,7 @@ bto_status atax_impl(int64_t m, int64_t n, double beta, const double* A, int64_t
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, ap.smem) != cudaSuccess)
         return BTO_ERR_CUDA;
-    if (occ < 1) return BTO_ERR_UNSUPPORTED;
+    if ((int64_t)occ * d.sms < ap.G) return BTO_ERR_UNSUPPORTED;   // cooperative grid must be co-resident
     void* args[] = {(void*)&a};
     if (cudaLaunchCooperativeKernel(fn, dim3(ap.G), dim3(kThreads), args, ap.smem, st) != cudaSuccess)
         return BTO_ERR_CUDA;

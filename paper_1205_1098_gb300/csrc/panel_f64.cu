@@ -11,11 +11,11 @@
 //     product, "A p": rows are independent, no reduction inside the tile),
 //   - forms sum_i A(i,j) * r_i over its 8 rows (the transposed product,
 //     "A^T r": a reduction over rows).
-// After a group of 32 columns the 32 lanes hold 32 column partials each; a
-// transposing butterfly (5 rounds of shuffles, 31 adds per lane) leaves lane
-// l with the warp's sum for column l of the group, so the transposed product
-// costs about one extra add per column per lane instead of a shuffle tree
-// per column.  Warps then add their column sums into per-warp shared-memory
+// After a group of 16 columns the 32 lanes hold 16 column partials each; a
+// transposing butterfly (5 rounds of shuffles, 16 adds per lane) leaves lane
+// l with the warp's sum for column l mod 16 of the group, so the transposed
+// product costs one extra add per column per lane instead of a shuffle tree
+// per column.  Loads of four columns are issued before any is consumed.  Warps then add their column sums into per-warp shared-memory
 // rows, which the block sums in warp order at the end of the tile.
 //
 // This is the GPU form of the paper's fused partitioned loop nests
@@ -37,11 +37,16 @@ constexpr int kRPT = 8;                           // rows per lane per column
 constexpr int kRowsPerWarp = 32 * kRPT;           // 256
 constexpr int kChunk = kWarps * kRowsPerWarp;     // 2048 rows per chunk
 constexpr int64_t kMaxPanel = 512;                // widest column panel
+constexpr int kGroup = 16;                        // columns per transposing group
+constexpr int kU = 4;                             // columns loaded before any is consumed
 
-// Lane l ends with sum over the warp's lanes of v[l] (v is destroyed).
-__device__ __forceinline__ double transpose_reduce32(double (&v)[32], int lane) {
+// Transposing butterfly over 16 column partials: after four rounds lane l
+// holds, for column l mod 16, the sum over the 16 lanes that share bit 4 of
+// l; one more exchange with lane l ^ 16 completes the warp sum.  16 adds per
+// lane for 16 columns (v is destroyed).
+__device__ __forceinline__ double transpose_reduce16(double (&v)[16], int lane) {
 #pragma unroll
-    for (int half = 16; half >= 1; half >>= 1) {
+    for (int half = 8; half >= 1; half >>= 1) {
         const bool upper = (lane & half) != 0;
 #pragma unroll
         for (int k = 0; k < half; k++) {
@@ -50,7 +55,7 @@ __device__ __forceinline__ double transpose_reduce32(double (&v)[32], int lane) 
             v[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
         }
     }
-    return v[0];
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
 // Row offset (within a chunk) of the lane's k-th element.
@@ -164,8 +169,14 @@ __device__ __host__ __forceinline__ int64_t row_split_at(int64_t m, int64_t part
     return (split_at(m, parts, b) / 64) * 64;
 }
 
+// Blocks per SM: the single-product modes fit in 128 registers and run two
+// blocks per SM, so one block's load latency overlaps the other's
+// arithmetic; the two-product modes need more registers than that.
+template <int MODE>
+struct BlocksPerSM { static constexpr int value = (MODE == PM_Q || MODE == PM_S) ? 2 : 1; };
+
 template <int MODE, int VEC>
-__global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelArgs a) {
+__global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kernel(const PanelArgs a) {
     constexpr bool HAS_Q = (MODE == PM_QS || MODE == PM_Q || MODE == PM_Q2);
     constexpr bool HAS_S = (MODE == PM_QS || MODE == PM_S || MODE == PM_G1);
     extern __shared__ double sw[];   // [kWarps][TCmax] per-warp column sums
@@ -194,57 +205,67 @@ __global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelArgs a) {
 #pragma unroll
             for (int k = 0; k < kRPT; k++) { qacc[k] = 0.0; qacc2[k] = 0.0; }
 
-            for (int64_t g0 = c0; g0 < c1; g0 += 32) {
-                const int nc = (int)((c1 - g0) < 32 ? (c1 - g0) : 32);
-                double sl[32];
+            for (int64_t g0 = c0; g0 < c1; g0 += kGroup) {
+                const int nc = (int)((c1 - g0) < kGroup ? (c1 - g0) : kGroup);
+                double sl[kGroup];
 #pragma unroll
-                for (int jj = 0; jj < 32; jj++) {
-                    if (jj < nc) {
-                        const int64_t j = g0 + jj;
-                        double av[kRPT];
-                        if (MODE == PM_G1)
-                            load_col_rw<VEC>(a.A + j * a.lda, R0, r1, warp, lane, av);
-                        else
-                            load_col<VEC>(a.A + j * a.lda, R0, r1, warp, lane, av);
-                        if (MODE == PM_Q2) {
-                            double bv[kRPT];
-                            load_col<VEC>(a.B + j * a.ldb, R0, r1, warp, lane, bv);
-                            const double pj = __ldg(a.p + j);
+                for (int jb = 0; jb < kGroup; jb += kU) {
+                    // Issue the loads of kU columns before consuming any of them.
+                    double av[kU][kRPT], bv[kU][kRPT], pj[kU], v1j[kU], v2j[kU];
 #pragma unroll
-                            for (int k = 0; k < kRPT; k++) {
-                                qacc[k] = fma(av[k], pj, qacc[k]);
-                                qacc2[k] = fma(bv[k], pj, qacc2[k]);
+                    for (int u = 0; u < kU; u++) {
+                        const int jj = jb + u;
+                        if (jj < nc) {
+                            const int64_t j = g0 + jj;
+                            if (MODE == PM_G1) {
+                                load_col_rw<VEC>(a.A + j * a.lda, R0, r1, warp, lane, av[u]);
+                                v1j[u] = __ldg(a.v1 + j);
+                                v2j[u] = __ldg(a.v2 + j);
+                            } else {
+                                load_col<VEC>(a.A + j * a.lda, R0, r1, warp, lane, av[u]);
                             }
-                        } else if (MODE == PM_G1) {
-                            const double v1j = __ldg(a.v1 + j), v2j = __ldg(a.v2 + j);
-                            double bv[kRPT];
-#pragma unroll
-                            for (int k = 0; k < kRPT; k++)
-                                bv[k] = fma(u2r[k], v2j, fma(u1r[k], v1j, av[k]));
-                            store_col<VEC>(a.Bout + j * a.ldb, R0, r1, warp, lane, bv);
-                            double acc = bv[0] * rv[0];
-#pragma unroll
-                            for (int k = 1; k < kRPT; k++) acc = fma(bv[k], rv[k], acc);
-                            sl[jj] = acc;
-                        } else {
-                            if (HAS_Q) {
-                                const double pj = __ldg(a.p + j);
-#pragma unroll
-                                for (int k = 0; k < kRPT; k++) qacc[k] = fma(av[k], pj, qacc[k]);
-                            }
-                            if (HAS_S) {
-                                double acc = av[0] * rv[0];
-#pragma unroll
-                                for (int k = 1; k < kRPT; k++) acc = fma(av[k], rv[k], acc);
-                                sl[jj] = acc;
-                            }
+                            if (MODE == PM_Q2) load_col<VEC>(a.B + j * a.ldb, R0, r1, warp, lane, bv[u]);
+                            if (HAS_Q) pj[u] = __ldg(a.p + j);
                         }
-                    } else if (HAS_S) {
-                        sl[jj] = 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        const int jj = jb + u;
+                        if (jj < nc) {
+                            const int64_t j = g0 + jj;
+                            if (MODE == PM_G1) {
+                                double b[kRPT];
+#pragma unroll
+                                for (int k = 0; k < kRPT; k++)
+                                    b[k] = fma(u2r[k], v2j[u], fma(u1r[k], v1j[u], av[u][k]));
+                                store_col<VEC>(a.Bout + j * a.ldb, R0, r1, warp, lane, b);
+                                double acc = b[0] * rv[0];
+#pragma unroll
+                                for (int k = 1; k < kRPT; k++) acc = fma(b[k], rv[k], acc);
+                                sl[jj] = acc;
+                            } else {
+                                if (HAS_Q) {
+#pragma unroll
+                                    for (int k = 0; k < kRPT; k++) qacc[k] = fma(av[u][k], pj[u], qacc[k]);
+                                }
+                                if (MODE == PM_Q2) {
+#pragma unroll
+                                    for (int k = 0; k < kRPT; k++) qacc2[k] = fma(bv[u][k], pj[u], qacc2[k]);
+                                }
+                                if (HAS_S) {
+                                    double acc = av[u][0] * rv[0];
+#pragma unroll
+                                    for (int k = 1; k < kRPT; k++) acc = fma(av[u][k], rv[k], acc);
+                                    sl[jj] = acc;
+                                }
+                            }
+                        } else if (HAS_S) {
+                            sl[jj] = 0.0;
+                        }
                     }
                 }
                 if (HAS_S) {
-                    const double cs = transpose_reduce32(sl, lane);
+                    const double cs = transpose_reduce16(sl, lane);
                     if (lane < nc) sw[warp * tcmax + (g0 - c0) + lane] += cs;
                 }
             }
@@ -267,40 +288,70 @@ __global__ void __launch_bounds__(kThreads, 1) panel_kernel(const PanelArgs a) {
     }
 }
 
-__global__ void combine_kernel(const CombineJob j0, const CombineJob j1, int njobs) {
-    const int64_t tot = j0.len + (njobs > 1 ? j1.len : 0);
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < tot;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const CombineJob& J = (g < j0.len) ? j0 : j1;
-        const int64_t i = (g < j0.len) ? g : g - j0.len;
-        double s1 = 0.0;
-        for (int k = 0; k < J.K1; k++) s1 += __ldg(J.P1 + k * J.ld1 + i);
-        double o = J.a1 * s1;
-        if (J.P2) {
-            double s2 = 0.0;
-            for (int k = 0; k < J.K2; k++) s2 += __ldg(J.P2 + k * J.ld2 + i);
-            o = fma(J.a2, s2, o);
+// Fixed-order combine of split partials.  A block handles 32 consecutive
+// outputs; warp w adds the partials k = w, w + 8, w + 16, ... of output
+// (block base + lane) with coalesced loads, then warp 0 adds the 8 warp
+// sums in warp order.  The order depends only on K, so results are
+// reproducible, and every load of a warp is one 256-byte segment.
+constexpr int kCombWarps = 8;
+
+__device__ __forceinline__ double strided_sum(const double* P, int64_t ld, int K, int w, int64_t i) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int k = w;
+    for (; k + 3 * kCombWarps < K; k += 4 * kCombWarps) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) acc[u] += __ldg(P + (int64_t)(k + u * kCombWarps) * ld + i);
+    }
+    for (int u = 0; k < K; k += kCombWarps, u++) acc[u] += __ldg(P + (int64_t)k * ld + i);
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
+__global__ void __launch_bounds__(kCombWarps * 32) combine_kernel(const CombineJob j0, const CombineJob j1, int njobs) {
+    __shared__ double red[2][kCombWarps][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t blocks0 = (j0.len + 31) / 32;
+    const int64_t nblk = blocks0 + (njobs > 1 ? (j1.len + 31) / 32 : 0);
+    for (int64_t bI = blockIdx.x; bI < nblk; bI += gridDim.x) {
+        const CombineJob& J = (bI < blocks0) ? j0 : j1;
+        const int64_t i = ((bI < blocks0) ? bI : bI - blocks0) * 32 + lane;
+        const bool ok = i < J.len;
+        red[0][w][lane] = ok ? strided_sum(J.P1, J.ld1, J.K1, w, i) : 0.0;
+        red[1][w][lane] = (ok && J.P2) ? strided_sum(J.P2, J.ld2, J.K2, w, i) : 0.0;
+        __syncthreads();
+        if (w == 0 && ok) {
+            double s1 = red[0][0][lane];
+#pragma unroll
+            for (int q = 1; q < kCombWarps; q++) s1 += red[0][q][lane];
+            double o = J.a1 * s1;
+            if (J.P2) {
+                double s2 = red[1][0][lane];
+#pragma unroll
+                for (int q = 1; q < kCombWarps; q++) s2 += red[1][q][lane];
+                o = fma(J.a2, s2, o);
+            }
+            if (J.v) o = fma(J.b, J.v[i], o);
+            J.out[i] = o;
         }
-        if (J.v) o = fma(J.b, J.v[i], o);
-        J.out[i] = o;
+        __syncthreads();
     }
 }
 
 template <int MODE>
 bto_status launch_mode(const PanelArgs& a, const PanelPlan& pl, bool vec2, cudaStream_t st) {
     const size_t smem = panel_smem_bytes(MODE, pl);
+    const int grid = (int)std::min<int64_t>(pl.ntiles, (int64_t)pl.grid * BlocksPerSM<MODE>::value);
     if (vec2) {
         auto k = panel_kernel<MODE, 2>;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return BTO_ERR_CUDA;
-        k<<<pl.grid, kThreads, smem, st>>>(a);
+        k<<<grid, kThreads, smem, st>>>(a);
     } else {
         auto k = panel_kernel<MODE, 1>;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return BTO_ERR_CUDA;
-        k<<<pl.grid, kThreads, smem, st>>>(a);
+        k<<<grid, kThreads, smem, st>>>(a);
     }
     return launch_status();
 }
@@ -315,17 +366,16 @@ PanelPlan panel_plan(int64_t m, int64_t n, int sms) {
     const int64_t G = sms;
     int64_t NC = ceil_div(n, ceil_div(n, G));           // balanced panels, about G of them
     if (ceil_div(n, NC) > kMaxPanel) NC = ceil_div(n, kMaxPanel);
-    int64_t NR = 1;
-    if (NC < G) {   // few columns: split the rows too, in blocks of >= 256 rows
-        NR = std::max<int64_t>(1, std::min<int64_t>(G / NC, ceil_div(m, 256)));
-    }
+    // About two tiles per SM (so the two-blocks-per-SM modes fill the
+    // machine): split the rows into blocks of >= 256 rows.
+    int64_t NR = std::max<int64_t>(1, std::min<int64_t>(ceil_div(2 * G, NC), ceil_div(m, 256)));
     // Row blocks start on multiples of 64: drop blocks that would be empty.
     while (NR > 1 && row_split_at(m, NR, 1) == 0) NR--;
     pl.NR = (int)NR;
     pl.NC = (int)NC;
     pl.TCmax = ceil_div(n, NC);
     pl.ntiles = NR * NC;
-    pl.grid = (int)std::min<int64_t>(pl.ntiles, G);
+    pl.grid = (int)G;   // times the blocks per SM of the mode, at launch
     return pl;
 }
 
@@ -352,14 +402,14 @@ bto_status launch_panel(int mode, const PanelArgs& a, const PanelPlan& pl, cudaS
 }
 
 bto_status launch_combine(const CombineJob* jobs, int njobs, cudaStream_t st) {
-    int64_t tot = 0;
-    for (int i = 0; i < njobs; i++) tot += jobs[i].len;
-    if (tot == 0) return BTO_OK;
+    int64_t blocks = 0;
+    for (int i = 0; i < njobs; i++) blocks += ceil_div(jobs[i].len, 32);
+    if (blocks == 0) return BTO_OK;
     DeviceInfo d;
     if (!device_info(&d)) return BTO_ERR_CUDA;
-    const int64_t blocks = std::min<int64_t>(ceil_div(tot, 256), (int64_t)d.sms * 8);
+    blocks = std::min<int64_t>(blocks, (int64_t)d.sms * 8);
     CombineJob j1 = njobs > 1 ? jobs[1] : jobs[0];
-    combine_kernel<<<(int)blocks, 256, 0, st>>>(jobs[0], j1, njobs);
+    combine_kernel<<<(int)blocks, kCombWarps * 32, 0, st>>>(jobs[0], j1, njobs);
     return launch_status();
 }
 

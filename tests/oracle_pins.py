@@ -272,5 +272,20 @@ def pin_dot2_bound(L):
     assert abs(Fraction(plain) - exact) > 1000 * Fraction(bound)
 
 
+def pin_mrhs_and_row_dot(L):
+    # Multi-RHS BICGK column by column against exact int64 products, and the
+    # sampled-row helper against the same exact sums.
+    m, n, k = 45, 38, 5
+    A = _imat(12, 0, m, n)
+    Ai = A.astype(np.int64)
+    P = np.asfortranarray(np.stack([_ints(12, 1 + c, n) for c in range(k)], axis=1))
+    R = np.asfortranarray(np.stack([_ints(12, 10 + c, m) for c in range(k)], axis=1))
+    Q, S = O.bicgk_mrhs(m, n, k, A, P, R, L=L)
+    assert np.array_equal(Q, (Ai @ P.astype(np.int64)).astype(float))
+    assert np.array_equal(S, (Ai.T @ R.astype(np.int64)).astype(float))
+    for i in (0, 17, m - 1):
+        assert O.row_dot(A[i], P[:, 0], L=L) == float(Ai[i] @ P[:, 0].astype(np.int64))
+
+
 PINS = [pin_golden, pin_integer_exact, pin_closed_forms, pin_identities,
-        pin_vector_special, pin_ieee_and_empty, pin_dot2_bound]
+        pin_vector_special, pin_ieee_and_empty, pin_dot2_bound, pin_mrhs_and_row_dot]

@@ -37,6 +37,9 @@ MUTANTS = [
     ("vadd_wrong_operand", "x[i] = (w[i] + y[i]) + z[i];", "x[i] = (w[i] + y[i]) + y[i];"),
     ("dot2_dropped_error", "s = s + (q + r);", "s = s + q;"),
     ("dot2_no_twoproduct", "*y = fma(a, b, -p);", "*y = 0.0;"),
+    ("mrhs_wrong_column", "oracle_bicgk(m, n, A, lda, P + (size_t)c * (size_t)ldp, R + (size_t)c * (size_t)ldr,",
+     "oracle_bicgk(m, n, A, lda, P, R + (size_t)c * (size_t)ldr,"),
+    ("row_dot_sign", "acc += row[j] * p[j];", "acc -= row[j] * p[j];"),
 ]
 
 

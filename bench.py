@@ -363,6 +363,92 @@ def run_reference(args):
     }))
 
 
+def precision_form(torch, bto, hbm, steps, n=32768):
+    """The reduced-precision storage form at n = 32768 (A in BF16 or FP32):
+    time per call (CUDA events), effective bandwidth over its compulsory bytes,
+    and sampled normwise errors computed with numpy in FP64, against the
+    stored values and against the original FP64 data."""
+    import synth
+    out = {}
+    m = n
+    rows = np.linspace(0, m - 1, 16).astype(np.int64)
+    f32 = dict(dtype=torch.float32, device="cuda")
+    pv = synth.vector(6, 1, n); rv = synth.vector(6, 2, m)
+    p32, r32 = synth.to_f32(pv), synth.to_f32(rv)
+    dp, dr = torch.from_numpy(p32).cuda(), torch.from_numpy(r32).cuda()
+    ids = synth.GEMVER_IDS
+    gv = {k: synth.vector(6, ids[k], n) for k in ("u1", "v1", "u2", "v2", "y", "z")}
+    g32 = {k: synth.to_f32(v) for k, v in gv.items()}
+    dg = {k: torch.from_numpy(v).cuda() for k, v in g32.items()}
+    st = torch.cuda.current_stream()
+
+    def deq(a64, t):
+        return synth.to_f32(a64).astype(np.float64) if t == "f32" else synth.bf16_bits_to_f64(synth.to_bf16_bits(a64))
+
+    def rel(a, b):
+        a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    for t, at, es in (("bf16", 2, 2), ("f32", 1, 4)):
+        for variant in ("plain", "colscaled"):
+            cs = synth.colscale(6, n) if variant == "colscaled" else None
+            dcs = torch.from_numpy(cs).cuda() if cs is not None else None
+            tdt = torch.float32 if t == "f32" else torch.int16
+            A = torch.empty(m * n, dtype=tdt, device="cuda")
+            (bto.bto_fill_f32 if t == "f32" else bto.bto_fill_bf16)(6, 0, 0, m, n, dcs, A, m, None)
+            q, s_ = torch.empty(m, **f32), torch.empty(n, **f32)
+            wb = bto.bto_workspace_bytes("bicgk", 0, m, n, at)
+            wsb = torch.empty(wb, dtype=torch.uint8, device="cuda")
+            res = {}
+            for _ in range(3):
+                bto.bto_bicgk_ex(m, n, at, A, m, dp, dr, q, s_, wsb, wb, None)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(); e0.record(st)
+            for _ in range(steps):
+                bto.bto_bicgk_ex(m, n, at, A, m, dp, dr, q, s_, wsb, wb, None)
+            e1.record(st); torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            byts = es * m * n + 4 * (2 * m + 2 * n)
+            R64 = synth.matrix_rows(6, 0, m, n, rows, scale=cs)
+            C64 = synth.matrix_cols(6, 0, m, n, rows, scale=cs)
+            qh, sh = q.cpu().numpy()[rows], s_.cpu().numpy()[rows]
+            res["bicgk"] = {"ms": round(ms, 4), "gbs": round(byts / ms / 1e6, 1),
+                            "hbm_frac": round(byts / ms / 1e6 / hbm, 3),
+                            "err_vs_stored": {"q": rel(qh, deq(R64, t) @ p32.astype(np.float64)),
+                                              "s": rel(sh, deq(C64, t).T @ r32.astype(np.float64))},
+                            "err_vs_fp64_data": {"q": rel(qh, R64 @ pv), "s": rel(sh, C64.T @ rv)}}
+            del wsb
+            if variant == "plain":
+                B = torch.empty(m * n, dtype=tdt, device="cuda")
+                x, w = torch.empty(n, **f32), torch.empty(m, **f32)
+                wb = bto.bto_workspace_bytes("gemver", 0, m, n, at)
+                wsb = torch.empty(wb, dtype=torch.uint8, device="cuda")
+                args = [dg[k] for k in ("u1", "v1", "u2", "v2", "y", "z")]
+                for _ in range(3):
+                    bto.bto_gemver_ex(m, n, 1.5, 1.2, at, A, m, *args, B, m, x, w, wsb, wb, None)
+                torch.cuda.synchronize(); e0.record(st)
+                for _ in range(steps):
+                    bto.bto_gemver_ex(m, n, 1.5, 1.2, at, A, m, *args, B, m, x, w, wsb, wb, None)
+                e1.record(st); torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / steps
+                byts = 3 * es * m * n + 4 * (4 * m + 4 * n)
+                Bcols = B.view(n, m)[torch.from_numpy(rows).cuda()].cpu().numpy()
+                Bc = Bcols.astype(np.float64) if t == "f32" else synth.bf16_bits_to_f64(Bcols.view(np.uint16))
+                xh = x.cpu().numpy()[rows]
+                xref = 1.2 * (Bc @ g32["y"].astype(np.float64)) + g32["z"][rows].astype(np.float64)
+                Bx64 = (C64 + np.outer(gv["u1"], gv["v1"][rows]) + np.outer(gv["u2"], gv["v2"][rows]))
+                x64 = 1.2 * (Bx64.T @ gv["y"]) + gv["z"][rows]
+                res["gemver"] = {"ms": round(ms, 4), "gbs": round(byts / ms / 1e6, 1),
+                                 "hbm_frac": round(byts / ms / 1e6 / hbm, 3),
+                                 "err_vs_stored": {"x": rel(xh, xref)},
+                                 "err_vs_fp64_data": {"B": rel(Bc, Bx64.T), "x": rel(xh, x64)}}
+                del B, wsb
+            del A
+            torch.cuda.empty_cache()
+            out["%s_%s" % (t, variant)] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,7 +458,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--only", default=None, help="comma-separated kernels (profiling runs)")
+    ap.add_argument("--precision-only", type=int, default=0,
+                    help="profiling runs: only the reduced-precision form at this n")
     ap.add_argument("--n", type=int, default=N_MAT, help="matrix size (profiling runs)")
     ap.add_argument("--nvec", type=int, default=N_VEC, help="vector length (profiling runs)")
     args = ap.parse_args()
@@ -381,6 +470,14 @@ def main():
         KERNELS = [k for k in KERNELS if k in args.only.split(",")]
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.precision_only:
+        import torch
+        from paper_1205_1098_gb300 import build
+        build.build()
+        import paper_1205_1098_gb300 as bto
+        hbm, _, _ = load_peaks()
+        print(json.dumps({"precision_form": precision_form(torch, bto, hbm, args.steps, n=args.precision_only)}))
         return
 
     import torch
@@ -461,6 +558,15 @@ def main():
         e2e = {"value": round(world * step_bytes / (ems * 1e-3) / 1e9, 2), "unit": "GB/s",
                "ms_per_step": round(ems, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    prec = None
+    if not args.no_precision and not args.only:
+        try:
+            del suite
+        except NameError:
+            pass
+        torch.cuda.empty_cache()
+        prec = precision_form(torch, bto, hbm, max(3, args.steps // 3))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ns, nv = 8192, 1 << 25
@@ -483,6 +589,7 @@ def main():
                        "l2": "every input is larger than L2 (2 GiB matrices, 512 MiB vectors); no flush"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "kernels": per, "unfused": unfused,
+            "precision_form_n32768": prec,
             "peaks": {"hbm_gbs": hbm, "hbm_source": peak_src, "fp64_tflops": round(fp64_peak, 4)},
         }))
     if dist:

@@ -168,6 +168,33 @@ bto_status bto_waxpby(int64_t n, double alpha, const double *x, double beta,
 bto_status bto_vadd(int64_t n, const double *w, const double *y, const double *z,
                     double *x, bto_stream_t stream);
 
+/* ------------------------------------------- reduced-precision storage form
+ * BICGK and GEMVER (Table I) with the matrix stored in FP32 or BF16 to cut
+ * the bytes of this bandwidth-bound path (the paper's kernels are FP64; this
+ * form has no counterpart there).  a_type is BTO_F32 or BTO_BF16 (raw BF16
+ * bits, as uint16).  Vectors and outputs are FP32.  Arithmetic is FP32 with
+ * compensated accumulation: products are summed in short FP32 FMA chains
+ * (16 columns for A p, 8 rows for A^T r) that are folded into TwoSum
+ * (hi, lo) pairs; per-tile results are combined in FP64 in a fixed order and
+ * rounded once to FP32.  Against an FP64 evaluation on the same (stored)
+ * values the normwise relative error is of order 1e-7.
+ * The workspace is bto_workspace_bytes(op, BTO_FORM_FUSED, m, n, a_type).
+ * Alignment: A (and B) must be aligned to their element size. */
+
+/* q <- A p ; s <- A^T r, with A m x n (lda) of type a_type. */
+bto_status bto_bicgk_ex(int64_t m, int64_t n, int a_type, const void *A, int64_t lda,
+                        const float *p, const float *r, float *q, float *s,
+                        void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* B <- A + u1 v1^T + u2 v2^T, formed in FP32 and rounded to a_type (round to
+ * nearest even); x <- beta B^T y + z ; w <- alpha B x, both computed from the
+ * stored (rounded) B.  B == A with ldb == lda and x == z are allowed. */
+bto_status bto_gemver_ex(int64_t m, int64_t n, float alpha, float beta, int a_type,
+                         const void *A, int64_t lda, const float *u1, const float *v1,
+                         const float *u2, const float *v2, const float *y, const float *z,
+                         void *B, int64_t ldb, float *x, float *w,
+                         void *ws, size_t ws_bytes, bto_stream_t stream);
+
 /* BICGK without a workspace argument (the paper has no counterpart; this is
  * a convenience of this library).  Some callers cannot call cudaMalloc: a
  * plugin whose host application owns all device memory through its own

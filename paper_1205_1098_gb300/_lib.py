@@ -15,7 +15,7 @@ _c_i64, _c_u64, _c_f64, _c_int = ctypes.c_int64, ctypes.c_uint64, ctypes.c_doubl
 _c_ptr, _c_size = ctypes.c_void_p, ctypes.c_size_t
 
 # Argument kinds: i = int64, u = uint64, d = double, p = pointer, z = size_t,
-# s = stream, k = int
+# s = stream, k = int, f = float
 SIGNATURES = {
     "bto_bicgk": "iipipppppzs",
     "bto_atax": "iidpipppzs",
@@ -40,8 +40,11 @@ SIGNATURES = {
     "bto_fill_bf16": "uukiippis",
     "bto_debug_atax_stall": "iidpipppziks",
     "bto_bicgk_noalloc": "iipipppps",
+    "bto_bicgk_ex": "iikpipppppzs",
+    "bto_gemver_ex": "iiffkpipppppppipppzs",
 }
-_KIND = {"i": _c_i64, "u": _c_u64, "d": _c_f64, "p": _c_ptr, "z": _c_size, "s": _c_ptr, "k": _c_int}
+_KIND = {"i": _c_i64, "u": _c_u64, "d": _c_f64, "f": ctypes.c_float, "p": _c_ptr, "z": _c_size,
+         "s": _c_ptr, "k": _c_int}
 
 BTO_OK, BTO_ERR_INVALID_VALUE, BTO_ERR_UNSUPPORTED, BTO_ERR_WORKSPACE = 0, 1, 2, 3
 BTO_ERR_CUDA, BTO_ERR_TIMEOUT, BTO_ERR_BUDGET = 4, 5, 6
@@ -114,7 +117,7 @@ def _conv(kind, v):
         return _ptr(v)
     if kind == "s":
         return _stream(v)
-    if kind == "d":
+    if kind in ("d", "f"):
         return float(v)
     return int(v)
 

@@ -85,6 +85,41 @@ struct CombineJob {
 };
 bto_status launch_combine(const CombineJob* jobs, int njobs, cudaStream_t st);
 
+// ------------------------------------------------------------ reduced-precision form
+// Tiles of the FP32/BF16 storage form: column panels are whole multiples of
+// `cu` columns (the TMA box width: 16 for FP32, 32 for BF16) and row blocks
+// whole multiples of 256 rows (the box height), so no panel's copies spill
+// into a neighbour's columns.
+__host__ __device__ inline int64_t lp_col_at(int64_t n, int64_t NC, int64_t cb, int64_t cu) {
+    const int64_t units = (n + cu - 1) / cu, c = (units * cb / NC) * cu;
+    return c < n ? c : n;
+}
+__host__ __device__ inline int64_t lp_row_at(int64_t m, int64_t NR, int64_t rb) {
+    const int64_t units = (m + 255) / 256, r = (units * rb / NR) * 256;
+    return r < m ? r : m;
+}
+inline int64_t lp_col_unit(int a_type) { return a_type == BTO_BF16 ? 32 : 16; }
+PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type);
+
+enum LpMode { LP_QS = 0, LP_Q = 1, LP_G1 = 2 };
+
+struct LpArgs {
+    int64_t m, n;
+    const void* A; int64_t lda;
+    void* Bout; int64_t ldb;
+    const float* p;            // column-indexed vector (LP_QS, LP_Q)
+    const float* r;            // row-indexed vector (LP_QS; LP_G1: y)
+    const float* u1; const float* v1; const float* u2; const float* v2;
+    double* qpart; double* spart;
+    int64_t ldq, lds, tcmax, cu;   // cu: panel column unit
+    int NR, NC; int64_t ntiles; int reverse;
+    int* status;               // device status word (timeouts of bounded waits)
+};
+// Launches the TMA-fed sweep; returns false (launching nothing) when the
+// layout does not meet the tensor-map rules, so the caller uses the
+// load-instruction sweep instead.
+bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, cudaStream_t st, bto_status* out);
+
 // ------------------------------------------------------------ ATAX wavefront
 // Rows are cut into bands of TB rows; block c of a cooperative grid of G
 // blocks owns a fixed slice of columns (so it owns those entries of y).

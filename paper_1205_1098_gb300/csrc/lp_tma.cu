@@ -1,0 +1,388 @@
+// TMA-fed sweep of the reduced-precision storage form (BICGK and both GEMVER
+// passes with A or B in FP32/BF16).
+//
+// Each stage is a 256-row x 16-column box of the matrix, copied by the tensor
+// memory accelerator (cp.async.bulk.tensor) into a ring of shared-memory
+// buffers.  One producer warp issues the copies; eight consumer warps take
+// two columns of the stage each, with lane l holding 8 rows (one 16-byte
+// shared-memory read per column for BF16, two for FP32).  Buffers are handed
+// back and forth with mbarriers (a "full" barrier completed by the copy's
+// transaction bytes, an "empty" barrier that the eight consumer warps arrive
+// on), so 6-8 stages of the matrix are in flight per SM without holding any
+// registers.  The arithmetic is that of the load-instruction sweep:
+//   A p   : FP32 FMA chains over 16 columns per row, folded into TwoSum pairs;
+//   A^T r : 8-row FMA chains per column, a 16-column transposing butterfly
+//           across the warp, folded into TwoSum pairs in shared memory;
+// tiles end in (hi, lo) FP32 pairs that a fixed-order FP64 combine adds.
+// Every mbarrier wait is bounded by %globaltimer (2 s) and by a shared abort
+// flag: on expiry the block records BTO_ERR_TIMEOUT in the status word,
+// skips the remaining waits (so every warp still reaches every named
+// barrier), and the producer waits, again with a bound, for the copies it
+// issued before the block exits.
+#include "check.cuh"
+#include "lp_math.cuh"
+#include "tma.cuh"
+#include <mutex>
+
+namespace bto {
+namespace {
+
+using namespace lp;
+
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumers = kConsumerWarps * 32;
+constexpr int kThreadsT = kConsumers + 32;       // + one producer warp
+constexpr int kBoxR = 256;                        // rows per stage
+constexpr int kRPT = 8;                           // rows per lane
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+// A stage is one 16 KB box: 256 rows x 32 columns of BF16 or 256 x 16 of
+// FP32 (the copy engine's cost grows with the number of boxes, so boxes are
+// as large as the panel unit allows); each consumer warp takes CPW = BoxC / 8
+// of its columns.  Twelve stages keep 192 KB of the matrix in flight per SM.
+template <typename TA> struct Cfg {
+    static constexpr int BoxC = sizeof(TA) == 2 ? 32 : 16;
+    static constexpr int CPW = BoxC / kConsumerWarps;
+    static constexpr int GroupStages = 16 / CPW;        // stages per 16-column butterfly group
+    static constexpr int S = 12;
+};
+
+template <typename TA>
+constexpr size_t stage_bytes() { return (size_t)kBoxR * Cfg<TA>::BoxC * sizeof(TA); }
+
+template <typename TA>
+size_t tma_smem(int64_t tcmax) {
+    return Cfg<TA>::S * stage_bytes<TA>()                   // ring
+           + 2 * Cfg<TA>::S * sizeof(uint64_t)               // full, empty
+           + 2 * kConsumerWarps * kBoxR * sizeof(float)      // q reduction (hi, lo)
+           + 5 * (size_t)tcmax * sizeof(float) + 128;        // s (hi, lo), p, v1, v2 of the tile
+}
+
+template <typename TA>
+constexpr int box_cols() { return Cfg<TA>::BoxC; }
+
+// Row (within the stage) of lane's k-th element: V = 16 / sizeof(TA) rows
+// per 16-byte read.
+template <int V>
+__device__ __forceinline__ int trow(int lane, int k) { return (k / V) * (32 * V) + lane * V + (k % V); }
+
+template <typename TA, int MODE>
+__global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                              const LpArgs a) {
+    constexpr int V = 16 / sizeof(TA);
+    constexpr int S = Cfg<TA>::S;
+    constexpr int kBoxC = Cfg<TA>::BoxC;
+    constexpr int CPW = Cfg<TA>::CPW;
+    constexpr bool HAS_Q = (MODE == LP_QS || MODE == LP_Q);
+    constexpr bool HAS_S = (MODE == LP_QS || MODE == LP_G1);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    TA* ring = reinterpret_cast<TA*>(smem);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes<TA>());
+    uint64_t* empty = full + S;
+    float* qred = reinterpret_cast<float*>(empty + S);          // [2][8][256]
+    float* shi = qred + 2 * kConsumerWarps * kBoxR;               // [tcmax]
+    float* slo = shi + a.tcmax;
+    float* sp = slo + a.tcmax;                                    // p, v1, v2 of the tile
+    float* sv1 = sp + a.tcmax;
+    float* sv2 = sv1 + a.tcmax;
+    __shared__ int s_abort_;
+    volatile int* s_abort_p = &s_abort_;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        *s_abort_p = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == kConsumerWarps) {
+        // ---------------- producer
+        if (lane == 0) {
+            long long g = 0;
+            for (int64_t t = blockIdx.x; t < a.ntiles && !*s_abort_p; t += gridDim.x) {
+                const int64_t tt = a.reverse ? (a.ntiles - 1 - t) : t;
+                const int64_t cb = tt / a.NR, rb = tt % a.NR;
+                const int64_t c0 = lp_col_at(a.n, a.NC, cb, kBoxC), c1 = lp_col_at(a.n, a.NC, cb + 1, kBoxC);
+                const int64_t r0 = lp_row_at(a.m, a.NR, rb), r1 = lp_row_at(a.m, a.NR, rb + 1);
+                for (int64_t R0 = r0; R0 < r1 && !*s_abort_p; R0 += kBoxR) {
+                    for (int64_t cs = c0; cs < c1; cs += kBoxC, g++) {
+                        const int slot = (int)(g % S);
+                        if (g >= S && !mbar_wait_bounded(&empty[slot], (uint32_t)(((g / S) - 1) & 1), kWaitNs, s_abort_p)) {
+                            atomicExch(a.status, (int)BTO_ERR_TIMEOUT);
+                            *s_abort_p = 1;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full[slot], (uint32_t)stage_bytes<TA>());
+                        tma_load_2d(ring + (size_t)slot * kBoxR * kBoxC, &tmA, (int)R0, (int)cs, &full[slot]);
+                    }
+                }
+            }
+            if (*s_abort_p) {
+                // Wait (bounded) for the copies this thread issued before leaving.
+                const long long first = g > S ? g - S : 0;
+                for (long long h = first; h < g; h++) {
+                    const int slot = (int)(h % S);
+                    const unsigned long long t0 = global_ns();
+                    while (!mbar_try_wait(&full[slot], (uint32_t)((h / S) & 1)) && global_ns() - t0 < kWaitNs) {
+                    }
+                }
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    TA* Bout = static_cast<TA*>(a.Bout);
+    long long g = 0;
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const int64_t tt = a.reverse ? (a.ntiles - 1 - t) : t;
+        const int64_t cb = tt / a.NR, rb = tt % a.NR;
+        const int64_t c0 = lp_col_at(a.n, a.NC, cb, kBoxC), c1 = lp_col_at(a.n, a.NC, cb + 1, kBoxC);
+        const int64_t r0 = lp_row_at(a.m, a.NR, rb), r1 = lp_row_at(a.m, a.NR, rb + 1);
+        const int ncols = (int)(c1 - c0);
+        for (int k = threadIdx.x; k < ncols; k += kConsumers) {
+            shi[k] = 0.0f; slo[k] = 0.0f;
+            if (HAS_Q) sp[k] = __ldg(a.p + c0 + k);
+            if (MODE == LP_G1) { sv1[k] = __ldg(a.v1 + c0 + k); sv2[k] = __ldg(a.v2 + c0 + k); }
+        }
+        named_bar(1, kConsumers);
+        for (int64_t R0 = r0; R0 < r1; R0 += kBoxR) {
+            float rv[kRPT], u1r[kRPT], u2r[kRPT], qhi[kRPT], qlo[kRPT], qt[kRPT], sl[16];
+#pragma unroll
+            for (int k = 0; k < kRPT; k++) {
+                const int64_t i = R0 + trow<V>(lane, k);
+                rv[k] = (HAS_S && i < r1) ? __ldg(a.r + i) : 0.0f;
+                u1r[k] = (MODE == LP_G1 && i < r1) ? __ldg(a.u1 + i) : 0.0f;
+                u2r[k] = (MODE == LP_G1 && i < r1) ? __ldg(a.u2 + i) : 0.0f;
+                qhi[k] = 0.0f; qlo[k] = 0.0f; qt[k] = 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < 16; k++) sl[k] = 0.0f;
+            int gs = 0;                 // stage within the butterfly group
+            int64_t gbase = c0;         // first column of the group
+            for (int64_t cs = c0; cs < c1; cs += kBoxC, g++) {
+                const int slot = (int)(g % S);
+                bool have = true;
+                if (!*s_abort_p && !mbar_wait_bounded(&full[slot], (uint32_t)((g / S) & 1), kWaitNs, s_abort_p)) {
+                    if (lane == 0) atomicExch(a.status, (int)BTO_ERR_TIMEOUT);
+                    *s_abort_p = 1;
+                }
+                if (*s_abort_p) have = false;
+                const TA* buf = ring + (size_t)slot * kBoxR * kBoxC;
+#pragma unroll
+                for (int cc = 0; cc < CPW; cc++) {
+                    const int c = CPW * warp + cc;
+                    const int64_t col = cs + c;
+                    if (have && col < c1) {
+                        float av[kRPT];
+#pragma unroll
+                        for (int h = 0; h < kRPT / V; h++) {
+                            const uint4 raw = *reinterpret_cast<const uint4*>(buf + c * kBoxR + h * 32 * V + lane * V);
+                            const TA* e = reinterpret_cast<const TA*>(&raw);
+#pragma unroll
+                            for (int q = 0; q < V; q++) av[h * V + q] = to_f<TA>(e[q]);
+                        }
+                        if (MODE == LP_G1) {
+                            const float v1j = sv1[col - c0], v2j = sv2[col - c0];
+                            TA bq[kRPT];
+                            float bf[kRPT];
+#pragma unroll
+                            for (int k = 0; k < kRPT; k++) {
+                                bq[k] = from_f<TA>(fmaf(u2r[k], v2j, fmaf(u1r[k], v1j, av[k])));
+                                bf[k] = to_f<TA>(bq[k]);
+                            }
+                            TA* bcol = Bout + col * a.ldb;
+#pragma unroll
+                            for (int h = 0; h < kRPT / V; h++) {
+                                const int64_t i = R0 + h * 32 * V + lane * V;
+                                if (i + V <= r1) {   // B and ldb are 16-byte aligned on this path
+                                    uint4 raw;
+                                    TA* e = reinterpret_cast<TA*>(&raw);
+#pragma unroll
+                                    for (int q = 0; q < V; q++) e[q] = bq[h * V + q];
+                                    *reinterpret_cast<uint4*>(bcol + i) = raw;
+                                } else {
+#pragma unroll
+                                    for (int q = 0; q < V; q++)
+                                        if (i + q < r1) bcol[i + q] = bq[h * V + q];
+                                }
+                            }
+                            float acc = bf[0] * rv[0];
+#pragma unroll
+                            for (int k = 1; k < kRPT; k++) acc = fmaf(bf[k], rv[k], acc);
+                            sl[CPW * gs + cc] = acc;
+                        } else {
+                            if (HAS_Q) {
+                                const float pj = sp[col - c0];
+#pragma unroll
+                                for (int k = 0; k < kRPT; k++) qt[k] = fmaf(av[k], pj, qt[k]);
+                            }
+                            if (HAS_S) {
+                                float acc = av[0] * rv[0];
+#pragma unroll
+                                for (int k = 1; k < kRPT; k++) acc = fmaf(av[k], rv[k], acc);
+                                sl[CPW * gs + cc] = acc;
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0 && have) mbar_arrive(&empty[slot]);
+                gs++;
+                if (gs == Cfg<TA>::GroupStages || cs + kBoxC >= c1) {
+                    if (HAS_Q) {
+#pragma unroll
+                        for (int k = 0; k < kRPT; k++) {
+                            float s, e;
+                            two_sum(qhi[k], qt[k], s, e);
+                            qhi[k] = s; qlo[k] += e; qt[k] = 0.0f;
+                        }
+                    }
+                    if (HAS_S) {
+                        const float v = butterfly16(sl, lane);
+                        if (lane < 16) {
+                            const int64_t col = gbase + (int64_t)(lane / CPW) * kBoxC + CPW * warp + (lane % CPW);
+                            if (col < c1) {
+                                float s, e;
+                                two_sum(shi[col - c0], v, s, e);
+                                shi[col - c0] = s;
+                                slo[col - c0] += e;
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < 16; k++) sl[k] = 0.0f;
+                    }
+                    gs = 0;
+                    gbase = cs + kBoxC;
+                }
+            }
+            if (HAS_Q) {
+                // Add the eight warps' row sums (each warp saw other columns) in FP64.
+#pragma unroll
+                for (int k = 0; k < kRPT; k++) {
+                    qred[warp * kBoxR + trow<V>(lane, k)] = qhi[k];
+                    qred[(kConsumerWarps + warp) * kBoxR + trow<V>(lane, k)] = qlo[k];
+                }
+                named_bar(1, kConsumers);
+                const int64_t i = R0 + threadIdx.x;
+                if (i < r1) {
+                    // Compensated FP32: TwoSum over the warps' hi parts, lo parts added;
+                    // the pair goes to the combine, which converts and adds in FP64.
+                    float hs = qred[threadIdx.x], ls = qred[kConsumerWarps * kBoxR + threadIdx.x];
+#pragma unroll
+                    for (int w = 1; w < kConsumerWarps; w++) {
+                        float s2, e2;
+                        two_sum(hs, qred[w * kBoxR + threadIdx.x], s2, e2);
+                        hs = s2;
+                        ls += e2 + qred[(kConsumerWarps + w) * kBoxR + threadIdx.x];
+                    }
+                    reinterpret_cast<float2*>(a.qpart)[cb * a.ldq + i] = make_float2(hs, ls);
+                }
+                named_bar(1, kConsumers);
+            }
+        }
+        named_bar(1, kConsumers);
+        if (HAS_S)
+            for (int k = threadIdx.x; k < ncols; k += kConsumers)
+                reinterpret_cast<float2*>(a.spart)[rb * a.lds + c0 + k] = make_float2(shi[k], slo[k]);
+        named_bar(1, kConsumers);
+    }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+    static std::once_flag once;
+    static EncodeFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+template <typename TA, int MODE>
+bto_status launch_t(const CUtensorMap& map, const LpArgs& a, int grid, cudaStream_t st) {
+    auto k = lp_tma_kernel<TA, MODE>;
+    const size_t smem = tma_smem<TA>(a.tcmax);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return BTO_ERR_CUDA;
+    k<<<grid, kThreadsT, smem, st>>>(map, a);
+    return launch_status();
+}
+
+}  // namespace
+
+bool encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, size_t esize, const void* base,
+                    int64_t rows, int64_t cols, int64_t ld, uint32_t box_rows, uint32_t box_cols) {
+    EncodeFn fn = encode_fn();
+    if (!fn || rows <= 0 || cols <= 0) return false;
+    if (!aligned16(base) || ((size_t)ld * esize) % 16 != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
+    const cuuint32_t box[2] = {box_rows, box_cols};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type) {
+    PanelPlan pl;
+    pl.ldq = round_up(m > 0 ? m : 1, 32);
+    pl.lds = round_up(n > 0 ? n : 1, 32);
+    if (m <= 0 || n <= 0) return pl;
+    const int64_t G = sms, cu = lp_col_unit(a_type);
+    const int64_t cunits = ceil_div(n, cu), runits = ceil_div(m, kBoxR);
+    const int64_t NC = std::min<int64_t>(G, cunits);
+    const int64_t NR = std::max<int64_t>(1, std::min<int64_t>(G / NC, runits));
+    pl.NC = (int)NC;
+    pl.NR = (int)NR;
+    pl.TCmax = ceil_div(cunits, NC) * cu;
+    pl.ntiles = NR * NC;
+    pl.grid = (int)G;
+    return pl;
+}
+
+bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, cudaStream_t st, bto_status* out) {
+    const size_t es = a_type == BTO_F32 ? 4 : 2;
+    const void* base = (mode == LP_Q || mode == LP_QS || mode == LP_G1) ? a.A : nullptr;
+    CUtensorMap map;
+    const CUtensorMapDataType dt = a_type == BTO_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    // In place (B == A) the B stores of one stage must not overwrite elements
+    // a later stage still has to copy: each element is copied once, before it
+    // is stored, so this holds; the copies of a stage complete before its
+    // consumers run.
+    if (a.m > INT32_MAX || a.n > INT32_MAX) return false;
+    // The B stores are 16-byte vector stores: B and its columns must be aligned.
+    if (mode == LP_G1 && !(aligned16(a.Bout) && ((size_t)a.ldb * es) % 16 == 0)) return false;
+    const uint32_t bc = a_type == BTO_F32 ? box_cols<float>() : box_cols<__nv_bfloat16>();
+    if (!encode_tmap_2d(&map, dt, es, base, a.m, a.n, a.lda, kBoxR, bc)) return false;
+    if (a_type == BTO_F32) {
+        switch (mode) {
+            case LP_QS: *out = launch_t<float, LP_QS>(map, a, grid, st); return true;
+            case LP_Q: *out = launch_t<float, LP_Q>(map, a, grid, st); return true;
+            case LP_G1: *out = launch_t<float, LP_G1>(map, a, grid, st); return true;
+        }
+    } else {
+        switch (mode) {
+            case LP_QS: *out = launch_t<__nv_bfloat16, LP_QS>(map, a, grid, st); return true;
+            case LP_Q: *out = launch_t<__nv_bfloat16, LP_Q>(map, a, grid, st); return true;
+            case LP_G1: *out = launch_t<__nv_bfloat16, LP_G1>(map, a, grid, st); return true;
+        }
+    }
+    return false;
+}
+
+}  // namespace bto

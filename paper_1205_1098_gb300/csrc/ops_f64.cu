@@ -16,10 +16,14 @@ size_t region(size_t& cur, size_t bytes) {
 
 bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type, const DeviceInfo& d,
                      WsLayout* out) {
-    if (a_type != BTO_F64) return BTO_ERR_UNSUPPORTED;
+    // Reduced-precision storage exists for the fused BICGK and GEMVER forms
+    // (bto_bicgk_ex, bto_gemver_ex); their partials are FP64 like the FP64 form's.
+    if (a_type != BTO_F64 &&
+        !(form == BTO_FORM_FUSED && (op == BTO_OP_BICGK || op == BTO_OP_GEMVER)))
+        return BTO_ERR_UNSUPPORTED;
     WsLayout L;
     size_t cur = WS_HEADER;
-    const PanelPlan pl = panel_plan(m, n, d.sms);
+    const PanelPlan pl = a_type == BTO_F64 ? panel_plan(m, n, d.sms) : lp_plan(m, n, d.sms, a_type);
     const size_t qp = (size_t)pl.NC * pl.ldq * sizeof(double);
     const size_t sp = (size_t)pl.NR * pl.lds * sizeof(double);
     switch (op) {

@@ -30,6 +30,8 @@ def _kind(a):
         return "i"
     if "double" in a:
         return "d"
+    if "float" in a:
+        return "f"
     if "bto_stream_t" in a:
         return "s"
     if "void" == a.strip():

@@ -449,6 +449,77 @@ def precision_form(torch, bto, hbm, steps, n=32768):
     return out
 
 
+def batched_form(torch, bto, hbm, steps, count=4096, seed=3):
+    """Config 4: `count` BICGK/GEMVER instances (50/50 by a draw), m, n
+    log-uniform in [32, 2048], FP32, one persistent launch, replayed from a
+    CUDA graph; the panel width is chosen by the measured-cost tuner."""
+    import synth
+    from paper_1205_1098_gb300 import autotune
+    u = synth.vector(seed, 500, 2 * count) * 0.5 + 0.5
+    sizes = np.round(np.exp(np.log(32) + u * (np.log(2048) - np.log(32)))).astype(np.int64)
+    ops = np.where(synth.vector(seed, 501, count) < 0, 0, 2)
+    descs = (bto.BatchDesc * count)()
+    keep = []
+    f32 = dict(dtype=torch.float32, device="cuda")
+    nbytes = 0
+    for i in range(count):
+        m, n = int(sizes[2 * i]), int(sizes[2 * i + 1])
+        op = int(ops[i])
+        d = descs[i]
+        d.op, d.m, d.n, d.lda, d.ldb, d.alpha, d.beta = op, m, n, m, m, 1.5, 1.25
+        A = torch.empty(m * n, **f32)
+        bto.bto_fill_f32(seed, 1000 * i, 0, m, n, 0, A, m, None)
+        keep.append(A)
+        d.A = A.data_ptr()
+        lens = [n, m] if op == 0 else [m, n, m, n, m, n]
+        for k, ln in enumerate(lens):
+            t = torch.empty(ln, **f32)
+            bto.bto_fill_f32(seed, 1000 * i + 1 + k, 0, ln, 1, 0, t, ln, None)
+            keep.append(t)
+            d.in_[k] = t.data_ptr()
+        for k, ln in enumerate([m, n] if op == 0 else [n, m]):
+            t = torch.empty(ln, **f32)
+            keep.append(t)
+            d.out[k] = t.data_ptr()
+        if op == 2:
+            B = torch.empty(m * n, **f32)
+            keep.append(B)
+            d.B = B.data_ptr()
+            nbytes += 3 * 4 * m * n + 4 * (4 * m + 4 * n)
+        else:
+            nbytes += 4 * m * n + 4 * (2 * m + 2 * n)
+    torch.cuda.synchronize()
+    best, cand_ms = autotune.tune(descs, use_cache=False)
+    nb = bto.bto_batch_workspace_bytes(descs, best)
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    bto.bto_batch_prepare(count, descs, best, ws, nb, None)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bto.bto_batch_run(ws, nb, s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bto.bto_batch_run(ws, nb, torch.cuda.current_stream())
+    for _ in range(3):
+        g.replay()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(steps):
+        g.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    status = bto.bto_device_status(ws)
+    return {"instances": count, "ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
+            "hbm_frac": round(nbytes / ms / 1e6 / hbm, 3), "compulsory_bytes": nbytes,
+            "tile_cols": best, "tuner_ms": {str(k): round(v, 4) for k, v in cand_ms.items()},
+            "status": status, "launch": "CUDA graph of bto_batch_run (reset + persistent kernel)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -460,6 +531,8 @@ def main():
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--only", default=None, help="comma-separated kernels (profiling runs)")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-only", action="store_true", help="profiling runs: only the batched form")
     ap.add_argument("--precision-only", type=int, default=0,
                     help="profiling runs: only the reduced-precision form at this n")
     ap.add_argument("--n", type=int, default=N_MAT, help="matrix size (profiling runs)")
@@ -470,6 +543,14 @@ def main():
         KERNELS = [k for k in KERNELS if k in args.only.split(",")]
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.batched_only:
+        import torch
+        from paper_1205_1098_gb300 import build
+        build.build()
+        import paper_1205_1098_gb300 as bto
+        hbm, _, _ = load_peaks()
+        print(json.dumps({"batched_form": batched_form(torch, bto, hbm, args.steps)}))
         return
     if args.precision_only:
         import torch
@@ -566,6 +647,10 @@ def main():
             pass
         torch.cuda.empty_cache()
         prec = precision_form(torch, bto, hbm, max(3, args.steps // 3))
+    batched = None
+    if not args.no_batched and not args.only:
+        torch.cuda.empty_cache()
+        batched = batched_form(torch, bto, hbm, max(3, args.steps // 3))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -590,6 +675,7 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "kernels": per, "unfused": unfused,
             "precision_form_n32768": prec,
+            "batched_4096": batched,
             "peaks": {"hbm_gbs": hbm, "hbm_source": peak_src, "fp64_tflops": round(fp64_peak, 4)},
         }))
     if dist:

@@ -195,6 +195,49 @@ bto_status bto_gemver_ex(int64_t m, int64_t n, float alpha, float beta, int a_ty
                          void *B, int64_t ldb, float *x, float *w,
                          void *ws, size_t ws_bytes, bto_stream_t stream);
 
+/* ------------------------------------------------------------ batched form
+ * Many independent, uneven BICGK and GEMVER instances (Table I) in one
+ * persistent launch, A and vectors in FP32 (no counterpart in the paper,
+ * which times one instance at a time).  Arithmetic is that of the
+ * reduced-precision form (FP32 FMA chains folded into TwoSum pairs, FP64 for
+ * the cross-panel combine); an instance gives the same bits alone or in a
+ * batch planned with the same tile_cols.
+ * Use: bto_batch_workspace_bytes -> bto_batch_prepare (host: builds the work
+ * list and copies it into ws, waiting for that copy) -> bto_batch_run, as
+ * often as wanted while the descriptors' buffers stay valid.  bto_batch_run
+ * only enqueues two kernels and performs no host synchronisation, so it may
+ * be recorded into a CUDA graph.  Calls sharing a ws must be ordered.
+ * tile_cols: width of the column panels each work item covers (16..1024, a
+ * multiple of 16; 0 picks 128).  Second-pass GEMVER items wait for their
+ * instance's first pass with a bounded wait (about 2 s); a timeout leaves
+ * BTO_ERR_TIMEOUT in the status word (bto_device_status). */
+typedef struct bto_batch_desc {
+    int32_t op;          /* BTO_OP_BICGK or BTO_OP_GEMVER                          */
+    int32_t reserved;
+    int64_t m, n;        /* sizes (>= 0)                                            */
+    int64_t lda, ldb;    /* leading dimensions of A and (GEMVER) B                  */
+    float alpha, beta;   /* GEMVER scalars; ignored for BICGK                      */
+    const float *A;      /* m x n, column-major                                    */
+    float *B;            /* GEMVER: output B (ldb); BICGK: unused                  */
+    const float *in[6];  /* BICGK: p (n), r (m); GEMVER: u1 (m), v1 (n), u2 (m),   */
+                         /*        v2 (n), y (m), z (n)                            */
+    float *out[2];       /* BICGK: q (m), s (n); GEMVER: x (n), w (m)              */
+} bto_batch_desc;
+
+/* Workspace bytes for a batch of `count` host descriptors. */
+bto_status bto_batch_workspace_bytes(int count, const bto_batch_desc *descs, int tile_cols,
+                                     size_t *bytes);
+
+/* Validates the host descriptors, builds the work list and copies it into
+ * ws (device, 256-byte aligned) on `stream`; returns once the copy is done.
+ * A descriptor with a bad size, leading dimension or NULL operand makes the
+ * call fail with BTO_ERR_INVALID_VALUE (argument 2). */
+bto_status bto_batch_prepare(int count, const bto_batch_desc *descs, int tile_cols, void *ws,
+                             size_t ws_bytes, bto_stream_t stream);
+
+/* Runs a prepared batch on `stream` (a reset kernel and the persistent kernel). */
+bto_status bto_batch_run(void *ws, size_t ws_bytes, bto_stream_t stream);
+
 /* BICGK without a workspace argument (the paper has no counterpart; this is
  * a convenience of this library).  Some callers cannot call cudaMalloc: a
  * plugin whose host application owns all device memory through its own

@@ -42,6 +42,8 @@ SIGNATURES = {
     "bto_bicgk_noalloc": "iipipppps",
     "bto_bicgk_ex": "iikpipppppzs",
     "bto_gemver_ex": "iiffkpipppppppipppzs",
+    "bto_batch_prepare": "kpkpzs",
+    "bto_batch_run": "pzs",
 }
 _KIND = {"i": _c_i64, "u": _c_u64, "d": _c_f64, "f": ctypes.c_float, "p": _c_ptr, "z": _c_size,
          "s": _c_ptr, "k": _c_int}
@@ -100,6 +102,8 @@ def _ptr(x):
         return None
     if isinstance(x, int):
         return x
+    if isinstance(x, (ctypes.Array, ctypes.Structure)):
+        return ctypes.addressof(x)
     return x.data_ptr()
 
 
@@ -175,6 +179,27 @@ def bto_device_status(ws, stream=None):
     st = L.bto_device_status(_ptr(ws), _stream(stream), ctypes.byref(out))
     if st != BTO_OK:
         raise BtoError("bto_device_status", st, L.bto_last_invalid_arg())
+    return out.value
+
+
+class BatchDesc(ctypes.Structure):
+    """bto_batch_desc of include/bto.h."""
+    _fields_ = [("op", ctypes.c_int32), ("reserved", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64),
+                ("alpha", ctypes.c_float), ("beta", ctypes.c_float), ("A", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("in_", ctypes.c_void_p * 6), ("out", ctypes.c_void_p * 2)]
+
+
+def bto_batch_workspace_bytes(descs, tile_cols=0):
+    """Workspace bytes for a ctypes array of BatchDesc."""
+    out = _c_size(0)
+    L = lib()
+    L.bto_batch_workspace_bytes.argtypes = [_c_int, ctypes.c_void_p, _c_int, ctypes.POINTER(_c_size)]
+    L.bto_batch_workspace_bytes.restype = _c_int
+    st = L.bto_batch_workspace_bytes(len(descs), ctypes.cast(descs, ctypes.c_void_p), int(tile_cols),
+                                     ctypes.byref(out))
+    if st != BTO_OK:
+        raise BtoError("bto_batch_workspace_bytes", st, L.bto_last_invalid_arg())
     return out.value
 
 

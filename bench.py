@@ -466,7 +466,7 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3):
         m, n = int(sizes[2 * i]), int(sizes[2 * i + 1])
         op = int(ops[i])
         d = descs[i]
-        d.op, d.m, d.n, d.lda, d.ldb, d.alpha, d.beta = op, m, n, m, m, 1.5, 1.25
+        d.op, d.a_type, d.m, d.n, d.lda, d.ldb, d.alpha, d.beta = op, 1, m, n, m, m, 1.5, 1.25
         A = torch.empty(m * n, **f32)
         bto.bto_fill_f32(seed, 1000 * i, 0, m, n, 0, A, m, None)
         keep.append(A)
@@ -520,6 +520,19 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3):
             "status": status, "launch": "CUDA graph of bto_batch_run (reset + persistent kernel)"}
 
 
+def serving_form(torch, duration=5.0, rate=20000.0, seed=4):
+    """Config 5: Poisson arrivals at `rate` of mixed GEMVER/BiCGK/ATAX/GESUMMV
+    requests, n log-uniform in [64, 8192], FP32 or BF16 matrices by a seeded
+    flag, resident operands, admission under a 40 GB budget."""
+    from paper_1205_1098_gb300.serve import Server, make_trace
+    srv = Server(budget_bytes=40e9, streams=4, max_batch=64, tile_cols=256, seed=seed)
+    srv.run(make_trace(seed + 1, rate, 0.0, count=200))          # warm-up trace
+    trace = make_trace(seed, rate, duration)
+    stats, _ = srv.run(trace, max_wall=duration * 6)
+    stats.update({"duration_s": duration, "rate_per_s": rate, "trace_requests": len(trace)})
+    return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in stats.items()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -532,6 +545,8 @@ def main():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--only", default=None, help="comma-separated kernels (profiling runs)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-only", type=float, default=0.0, help="profiling runs: only serving, for this many s")
     ap.add_argument("--batched-only", action="store_true", help="profiling runs: only the batched form")
     ap.add_argument("--precision-only", type=int, default=0,
                     help="profiling runs: only the reduced-precision form at this n")
@@ -543,6 +558,12 @@ def main():
         KERNELS = [k for k in KERNELS if k in args.only.split(",")]
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.serving_only:
+        import torch
+        from paper_1205_1098_gb300 import build
+        build.build()
+        print(json.dumps({"serving": serving_form(torch, duration=args.serving_only)}))
         return
     if args.batched_only:
         import torch
@@ -651,6 +672,10 @@ def main():
     if not args.no_batched and not args.only:
         torch.cuda.empty_cache()
         batched = batched_form(torch, bto, hbm, max(3, args.steps // 3))
+    serving = None
+    if not args.no_serving and not args.only:
+        torch.cuda.empty_cache()
+        serving = serving_form(torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -676,6 +701,7 @@ def main():
             "gpu_launches": launches, "kernels": per, "unfused": unfused,
             "precision_form_n32768": prec,
             "batched_4096": batched,
+            "serving": serving,
             "peaks": {"hbm_gbs": hbm, "hbm_source": peak_src, "fp64_tflops": round(fp64_peak, 4)},
         }))
     if dist:

@@ -196,32 +196,36 @@ bto_status bto_gemver_ex(int64_t m, int64_t n, float alpha, float beta, int a_ty
                          void *ws, size_t ws_bytes, bto_stream_t stream);
 
 /* ------------------------------------------------------------ batched form
- * Many independent, uneven BICGK and GEMVER instances (Table I) in one
- * persistent launch, A and vectors in FP32 (no counterpart in the paper,
- * which times one instance at a time).  Arithmetic is that of the
- * reduced-precision form (FP32 FMA chains folded into TwoSum pairs, FP64 for
- * the cross-panel combine); an instance gives the same bits alone or in a
- * batch planned with the same tile_cols.
+ * Many independent, uneven BICGK, GEMVER, ATAX and GESUMMV instances
+ * (Table I) in one persistent launch; matrices in FP32 or BF16, vectors FP32
+ * (no counterpart in the paper, which times one instance at a time).
+ * Arithmetic is that of the reduced-precision form (FP32 FMA chains folded
+ * into TwoSum pairs, FP64 for the cross-panel combines); GEMVER's B is
+ * rounded to the storage type and x, w use the stored B; ATAX forms
+ * t = A x in the workspace (FP32) and reads A a second time for
+ * y = beta A^T t.  An instance gives the same bits alone or in a batch
+ * planned with the same tile_cols.
  * Use: bto_batch_workspace_bytes -> bto_batch_prepare (host: builds the work
  * list and copies it into ws, waiting for that copy) -> bto_batch_run, as
  * often as wanted while the descriptors' buffers stay valid.  bto_batch_run
  * only enqueues two kernels and performs no host synchronisation, so it may
  * be recorded into a CUDA graph.  Calls sharing a ws must be ordered.
  * tile_cols: width of the column panels each work item covers (16..1024, a
- * multiple of 16; 0 picks 128).  Second-pass GEMVER items wait for their
- * instance's first pass with a bounded wait (about 2 s); a timeout leaves
- * BTO_ERR_TIMEOUT in the status word (bto_device_status). */
+ * multiple of 16; 0 picks 128).  Second-stage items (GEMVER's w, ATAX's y)
+ * wait for their instance's first stage with a bounded wait (about 2 s); a
+ * timeout leaves BTO_ERR_TIMEOUT in the status word (bto_device_status). */
 typedef struct bto_batch_desc {
-    int32_t op;          /* BTO_OP_BICGK or BTO_OP_GEMVER                          */
-    int32_t reserved;
-    int64_t m, n;        /* sizes (>= 0)                                            */
-    int64_t lda, ldb;    /* leading dimensions of A and (GEMVER) B                  */
-    float alpha, beta;   /* GEMVER scalars; ignored for BICGK                      */
-    const float *A;      /* m x n, column-major                                    */
-    float *B;            /* GEMVER: output B (ldb); BICGK: unused                  */
-    const float *in[6];  /* BICGK: p (n), r (m); GEMVER: u1 (m), v1 (n), u2 (m),   */
-                         /*        v2 (n), y (m), z (n)                            */
-    float *out[2];       /* BICGK: q (m), s (n); GEMVER: x (n), w (m)              */
+    int32_t op;          /* BTO_OP_BICGK, BTO_OP_GEMVER, BTO_OP_ATAX or BTO_OP_GESUMMV       */
+    int32_t a_type;      /* storage type of the matrices: BTO_F32 or BTO_BF16                */
+    int64_t m, n;        /* sizes (>= 0)                                                      */
+    int64_t lda, ldb;    /* leading dimensions of A and B                                     */
+    float alpha, beta;   /* GEMVER, GESUMMV: alpha, beta; ATAX: beta; BICGK: unused           */
+    const void *A;       /* m x n, column-major, a_type                                       */
+    void *B;             /* GEMVER: output B (ldb, a_type); GESUMMV: second input matrix     */
+    const float *in[6];  /* BICGK: p (n), r (m); GEMVER: u1 (m), v1 (n), u2 (m), v2 (n),     */
+                         /* y (m), z (n); ATAX: x (n); GESUMMV: x (n)                         */
+    float *out[2];       /* BICGK: q (m), s (n); GEMVER: x (n), w (m); ATAX: y (n);          */
+                         /* GESUMMV: y (m)                                                    */
 } bto_batch_desc;
 
 /* Workspace bytes for a batch of `count` host descriptors. */

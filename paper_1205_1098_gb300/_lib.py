@@ -184,7 +184,7 @@ def bto_device_status(ws, stream=None):
 
 class BatchDesc(ctypes.Structure):
     """bto_batch_desc of include/bto.h."""
-    _fields_ = [("op", ctypes.c_int32), ("reserved", ctypes.c_int32), ("m", ctypes.c_int64),
+    _fields_ = [("op", ctypes.c_int32), ("a_type", ctypes.c_int32), ("m", ctypes.c_int64),
                 ("n", ctypes.c_int64), ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64),
                 ("alpha", ctypes.c_float), ("beta", ctypes.c_float), ("A", ctypes.c_void_p),
                 ("B", ctypes.c_void_p), ("in_", ctypes.c_void_p * 6), ("out", ctypes.c_void_p * 2)]

@@ -1,27 +1,28 @@
-// Batched form: many independent, uneven BICGK and GEMVER instances (FP32
-// storage) in one persistent launch.
+// Batched form: many independent, uneven BICGK, GEMVER, ATAX and GESUMMV
+// instances (matrices in FP32 or BF16, vectors in FP32) in one persistent
+// launch.  The serving loop drives it too.
 //
 // bto_batch_prepare builds a work list on the host and uploads it into the
-// caller's workspace: one item per (instance, column panel) for BICGK and for
-// GEMVER's first pass, one item per (instance, 256-row block) for GEMVER's
-// second pass.  First-pass-like items come first, largest estimated cost
-// first (longest-processing-time order), then the second-pass items.
-// bto_batch_run launches a persistent grid (as many blocks as are resident)
-// whose blocks pull items from a device counter, so the load balances itself
-// and the launch contains no host synchronisation (it can be captured into a
-// CUDA graph).
+// caller's workspace.  Stage-one items: (instance, column panel) for BICGK,
+// GEMVER's first pass and GESUMMV; (instance, 256-row block) for ATAX's t = A x.
+// Stage-two items: (instance, 256-row block) for GEMVER's w = alpha B x and
+// (instance, column panel) for ATAX's y = beta A^T t.  Stage-one items come
+// first, largest estimated cost first (longest-processing-time order), then
+// the stage-two items.  bto_batch_run launches a persistent grid whose blocks
+// pull items from a device counter, so the load balances itself and the
+// launch contains no host synchronisation (it can be captured into a graph).
 //
 // Per item the arithmetic is that of the reduced-precision form: warps own
-// 16-column groups, lanes own 8 rows (two 16-byte loads per column), FP32
-// FMA chains folded into TwoSum (hi, lo) pairs, a transposing butterfly for
-// column sums.  A BICGK instance split into P panels leaves P row-partial
-// vectors; the panel that finishes last (per-instance counter) adds them in
-// panel order in FP64.  A GEMVER second-pass item waits, bounded by
-// %globaltimer, until every first-pass panel of its instance has published
+// 16-column groups, lanes own 8 rows (16-byte loads), FP32 FMA chains folded
+// into TwoSum (hi, lo) pairs, a transposing butterfly for column sums.  An
+// instance split into P column panels (BICGK's q, GESUMMV's y) leaves P
+// row-partial vectors; the panel that finishes last (per-instance counter)
+// adds them in panel order in FP64.  A stage-two item waits, bounded by
+// %globaltimer, until every stage-one item of its instance has published
 // (release/acquire on the counter); the wait always ends because all those
 // items were taken earlier by resident blocks.  Results do not depend on
 // which block runs an item, so an instance gives the same bits alone or in a
-// batch with the same panel width.
+// batch planned with the same panel width.
 #include "check.cuh"
 #include "lp_math.cuh"
 #include <algorithm>
@@ -38,19 +39,24 @@ constexpr int kWarps = 8;
 constexpr int kRows = 256;                 // rows per chunk: 32 lanes x 8 rows
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
-enum ItemKind { IT_BICGK = 0, IT_GEMVER1 = 1, IT_GEMVER2 = 2 };
+enum ItemKind { IT_BICGK = 0, IT_GEMVER1 = 1, IT_GEMVER2 = 2, IT_ATAX1 = 3, IT_ATAX2 = 4, IT_GESUMMV = 5 };
 
 struct Item { int32_t inst, kind, lo, hi; };
 
 struct InstInfo {
-    int32_t panels;        // first-pass panels of the instance
-    int32_t vec;           // 16-byte loads allowed (A, B and their leading dimensions aligned)
-    int64_t qoff;          // BICGK: offset (in float2) of its panel partials, -1 if one panel
+    int32_t stage1;        // stage-one items of the instance (what stage two waits for)
+    int32_t vec;           // 16-byte loads allowed (matrices and leading dimensions aligned)
+    int64_t qoff;          // BICGK/GESUMMV: offset (float2) of the panel partials, -1 if one panel
+    int64_t toff;          // ATAX: offset (float) of t
 };
 
+constexpr int kQueues = 4;   // (FP32, BF16) x (BICGK/GEMVER, ATAX/GESUMMV)
+
 struct Header {
-    int32_t count, nitems, tile_cols, pad;
-    int64_t off_desc, off_info, off_items, off_counters, off_qpart;
+    int32_t count, nitems, tile_cols, pad0;
+    int32_t qstart[kQueues + 1];                 // items of queue q: [qstart[q], qstart[q+1])
+    int32_t pad1[3];
+    int64_t off_desc, off_info, off_items, off_counters, off_qpart, off_t;
     int64_t counters_bytes, total;
 };
 
@@ -67,35 +73,98 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
-// Lane's k-th row within a 256-row chunk: two groups of four consecutive rows.
-__device__ __forceinline__ int brow(int lane, int k) { return (k >> 2) * 128 + lane * 4 + (k & 3); }
+// Lane's k-th row within a 256-row chunk: FP32 as two groups of four
+// consecutive rows, BF16 as eight consecutive rows (one 16-byte load).
+template <typename TA>
+__device__ __forceinline__ int brow(int lane, int k) {
+    if (sizeof(TA) == 2) return lane * 8 + k;
+    return (k >> 2) * 128 + lane * 4 + (k & 3);
+}
 
-template <bool COHERENT>
-__device__ __forceinline__ void load8(const float* col, int64_t R0, int64_t m, int lane, bool vec, float (&a)[8]) {
+// Element q of a 16-byte vector, as FP32, using register operations only.
+template <typename TA>
+__device__ __forceinline__ float unpack(const uint4& t, int q) {
+    const unsigned w = q < (sizeof(TA) == 2 ? 2 : 1) ? t.x
+                     : q < (sizeof(TA) == 2 ? 4 : 2) ? t.y
+                     : q < (sizeof(TA) == 2 ? 6 : 3) ? t.z : t.w;
+    if (sizeof(TA) == 4) return __uint_as_float(w);
+    return __uint_as_float((q & 1) ? (w & 0xFFFF0000u) : (w << 16));
+}
+
+template <typename TA>
+__device__ __forceinline__ unsigned bits_of(TA v);
+template <> __device__ __forceinline__ unsigned bits_of<float>(float v) { return __float_as_uint(v); }
+template <> __device__ __forceinline__ unsigned bits_of<__nv_bfloat16>(__nv_bfloat16 v) {
+    return (unsigned)__bfloat16_as_ushort(v);
+}
+
+template <typename TA, bool COHERENT>
+__device__ __forceinline__ void load8(const TA* col, int64_t R0, int64_t m, int lane, bool vec, float (&a)[8]) {
+    constexpr int V = 16 / sizeof(TA);
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const int64_t i = R0 + h * 128 + lane * 4;
-        if (vec && i + 4 <= m) {
-            const float4 t = COHERENT ? __ldcg(reinterpret_cast<const float4*>(col + i))
-                                      : __ldg(reinterpret_cast<const float4*>(col + i));
-            a[4 * h] = t.x; a[4 * h + 1] = t.y; a[4 * h + 2] = t.z; a[4 * h + 3] = t.w;
+    for (int h = 0; h < 8 / V; h++) {
+        const int64_t i = R0 + brow<TA>(lane, h * V);
+        if (vec && i + V <= m) {
+            const uint4 t = COHERENT ? __ldcg(reinterpret_cast<const uint4*>(col + i))
+                                     : __ldg(reinterpret_cast<const uint4*>(col + i));
+#pragma unroll
+            for (int q = 0; q < V; q++) a[h * V + q] = unpack<TA>(t, q);
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; e++) a[4 * h + e] = (i + e < m) ? (COHERENT ? __ldcg(col + i + e) : __ldg(col + i + e)) : 0.0f;
+            for (int q = 0; q < V; q++) {
+                float v = 0.0f;
+                if (i + q < m) {
+                    if (sizeof(TA) == 2) {
+                        const unsigned short b = COHERENT ? __ldcg(reinterpret_cast<const unsigned short*>(col + i + q))
+                                                          : __ldg(reinterpret_cast<const unsigned short*>(col + i + q));
+                        v = __uint_as_float((unsigned)b << 16);
+                    } else {
+                        v = COHERENT ? __ldcg(reinterpret_cast<const float*>(col + i + q))
+                                     : __ldg(reinterpret_cast<const float*>(col + i + q));
+                    }
+                }
+                a[h * V + q] = v;
+            }
         }
     }
 }
 
-__device__ __forceinline__ void load_rows(const float* v, int64_t R0, int64_t m, int lane, float (&o)[8]) {
+template <typename TA>
+__device__ __forceinline__ void store8(TA* col, int64_t R0, int64_t m, int lane, bool vec, const TA (&b)[8]) {
+    constexpr int V = 16 / sizeof(TA);
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-        const int64_t i = R0 + brow(lane, k);
-        o[k] = (i < m) ? __ldg(v + i) : 0.0f;
+    for (int h = 0; h < 8 / V; h++) {
+        const int64_t i = R0 + brow<TA>(lane, h * V);
+        if (vec && i + V <= m) {
+            uint4 t;
+            if (sizeof(TA) == 4) {
+                t.x = bits_of<TA>(b[h * V]); t.y = bits_of<TA>(b[h * V + 1]);
+                t.z = bits_of<TA>(b[h * V + 2]); t.w = bits_of<TA>(b[h * V + 3]);
+            } else {
+                t.x = bits_of<TA>(b[0]) | (bits_of<TA>(b[1]) << 16);
+                t.y = bits_of<TA>(b[2]) | (bits_of<TA>(b[3]) << 16);
+                t.z = bits_of<TA>(b[4]) | (bits_of<TA>(b[5]) << 16);
+                t.w = bits_of<TA>(b[6]) | (bits_of<TA>(b[7]) << 16);
+            }
+            *reinterpret_cast<uint4*>(col + i) = t;
+        } else {
+#pragma unroll
+            for (int q = 0; q < V; q++) if (i + q < m) col[i + q] = b[h * V + q];
+        }
     }
 }
 
-// Adds the warps' (hi, lo) row partials of one chunk (red: [2][kWarps][kRows])
-// in warp order with TwoSum; thread t handles row t.
+template <typename TA, bool COHERENT>
+__device__ __forceinline__ void load_rows(const float* v, int64_t R0, int64_t m, int lane, float (&o)[8]) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int64_t i = R0 + brow<TA>(lane, k);
+        o[k] = (i < m) ? (COHERENT ? __ldcg(v + i) : __ldg(v + i)) : 0.0f;
+    }
+}
+
+// Adds the warps' (hi, lo) row partials (red: [2][kWarps][kRows]) in warp
+// order with TwoSum; thread t handles row t.
 __device__ __forceinline__ void warp_rows_sum(const float* red, int t, float& hs, float& ls) {
     hs = red[t];
     ls = red[kWarps * kRows + t];
@@ -108,136 +177,178 @@ __device__ __forceinline__ void warp_rows_sum(const float* red, int t, float& hs
     }
 }
 
-// First-pass item: columns [c0, c1) of instance d over all its rows.
-// BICGK: s complete for the panel's columns, q partial (or complete).
-// GEMVER: B = A + u1 v1^T + u2 v2^T for the panel, x complete for its columns.
-template <int KIND>
-__device__ void first_pass(const bto_batch_desc& d, const InstInfo& info, int panel, int64_t c0, int64_t c1,
-                           float* red, float* shi, float* slo, float2* qpart) {
+template <typename TA>
+__device__ __forceinline__ void stash_rows(float* red, int warp, int lane, const float (&hi)[8], const float (&lo)[8]) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        red[warp * kRows + brow<TA>(lane, k)] = hi[k];
+        red[(kWarps + warp) * kRows + brow<TA>(lane, k)] = lo[k];
+    }
+}
+
+__device__ __forceinline__ void fold(float (&hi)[8], float (&lo)[8], float (&t)[8]) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        float s2, e2;
+        two_sum(hi[k], t[k], s2, e2);
+        hi[k] = s2; lo[k] += e2; t[k] = 0.0f;
+    }
+}
+
+// Column-panel item over all rows of instance d, columns [c0, c1).
+//   IT_BICGK   : s for the panel's columns, q row partials.
+//   IT_GEMVER1 : B = A + u1 v1^T + u2 v2^T for the panel, x for its columns.
+//   IT_ATAX2   : y = beta A^T t for the panel's columns (t from the workspace).
+//   IT_GESUMMV : row partials of A x and B x.
+template <int KIND, typename TA>
+__device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstInfo& info, int panel, int64_t c0, int64_t c1,
+                           float* red, float* red2, float* shi, float* slo, float2* qpart, const float* tbuf) {
+    constexpr bool HAS_Q = (KIND == IT_BICGK || KIND == IT_GESUMMV);
+    constexpr bool HAS_S = (KIND == IT_BICGK || KIND == IT_GEMVER1 || KIND == IT_ATAX2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t m = d.m, ncols = c1 - c0;
     const bool vec = info.vec != 0;
+    const TA* A = static_cast<const TA*>(d.A);
+    const TA* B2 = static_cast<const TA*>(d.B);      // GESUMMV's second matrix
+    TA* Bo = static_cast<TA*>(d.B);                  // GEMVER's output
+    const float* xin = d.in[0];
     for (int k = threadIdx.x; k < ncols; k += kThreads) { shi[k] = 0.0f; slo[k] = 0.0f; }
     __syncthreads();
-    const float* rvec = (KIND == IT_BICGK) ? d.in[1] : d.in[4];        // r, or GEMVER's y
     for (int64_t R0 = 0; R0 < m; R0 += kRows) {
-        float rv[8], u1r[8], u2r[8], qhi[8], qlo[8];
-        load_rows(rvec, R0, m, lane, rv);
-        if (KIND == IT_GEMVER1) { load_rows(d.in[0], R0, m, lane, u1r); load_rows(d.in[2], R0, m, lane, u2r); }
+        float rv[8], u1r[8], u2r[8], qhi[8], qlo[8], q2hi[8], q2lo[8];
+        if (KIND == IT_BICGK) load_rows<TA, false>(d.in[1], R0, m, lane, rv);
+        if (KIND == IT_GEMVER1) {
+            load_rows<TA, false>(d.in[4], R0, m, lane, rv);
+            load_rows<TA, false>(d.in[0], R0, m, lane, u1r);
+            load_rows<TA, false>(d.in[2], R0, m, lane, u2r);
+        }
+        if (KIND == IT_ATAX2) load_rows<TA, true>(tbuf + info.toff, R0, m, lane, rv);
 #pragma unroll
-        for (int k = 0; k < 8; k++) { qhi[k] = 0.0f; qlo[k] = 0.0f; }
+        for (int k = 0; k < 8; k++) { qhi[k] = 0.0f; qlo[k] = 0.0f; q2hi[k] = 0.0f; q2lo[k] = 0.0f; }
         for (int64_t g0 = c0 + 16 * warp; g0 < c1; g0 += 16 * kWarps) {
             const int nc = (int)((c1 - g0) < 16 ? (c1 - g0) : 16);
-            float sl[16], qt[8];
+            float sl[16], qt[8], q2t[8];
 #pragma unroll
-            for (int k = 0; k < 8; k++) qt[k] = 0.0f;
+            for (int k = 0; k < 8; k++) { qt[k] = 0.0f; q2t[k] = 0.0f; }
+            // Columns loaded ahead of use: four (two for GESUMMV, which loads two matrices).
+            constexpr int KU = KIND == IT_GESUMMV ? 2 : 4;
 #pragma unroll
-            for (int jb = 0; jb < 16; jb += 4) {
-                float av[4][8];
+            for (int jb = 0; jb < 16; jb += KU) {
+                float av[KU][8], bv[KU][8];
 #pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (jb + u < nc) load8<false>(d.A + (g0 + jb + u) * d.lda, R0, m, lane, vec, av[u]);
+                for (int u = 0; u < KU; u++)
+                    if (jb + u < nc) {
+                        load8<TA, false>(A + (g0 + jb + u) * d.lda, R0, m, lane, vec, av[u]);
+                        if (KIND == IT_GESUMMV) load8<TA, false>(B2 + (g0 + jb + u) * d.ldb, R0, m, lane, vec, bv[u]);
+                    }
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
+                for (int u = 0; u < KU; u++) {
                     const int jj = jb + u;
                     if (jj < nc) {
                         const int64_t j = g0 + jj;
-                        if (KIND == IT_BICGK) {
-                            const float pj = __ldg(d.in[0] + j);
+                        if (HAS_Q) {
+                            const float pj = __ldg(xin + j);
 #pragma unroll
                             for (int k = 0; k < 8; k++) qt[k] = fmaf(av[u][k], pj, qt[k]);
+                            if (KIND == IT_GESUMMV) {
+#pragma unroll
+                                for (int k = 0; k < 8; k++) q2t[k] = fmaf(bv[u][k], pj, q2t[k]);
+                            }
+                        }
+                        if (KIND == IT_GEMVER1) {
+                            const float v1j = __ldg(d.in[1] + j), v2j = __ldg(d.in[3] + j);
+                            TA bq[8];
+#pragma unroll
+                            for (int k = 0; k < 8; k++) {
+                                bq[k] = from_f<TA>(fmaf(u2r[k], v2j, fmaf(u1r[k], v1j, av[u][k])));
+                                av[u][k] = to_f<TA>(bq[k]);     // x uses the stored B
+                            }
+                            store8<TA>(Bo + j * d.ldb, R0, m, lane, vec, bq);
+                        }
+                        if (HAS_S) {
                             float acc = av[u][0] * rv[0];
 #pragma unroll
                             for (int k = 1; k < 8; k++) acc = fmaf(av[u][k], rv[k], acc);
                             sl[jj] = acc;
-                        } else {
-                            const float v1j = __ldg(d.in[1] + j), v2j = __ldg(d.in[3] + j);
-                            float b[8];
-#pragma unroll
-                            for (int k = 0; k < 8; k++) b[k] = fmaf(u2r[k], v2j, fmaf(u1r[k], v1j, av[u][k]));
-                            float* bc = d.B + j * d.ldb;
-#pragma unroll
-                            for (int h = 0; h < 2; h++) {
-                                const int64_t i = R0 + h * 128 + lane * 4;
-                                if (vec && i + 4 <= m) {
-                                    *reinterpret_cast<float4*>(bc + i) = make_float4(b[4 * h], b[4 * h + 1], b[4 * h + 2], b[4 * h + 3]);
-                                } else {
-#pragma unroll
-                                    for (int e = 0; e < 4; e++) if (i + e < m) bc[i + e] = b[4 * h + e];
-                                }
-                            }
-                            float acc = b[0] * rv[0];
-#pragma unroll
-                            for (int k = 1; k < 8; k++) acc = fmaf(b[k], rv[k], acc);
-                            sl[jj] = acc;
                         }
-                    } else {
+                    } else if (HAS_S) {
                         sl[jj] = 0.0f;
                     }
                 }
             }
-            if (KIND == IT_BICGK) {
-#pragma unroll
-                for (int k = 0; k < 8; k++) {
+            if (HAS_Q) fold(qhi, qlo, qt);
+            if (KIND == IT_GESUMMV) fold(q2hi, q2lo, q2t);
+            if (HAS_S) {
+                const float cs = butterfly16(sl, lane);
+                if (lane < nc) {
+                    const int64_t o = g0 + lane - c0;
                     float s2, e2;
-                    two_sum(qhi[k], qt[k], s2, e2);
-                    qhi[k] = s2; qlo[k] += e2;
+                    two_sum(shi[o], cs, s2, e2);
+                    shi[o] = s2; slo[o] += e2;
                 }
             }
-            const float cs = butterfly16(sl, lane);
-            if (lane < nc) {
-                const int64_t o = g0 + lane - c0;
-                float s2, e2;
-                two_sum(shi[o], cs, s2, e2);
-                shi[o] = s2; slo[o] += e2;
-            }
         }
-        if (KIND == IT_BICGK) {
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                red[warp * kRows + brow(lane, k)] = qhi[k];
-                red[(kWarps + warp) * kRows + brow(lane, k)] = qlo[k];
-            }
+        if (HAS_Q) {
+            stash_rows<TA>(red, warp, lane, qhi, qlo);
+            if (KIND == IT_GESUMMV) stash_rows<TA>(red2, warp, lane, q2hi, q2lo);
             __syncthreads();
             const int64_t i = R0 + threadIdx.x;
             if (i < m) {
                 float hs, ls;
                 warp_rows_sum(red, threadIdx.x, hs, ls);
-                if (info.qoff < 0) d.out[0][i] = (float)((double)hs + (double)ls);
-                else qpart[info.qoff + (int64_t)panel * m + i] = make_float2(hs, ls);
+                if (KIND == IT_BICGK) {
+                    if (info.qoff < 0) d.out[0][i] = (float)((double)hs + (double)ls);
+                    else qpart[info.qoff + (int64_t)panel * m + i] = make_float2(hs, ls);
+                } else {
+                    float h2, l2;
+                    warp_rows_sum(red2, threadIdx.x, h2, l2);
+                    if (info.qoff < 0) {
+                        d.out[0][i] = (float)fma((double)d.alpha, (double)hs + (double)ls,
+                                                 (double)d.beta * ((double)h2 + (double)l2));
+                    } else {
+                        qpart[info.qoff + ((int64_t)panel * 2) * m + i] = make_float2(hs, ls);
+                        qpart[info.qoff + ((int64_t)panel * 2 + 1) * m + i] = make_float2(h2, l2);
+                    }
+                }
             }
             __syncthreads();
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < ncols; k += kThreads) {
-        const double s = (double)shi[k] + (double)slo[k];
-        if (KIND == IT_BICGK) d.out[1][c0 + k] = (float)s;
-        else d.out[0][c0 + k] = (float)fma((double)d.beta, s, (double)__ldg(d.in[5] + c0 + k));
+    if (HAS_S) {
+        for (int k = threadIdx.x; k < ncols; k += kThreads) {
+            const double s = (double)shi[k] + (double)slo[k];
+            if (KIND == IT_BICGK) d.out[1][c0 + k] = (float)s;
+            else if (KIND == IT_GEMVER1) d.out[0][c0 + k] = (float)fma((double)d.beta, s, (double)__ldg(d.in[5] + c0 + k));
+            else d.out[0][c0 + k] = (float)((double)d.beta * s);
+        }
     }
 }
 
-// GEMVER second pass: w = alpha B x for rows [r0, r1) (r1 - r0 <= 256), all columns.
-__device__ void gemver_second(const bto_batch_desc& d, const InstInfo& info, int64_t R0, float* red) {
+// Row-block item over all columns, rows [R0, R0 + 256): out = scale * M v.
+//   IT_GEMVER2 : w = alpha B x (B and x written by stage one: coherent loads).
+//   IT_ATAX1   : t = A x into the workspace.
+template <int KIND, typename TA>
+__device__ __forceinline__ void row_item(const bto_batch_desc& d, const InstInfo& info, int64_t R0, float* red, float* tbuf) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t m = d.m, n = d.n;
     const bool vec = info.vec != 0;
-    float qhi[8], qlo[8];
+    const TA* M = static_cast<const TA*>(KIND == IT_GEMVER2 ? d.B : d.A);
+    const int64_t ld = KIND == IT_GEMVER2 ? d.ldb : d.lda;
+    const float* v = KIND == IT_GEMVER2 ? d.out[0] : d.in[0];
+    float qhi[8], qlo[8], qt[8];
 #pragma unroll
-    for (int k = 0; k < 8; k++) { qhi[k] = 0.0f; qlo[k] = 0.0f; }
+    for (int k = 0; k < 8; k++) { qhi[k] = 0.0f; qlo[k] = 0.0f; qt[k] = 0.0f; }
     for (int64_t g0 = 16 * warp; g0 < n; g0 += 16 * kWarps) {
         const int nc = (int)((n - g0) < 16 ? (n - g0) : 16);
-        float qt[8];
-#pragma unroll
-        for (int k = 0; k < 8; k++) qt[k] = 0.0f;
 #pragma unroll
         for (int jb = 0; jb < 16; jb += 4) {
             float av[4][8], xj[4];
 #pragma unroll
             for (int u = 0; u < 4; u++)
                 if (jb + u < nc) {
-                    load8<true>(d.B + (g0 + jb + u) * d.ldb, R0, m, lane, vec, av[u]);
-                    xj[u] = __ldcg(d.out[0] + g0 + jb + u);
+                    load8<TA, KIND == IT_GEMVER2>(M + (g0 + jb + u) * ld, R0, m, lane, vec, av[u]);
+                    xj[u] = KIND == IT_GEMVER2 ? __ldcg(v + g0 + jb + u) : __ldg(v + g0 + jb + u);
                 }
 #pragma unroll
             for (int u = 0; u < 4; u++)
@@ -246,44 +357,65 @@ __device__ void gemver_second(const bto_batch_desc& d, const InstInfo& info, int
                     for (int k = 0; k < 8; k++) qt[k] = fmaf(av[u][k], xj[u], qt[k]);
                 }
         }
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            float s2, e2;
-            two_sum(qhi[k], qt[k], s2, e2);
-            qhi[k] = s2; qlo[k] += e2;
-        }
+        fold(qhi, qlo, qt);
     }
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-        red[warp * kRows + brow(lane, k)] = qhi[k];
-        red[(kWarps + warp) * kRows + brow(lane, k)] = qlo[k];
-    }
+    stash_rows<TA>(red, warp, lane, qhi, qlo);
     __syncthreads();
     const int64_t i = R0 + threadIdx.x;
     if (i < m) {
         float hs, ls;
         warp_rows_sum(red, threadIdx.x, hs, ls);
-        d.out[1][i] = (float)((double)d.alpha * ((double)hs + (double)ls));
+        if (KIND == IT_GEMVER2) d.out[1][i] = (float)((double)d.alpha * ((double)hs + (double)ls));
+        else tbuf[info.toff + i] = (float)((double)hs + (double)ls);
     }
     __syncthreads();
 }
 
+// Item families, each run by its own kernel so that one family's register
+// needs do not burden the other's: 0 = BICGK and GEMVER, 1 = ATAX and GESUMMV.
+__host__ __device__ inline int family_of(int kind) {
+    return (kind == IT_BICGK || kind == IT_GEMVER1 || kind == IT_GEMVER2) ? 0 : 1;
+}
+
+template <typename TA, int FAM>
+__device__ void run_item(const Item& item, const bto_batch_desc& d, const InstInfo& info, int tile_cols,
+                         float* red, float* red2, float* shi, float* slo, float2* qpart, float* tbuf) {
+    const int panel = tile_cols ? (int)(item.lo / tile_cols) : 0;
+    if (FAM == 0) {
+        switch (item.kind) {
+            case IT_BICGK: panel_item<IT_BICGK, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf); break;
+            case IT_GEMVER1: panel_item<IT_GEMVER1, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf); break;
+            case IT_GEMVER2: row_item<IT_GEMVER2, TA>(d, info, item.lo, red, tbuf); break;
+        }
+    } else {
+        switch (item.kind) {
+            case IT_ATAX2: panel_item<IT_ATAX2, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf); break;
+            case IT_GESUMMV: panel_item<IT_GESUMMV, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf); break;
+            case IT_ATAX1: row_item<IT_ATAX1, TA>(d, info, item.lo, red, tbuf); break;
+        }
+    }
+}
+
+template <typename TA, int FAM>
 __global__ void __launch_bounds__(kThreads, 1) batch_kernel(char* ws) {
     const Header* h = reinterpret_cast<const Header*>(ws + kHeaderOff);
     const bto_batch_desc* descs = reinterpret_cast<const bto_batch_desc*>(ws + h->off_desc);
     const InstInfo* infos = reinterpret_cast<const InstInfo*>(ws + h->off_info);
-    const Item* items = reinterpret_cast<const Item*>(ws + h->off_items);
-    unsigned* counters = reinterpret_cast<unsigned*>(ws + h->off_counters);   // [0] queue, [1+i] instance
+    constexpr int Q = (sizeof(TA) == 2 ? 2 : 0) + FAM;   // this kernel's queue (storage type, family)
+    const Item* items = reinterpret_cast<const Item*>(ws + h->off_items) + h->qstart[Q];
+    unsigned* counters = reinterpret_cast<unsigned*>(ws + h->off_counters);   // [0..3] queues, [4+i] instances
     float2* qpart = reinterpret_cast<float2*>(ws + h->off_qpart);
+    float* tbuf = reinterpret_cast<float*>(ws + h->off_t);
     int* status = reinterpret_cast<int*>(ws);
-    __shared__ float red[2 * kWarps * kRows];
-    extern __shared__ float sacc[];   // [2][tile_cols]
-    float* shi = sacc;
-    float* slo = sacc + h->tile_cols;
+    extern __shared__ float sm[];   // red [2][8][256], red2 [2][8][256], s (hi, lo) [2][tile_cols]
+    float* red = sm;
+    float* red2 = sm + 2 * kWarps * kRows;
+    float* shi = red2 + 2 * kWarps * kRows;
+    float* slo = shi + h->tile_cols;
     __shared__ int s_item, s_ok, s_last;
-    const int nitems = h->nitems;
+    const int nitems = h->qstart[Q + 1] - h->qstart[Q];
     while (true) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(counters, 1u);
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counters + Q, 1u);
         __syncthreads();
         const int it = s_item;
         __syncthreads();
@@ -291,41 +423,52 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(char* ws) {
         const Item item = items[it];
         const bto_batch_desc d = descs[item.inst];
         const InstInfo info = infos[item.inst];
-        if (item.kind == IT_GEMVER2) {
+        const bool stage2 = item.kind == IT_GEMVER2 || item.kind == IT_ATAX2;
+        if (stage2) {
             if (threadIdx.x == 0) {
                 const unsigned long long t0 = gtimer();
                 int ok = 1;
-                while (ld_acquire_u32(counters + 1 + item.inst) < (unsigned)info.panels) {
+                while (ld_acquire_u32(counters + kQueues + item.inst) < (unsigned)info.stage1) {
                     if (gtimer() - t0 > kWaitNs) { ok = 0; atomicExch(status, (int)BTO_ERR_TIMEOUT); break; }
                     __nanosleep(100);
                 }
                 s_ok = ok;
             }
             __syncthreads();
-            if (s_ok) gemver_second(d, info, item.lo, red);
-            continue;
         }
-        const int64_t c0 = item.lo, c1 = item.hi;
-        const int panel = (int)(c0 / h->tile_cols);
-        if (item.kind == IT_BICGK) first_pass<IT_BICGK>(d, info, panel, c0, c1, red, shi, slo, qpart);
-        else first_pass<IT_GEMVER1>(d, info, panel, c0, c1, red, shi, slo, qpart);
-        // Publish this panel (release); the last BICGK panel adds the row partials.
+        if (!stage2 || s_ok) run_item<TA, FAM>(item, d, info, h->tile_cols, red, red2, shi, slo, qpart, tbuf);
+        if (stage2) continue;
+        // Publish this stage-one item (release); the last panel of a split
+        // BICGK or GESUMMV adds the row partials in panel order.
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            const unsigned old = atomicAdd(counters + 1 + item.inst, 1u);
-            s_last = (item.kind == IT_BICGK && info.qoff >= 0 && old == (unsigned)(info.panels - 1));
+            const unsigned old = atomicAdd(counters + kQueues + item.inst, 1u);
+            s_last = ((item.kind == IT_BICGK || item.kind == IT_GESUMMV) && info.qoff >= 0 &&
+                      old == (unsigned)(info.stage1 - 1));
         }
         __syncthreads();
         if (s_last) {
             __threadfence();
+            const int P = info.stage1;   // panels of this split instance
             for (int64_t i = threadIdx.x; i < d.m; i += kThreads) {
-                double s = 0.0;
-                for (int p = 0; p < info.panels; p++) {
-                    const float2 v = __ldcg(qpart + info.qoff + (int64_t)p * d.m + i);
-                    s += (double)v.x + (double)v.y;
+                if (item.kind == IT_BICGK) {
+                    double s = 0.0;
+                    for (int p = 0; p < P; p++) {
+                        const float2 v = __ldcg(qpart + info.qoff + (int64_t)p * d.m + i);
+                        s += (double)v.x + (double)v.y;
+                    }
+                    d.out[0][i] = (float)s;
+                } else {
+                    double sa = 0.0, sb = 0.0;
+                    for (int p = 0; p < P; p++) {
+                        const float2 va = __ldcg(qpart + info.qoff + ((int64_t)p * 2) * d.m + i);
+                        const float2 vb = __ldcg(qpart + info.qoff + ((int64_t)p * 2 + 1) * d.m + i);
+                        sa += (double)va.x + (double)va.y;
+                        sb += (double)vb.x + (double)vb.y;
+                    }
+                    d.out[0][i] = (float)fma((double)d.alpha, sa, (double)d.beta * sb);
                 }
-                d.out[0][i] = (float)s;
             }
         }
     }
@@ -340,7 +483,8 @@ __global__ void batch_reset_kernel(char* ws) {
     if (threadIdx.x == 0) *reinterpret_cast<int*>(ws) = 0;
 }
 
-constexpr size_t kSaccBytes = 2 * 1024 * sizeof(float);   // s (hi, lo) for panels up to 1024 columns
+constexpr int kMaxTile = 1024;
+constexpr size_t kSmemBytes = (4 * kWarps * kRows + 2 * kMaxTile) * sizeof(float);
 
 struct Plan {
     Header h{};
@@ -348,58 +492,78 @@ struct Plan {
     std::vector<Item> items;
 };
 
+int64_t esize(int a_type) { return a_type == BTO_BF16 ? 2 : 4; }
+
+bool valid_desc(const bto_batch_desc& d) {
+    const int op = d.op;
+    if (op != BTO_OP_BICGK && op != BTO_OP_GEMVER && op != BTO_OP_ATAX && op != BTO_OP_GESUMMV) return false;
+    if (d.a_type != BTO_F32 && d.a_type != BTO_BF16) return false;
+    if (d.m < 0 || d.n < 0 || d.m > INT32_MAX || d.n > INT32_MAX) return false;
+    if (d.lda < std::max<int64_t>(1, d.m)) return false;
+    const bool mat = d.m > 0 && d.n > 0;
+    if (mat && (!d.A || reinterpret_cast<uintptr_t>(d.A) % esize(d.a_type))) return false;
+    if ((op == BTO_OP_GEMVER || op == BTO_OP_GESUMMV) &&
+        (d.ldb < std::max<int64_t>(1, d.m) || (mat && !d.B))) return false;
+    // Input and output vector lengths per op.
+    int64_t in_len[6] = {0, 0, 0, 0, 0, 0}, out_len[2] = {0, 0};
+    if (op == BTO_OP_BICGK) { in_len[0] = d.n; in_len[1] = d.m; out_len[0] = d.m; out_len[1] = d.n; }
+    if (op == BTO_OP_GEMVER) {
+        for (int k = 0; k < 6; k++) in_len[k] = (k % 2 == 0) ? d.m : d.n;
+        out_len[0] = d.n; out_len[1] = d.m;
+    }
+    if (op == BTO_OP_ATAX) { in_len[0] = d.n; out_len[0] = d.n; }
+    if (op == BTO_OP_GESUMMV) { in_len[0] = d.n; out_len[0] = d.m; }
+    for (int k = 0; k < 6; k++) if (in_len[k] > 0 && !d.in[k]) return false;
+    for (int k = 0; k < 2; k++) if (out_len[k] > 0 && !d.out[k]) return false;
+    return true;
+}
+
 bool make_plan(int count, const bto_batch_desc* descs, int tile_cols, Plan* P, int* bad_desc) {
     P->info.resize(count);
     std::vector<std::pair<double, Item>> first, second;
-    int64_t qsize = 0;
+    int64_t qsize = 0, tsize = 0;
     for (int i = 0; i < count; i++) {
         const bto_batch_desc& d = descs[i];
-        const bool bicgk = d.op == BTO_OP_BICGK, gemver = d.op == BTO_OP_GEMVER;
-        bool ok = (bicgk || gemver) && d.m >= 0 && d.n >= 0 && d.lda >= std::max<int64_t>(1, d.m);
-        if (ok && d.m > 0 && d.n > 0) ok = d.A != nullptr;
-        if (ok && gemver) ok = d.ldb >= std::max<int64_t>(1, d.m) && (d.m == 0 || d.n == 0 || d.B);
-        const int nin = bicgk ? 2 : 6;
-        for (int k = 0; ok && k < nin; k++) {
-            // BICGK: p (n), r (m).  GEMVER: u1 (m), v1 (n), u2 (m), v2 (n), y (m), z (n).
-            const int64_t len = bicgk ? (k == 0 ? d.n : d.m) : (k % 2 == 0 ? d.m : d.n);
-            if (len > 0 && !d.in[k]) ok = false;
-        }
-        for (int k = 0; ok && k < 2; k++) {
-            const int64_t len = bicgk ? (k == 0 ? d.m : d.n) : (k == 0 ? d.n : d.m);
-            if (len > 0 && !d.out[k]) ok = false;
-        }
-        if (!ok) { *bad_desc = i; return false; }
+        if (!valid_desc(d)) { *bad_desc = i; return false; }
+        const int op = d.op;
+        const int64_t m = d.m, n = d.n, es = esize(d.a_type), V = 16 / es;
         InstInfo& inf = P->info[i];
-        const int64_t panels = d.n > 0 ? ceil_div(d.n, tile_cols) : 0;
-        inf.panels = (int32_t)panels;
-        inf.vec = aligned16(d.A) && d.lda % 4 == 0 && (!gemver || (aligned16(d.B) && d.ldb % 4 == 0));
+        inf.vec = aligned16(d.A) && d.lda % V == 0 &&
+                  ((op != BTO_OP_GEMVER && op != BTO_OP_GESUMMV) || (aligned16(d.B) && d.ldb % V == 0));
         inf.qoff = -1;
-        if (bicgk && panels > 1 && d.m > 0) { inf.qoff = qsize; qsize += panels * d.m; }
-        if (d.n == 0 || d.m == 0) {
-            // Degenerate instance: one first-pass item still writes the empty sums.
-            if (d.n > 0) {
-                for (int64_t c = 0; c < d.n; c += tile_cols)
-                    first.push_back({0.0, Item{i, bicgk ? IT_BICGK : IT_GEMVER1, (int32_t)c,
-                                               (int32_t)std::min<int64_t>(d.n, c + tile_cols)}});
-            } else if (d.m > 0) {
-                inf.panels = 0;
-                if (bicgk) first.push_back({0.0, Item{i, IT_BICGK, 0, 0}});
+        inf.toff = -1;
+        const int64_t panels = n > 0 ? ceil_div(n, tile_cols) : 0;
+        const int64_t rblocks = m > 0 ? ceil_div(m, kRows) : 0;
+        auto push = [&](std::vector<std::pair<double, Item>>& v, int kind, int64_t lo, int64_t hi, double cost) {
+            v.push_back({cost, Item{i, kind, (int32_t)lo, (int32_t)hi}});
+        };
+        const double mm = (double)m;
+        if (op == BTO_OP_BICGK || op == BTO_OP_GESUMMV) {
+            const int kind = op == BTO_OP_BICGK ? IT_BICGK : IT_GESUMMV;
+            const double w = op == BTO_OP_GESUMMV ? 2.0 : 1.0;
+            if (panels == 0) {
+                if (m > 0) push(first, kind, 0, 0, 0.0);     // writes the empty sums
+                inf.stage1 = m > 0 ? 1 : 0;
+            } else {
+                for (int64_t c = 0; c < n; c += tile_cols)
+                    push(first, kind, c, std::min<int64_t>(n, c + tile_cols), w * mm * (double)(std::min<int64_t>(n, c + tile_cols) - c));
+                inf.stage1 = (int32_t)panels;
+                if (panels > 1 && m > 0) { inf.qoff = qsize; qsize += panels * m * (op == BTO_OP_GESUMMV ? 2 : 1); }
             }
-            if (gemver && d.m > 0)
-                for (int64_t r = 0; r < d.m; r += kRows)
-                    second.push_back({0.0, Item{i, IT_GEMVER2, (int32_t)r, (int32_t)std::min<int64_t>(d.m, r + kRows)}});
-            continue;
+        } else if (op == BTO_OP_GEMVER) {
+            for (int64_t c = 0; c < n; c += tile_cols)
+                push(first, IT_GEMVER1, c, std::min<int64_t>(n, c + tile_cols), 2.0 * mm * (double)(std::min<int64_t>(n, c + tile_cols) - c));
+            inf.stage1 = (int32_t)panels;
+            for (int64_t r = 0; r < m; r += kRows)
+                push(second, IT_GEMVER2, r, std::min<int64_t>(m, r + kRows), (double)(std::min<int64_t>(m, r + kRows) - r) * (double)n);
+        } else {   // ATAX: t = A x by row blocks, then y = beta A^T t by panels
+            for (int64_t r = 0; r < m; r += kRows)
+                push(first, IT_ATAX1, r, std::min<int64_t>(m, r + kRows), (double)(std::min<int64_t>(m, r + kRows) - r) * (double)n);
+            inf.stage1 = (int32_t)rblocks;
+            if (m > 0) { inf.toff = tsize; tsize += round_up(m, 64); }
+            for (int64_t c = 0; c < n; c += tile_cols)
+                push(second, IT_ATAX2, c, std::min<int64_t>(n, c + tile_cols), mm * (double)(std::min<int64_t>(n, c + tile_cols) - c));
         }
-        for (int64_t c = 0; c < d.n; c += tile_cols) {
-            const int64_t c1 = std::min<int64_t>(d.n, c + tile_cols);
-            const double cost = (double)d.m * (double)(c1 - c) * (gemver ? 2.0 : 1.0);
-            first.push_back({cost, Item{i, bicgk ? IT_BICGK : IT_GEMVER1, (int32_t)c, (int32_t)c1}});
-        }
-        if (gemver)
-            for (int64_t r = 0; r < d.m; r += kRows) {
-                const int64_t r1 = std::min<int64_t>(d.m, r + kRows);
-                second.push_back({(double)(r1 - r) * (double)d.n, Item{i, IT_GEMVER2, (int32_t)r, (int32_t)r1}});
-            }
     }
     auto by_cost = [](const std::pair<double, Item>& a, const std::pair<double, Item>& b) {
         if (a.first != b.first) return a.first > b.first;
@@ -408,9 +572,18 @@ bool make_plan(int count, const bto_batch_desc* descs, int tile_cols, Plan* P, i
     };
     std::stable_sort(first.begin(), first.end(), by_cost);
     std::stable_sort(second.begin(), second.end(), by_cost);
-    for (auto& e : first) P->items.push_back(e.second);
-    for (auto& e : second) P->items.push_back(e.second);
+    // Four queues, one per (storage type, item family), each run by its own
+    // kernel; within a queue, stage one before stage two.
     Header& H = P->h;
+    for (int q = 0; q < kQueues; q++) {
+        const int want_t = q < 2 ? BTO_F32 : BTO_BF16, want_f = q % 2;
+        H.qstart[q] = (int32_t)P->items.size();
+        for (auto* v : {&first, &second})
+            for (auto& e : *v)
+                if (descs[e.second.inst].a_type == want_t && family_of(e.second.kind) == want_f)
+                    P->items.push_back(e.second);
+    }
+    H.qstart[kQueues] = (int32_t)P->items.size();
     H.count = count;
     H.nitems = (int32_t)P->items.size();
     H.tile_cols = tile_cols;
@@ -419,14 +592,15 @@ bool make_plan(int count, const bto_batch_desc* descs, int tile_cols, Plan* P, i
     H.off_desc = region((size_t)count * sizeof(bto_batch_desc));
     H.off_info = region((size_t)count * sizeof(InstInfo));
     H.off_items = region(P->items.size() * sizeof(Item));
-    H.counters_bytes = (int64_t)(count + 1) * sizeof(unsigned);
+    H.counters_bytes = (int64_t)(count + kQueues) * sizeof(unsigned);
     H.off_counters = region((size_t)H.counters_bytes);
     H.off_qpart = region((size_t)std::max<int64_t>(qsize, 1) * sizeof(float2));
+    H.off_t = region((size_t)std::max<int64_t>(tsize, 1) * sizeof(float));
     H.total = cur;
     return true;
 }
 
-bool check_tile(int tile_cols) { return tile_cols >= 16 && tile_cols <= 1024 && tile_cols % 16 == 0; }
+bool check_tile(int tile_cols) { return tile_cols >= 16 && tile_cols <= kMaxTile && tile_cols % 16 == 0; }
 
 }  // namespace
 }  // namespace bto
@@ -482,13 +656,23 @@ extern "C" bto_status bto_batch_run(void* ws, size_t ws_bytes, bto_stream_t stre
     DeviceInfo dinf;
     if (!device_info(&dinf)) return BTO_ERR_CUDA;
     static int occ = 0;
-    if (occ == 0 &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kThreads, kSaccBytes) != cudaSuccess)
-        return BTO_ERR_CUDA;
+    if (occ == 0) {
+        if (cudaFuncSetAttribute(batch_kernel<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
+            cudaFuncSetAttribute(batch_kernel<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
+            cudaFuncSetAttribute(batch_kernel<__nv_bfloat16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
+            cudaFuncSetAttribute(batch_kernel<__nv_bfloat16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<float, 0>, kThreads, kSmemBytes) != cudaSuccess)
+            return BTO_ERR_CUDA;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     char* w = static_cast<char*>(ws);
+    const int grid = dinf.sms * std::max(occ, 1);
     batch_reset_kernel<<<1, 256, 0, st>>>(w);
     if (cudaGetLastError() != cudaSuccess) return BTO_ERR_CUDA;
-    batch_kernel<<<dinf.sms * std::max(occ, 1), kThreads, kSaccBytes, st>>>(w);
+    // One kernel per queue, in order; a kernel whose queue is empty exits at once.
+    batch_kernel<float, 0><<<grid, kThreads, kSmemBytes, st>>>(w);
+    batch_kernel<float, 1><<<grid, kThreads, kSmemBytes, st>>>(w);
+    batch_kernel<__nv_bfloat16, 0><<<grid, kThreads, kSmemBytes, st>>>(w);
+    batch_kernel<__nv_bfloat16, 1><<<grid, kThreads, kSmemBytes, st>>>(w);
     return launch_status();
 }

@@ -449,6 +449,63 @@ def precision_form(torch, bto, hbm, steps, n=32768):
     return out
 
 
+def mrhs_form(torch, bto, hbm, steps, n=8192, k=64, seed=6):
+    """Multi-right-hand-side BICGK: Q = A P, S = A^T R with A n x n BF16 and
+    k BF16 right-hand sides, FP32 Q and S, on the tensor cores.  Each timed
+    call is bracketed by CUDA events after an L2 flush (a 512 MiB read), so
+    A comes from HBM every time.  Effective bandwidth is over the compulsory
+    bytes (A once, P and R once, Q and S written once); the tensor rate is
+    4 n^2 k flops over the same time.  Sampled normwise errors are computed
+    with numpy in FP64 on the stored BF16 values."""
+    import synth
+    st = torch.cuda.current_stream()
+    A = torch.empty(n * n, dtype=torch.int16, device="cuda")
+    bto.bto_fill_bf16(seed, 0, 0, n, n, 0, A, n, None)
+    Pb = synth.to_bf16_bits(synth.matrix(seed, 1, n, k)).ravel(order="F")
+    Rb = synth.to_bf16_bits(synth.matrix(seed, 2, n, k)).ravel(order="F")
+    dP = torch.from_numpy(Pb.view(np.int16).copy()).cuda()
+    dR = torch.from_numpy(Rb.view(np.int16).copy()).cuda()
+    Q = torch.empty(n * k, dtype=torch.float32, device="cuda")
+    S = torch.empty(n * k, dtype=torch.float32, device="cuda")
+    wb = bto.bto_bicgk_mrhs_workspace_bytes(n, n, k)
+    wsb = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    flush = torch.ones(128 << 20, dtype=torch.float32, device="cuda")
+
+    def call():
+        bto.bto_bicgk_mrhs(n, n, k, A, n, dP, n, dR, n, Q, n, S, n, wsb, wb, None)
+
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in evs:
+        flush.sum()            # reads 512 MiB: evicts A without leaving dirty lines in L2
+        e0.record(st)
+        call()
+        e1.record(st)
+    torch.cuda.synchronize()
+    ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in evs]))
+    status = bto.bto_device_status(wsb)
+    byts = 2 * n * n + 2 * 2 * k * n + 2 * 4 * k * n
+    fl = 4.0 * n * n * k
+    rows = np.linspace(0, n - 1, 8).astype(np.int64)
+    Pq = synth.bf16_bits_to_f64(Pb.reshape(k, n).T)
+    Rq = synth.bf16_bits_to_f64(Rb.reshape(k, n).T)
+    Ar = synth.bf16_bits_to_f64(synth.to_bf16_bits(synth.matrix_rows(seed, 0, n, n, rows)))
+    Ac = synth.bf16_bits_to_f64(synth.to_bf16_bits(synth.matrix_cols(seed, 0, n, n, rows)))
+    Qh = Q.view(k, n).T.cpu().numpy()[rows].astype(np.float64)
+    Sh = S.view(k, n).T.cpu().numpy()[rows].astype(np.float64)
+    qref, sref = Ar @ Pq, Ac.T @ Rq
+    del A, flush, wsb
+    torch.cuda.empty_cache()
+    return {"workload": "A %dx%d BF16, k=%d BF16 right-hand sides, Q/S FP32" % (n, n, k),
+            "ms": round(ms, 4), "gbs": round(byts / ms / 1e6, 1), "hbm_frac": round(byts / ms / 1e6 / hbm, 3),
+            "tflops": round(fl / ms / 1e9, 1), "compulsory_bytes": byts, "flops": fl, "status": status,
+            "l2": "flushed (512 MiB read) before every timed call",
+            "sampled_err": {"q": float(np.linalg.norm(Qh - qref) / np.linalg.norm(qref)),
+                            "s": float(np.linalg.norm(Sh - sref) / np.linalg.norm(sref))}}
+
+
 def batched_form(torch, bto, hbm, steps, count=4096, seed=3):
     """Config 4: `count` BICGK/GEMVER instances (50/50 by a draw), m, n
     log-uniform in [32, 2048], FP32, one persistent launch, replayed from a
@@ -548,6 +605,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-only", type=float, default=0.0, help="profiling runs: only serving, for this many s")
     ap.add_argument("--batched-only", action="store_true", help="profiling runs: only the batched form")
+    ap.add_argument("--mrhs-only", type=int, default=0, help="profiling runs: only multi-RHS BICGK with this k")
+    ap.add_argument("--no-mrhs", action="store_true")
     ap.add_argument("--precision-only", type=int, default=0,
                     help="profiling runs: only the reduced-precision form at this n")
     ap.add_argument("--n", type=int, default=N_MAT, help="matrix size (profiling runs)")
@@ -572,6 +631,15 @@ def main():
         import paper_1205_1098_gb300 as bto
         hbm, _, _ = load_peaks()
         print(json.dumps({"batched_form": batched_form(torch, bto, hbm, args.steps)}))
+        return
+    if args.mrhs_only:
+        import torch
+        from paper_1205_1098_gb300 import build
+        build.build()
+        import paper_1205_1098_gb300 as bto
+        hbm, _, _ = load_peaks()
+        print(json.dumps({"mrhs": mrhs_form(torch, bto, hbm, args.steps, n=args.n if args.n != N_MAT else 8192,
+                                            k=args.mrhs_only)}))
         return
     if args.precision_only:
         import torch
@@ -672,6 +740,10 @@ def main():
     if not args.no_batched and not args.only:
         torch.cuda.empty_cache()
         batched = batched_form(torch, bto, hbm, max(3, args.steps // 3))
+    mrhs = None
+    if not args.no_mrhs and not args.only:
+        torch.cuda.empty_cache()
+        mrhs = mrhs_form(torch, bto, hbm, max(3, args.steps // 3))
     serving = None
     if not args.no_serving and not args.only:
         torch.cuda.empty_cache()
@@ -695,12 +767,13 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (SplitMix64 uniform[-1,1), seed 1), generated on the device",
             "config": {"workload": "FP64 kernel suite: 16384x16384 column-major matrices, 2^26-element "
-                                   "vectors (configs[1])", "parallelism": "replicas" if world > 1 else "single",
+                                   "vectors", "parallelism": "replicas" if world > 1 else "single",
                        "l2": "every input is larger than L2 (2 GiB matrices, 512 MiB vectors); no flush"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "kernels": per, "unfused": unfused,
             "precision_form_n32768": prec,
             "batched_4096": batched,
+            "mrhs_8192_k64": mrhs,
             "serving": serving,
             "peaks": {"hbm_gbs": hbm, "hbm_source": peak_src, "fp64_tflops": round(fp64_peak, 4)},
         }))

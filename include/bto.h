@@ -242,6 +242,40 @@ bto_status bto_batch_prepare(int count, const bto_batch_desc *descs, int tile_co
 /* Runs a prepared batch on `stream` (a reset kernel and the persistent kernel). */
 bto_status bto_batch_run(void *ws, size_t ws_bytes, bto_stream_t stream);
 
+/* ------------------------------------------------- multi-right-hand-side BICGK
+ * The BICGK kernel of Table I with k right-hand sides at once (the paper has
+ * one; a block Krylov method or several independent solves sharing A has k):
+ *     Q <- A P,   S <- A^T R
+ * A m x n, P n x k, R m x k, all BF16 (raw 16-bit words, column-major with
+ * leading dimensions lda, ldp, ldr); Q m x k and S n x k FP32 (ldq, lds).
+ * Every element of A is read from device memory once and feeds both
+ * products, which run on the tensor cores (BF16 products, FP32
+ * accumulation); partial sums over 512-column panels and over row ranges are
+ * added in compensated FP32 (TwoSum) in a fixed order, so the result is
+ * reproducible bit for bit and its normwise error against the exact product
+ * of the BF16 inputs is of order 1e-7 for uniform random data.
+ *  - k: 16 to 96, a multiple of 16.  m = 0 or n = 0 is accepted (Q or S
+ *    becomes 0; the other is empty).
+ *  - A, P, R must be 2-byte aligned, Q and S 4-byte aligned.  When A, P and
+ *    R are 16-byte aligned with leading dimensions that are multiples of 8,
+ *    tiles are copied by the tensor memory accelerator; otherwise a slower
+ *    kernel copies 16-byte chunks (element by element where unaligned).  Both
+ *    give the same bits.
+ *  - Q and S must not overlap each other or any input.
+ *  - ws: device memory of bto_bicgk_mrhs_workspace_bytes(m, n, k) bytes,
+ *    256-byte aligned, owned by the caller; nothing in it needs to start at
+ *    zero.  Its first int is the status word (bto_device_status).
+ *  - Waits inside the kernel are bounded (1 s); a timeout leaves
+ *    BTO_ERR_TIMEOUT in the status word.
+ * Errors: BTO_ERR_INVALID_VALUE with bto_last_invalid_arg() naming the
+ * argument (1-based), BTO_ERR_WORKSPACE (argument 14) for a missing, short
+ * or misaligned workspace, BTO_ERR_CUDA for a failed launch. */
+bto_status bto_bicgk_mrhs_workspace_bytes(int64_t m, int64_t n, int64_t k, size_t *bytes);
+bto_status bto_bicgk_mrhs(int64_t m, int64_t n, int64_t k, const uint16_t *A, int64_t lda,
+                          const uint16_t *P, int64_t ldp, const uint16_t *R, int64_t ldr,
+                          float *Q, int64_t ldq, float *S, int64_t lds,
+                          void *ws, size_t ws_bytes, bto_stream_t stream);
+
 /* BICGK without a workspace argument (the paper has no counterpart; this is
  * a convenience of this library).  Some callers cannot call cudaMalloc: a
  * plugin whose host application owns all device memory through its own

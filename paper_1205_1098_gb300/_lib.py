@@ -44,6 +44,7 @@ SIGNATURES = {
     "bto_gemver_ex": "iiffkpipppppppipppzs",
     "bto_batch_prepare": "kpkpzs",
     "bto_batch_run": "pzs",
+    "bto_bicgk_mrhs": "iiipipipipipipzs",
 }
 _KIND = {"i": _c_i64, "u": _c_u64, "d": _c_f64, "f": ctypes.c_float, "p": _c_ptr, "z": _c_size,
          "s": _c_ptr, "k": _c_int}
@@ -89,6 +90,8 @@ def lib():
         L.bto_workspace_bytes.restype = _c_int
         L.bto_device_status.argtypes = [_c_ptr, _c_ptr, ctypes.POINTER(_c_int)]
         L.bto_device_status.restype = _c_int
+        L.bto_bicgk_mrhs_workspace_bytes.argtypes = [_c_i64, _c_i64, _c_i64, ctypes.POINTER(_c_size)]
+        L.bto_bicgk_mrhs_workspace_bytes.restype = _c_int
         _LIB = L
     return _LIB
 
@@ -173,6 +176,16 @@ def bto_workspace_bytes(op, form, m, n, a_type=BTO_F64):
     return out.value
 
 
+def bto_bicgk_mrhs_workspace_bytes(m, n, k):
+    """Workspace bytes of bto_bicgk_mrhs for an m x n A and k right-hand sides."""
+    out = _c_size(0)
+    L = lib()
+    st = L.bto_bicgk_mrhs_workspace_bytes(int(m), int(n), int(k), ctypes.byref(out))
+    if st != BTO_OK:
+        raise BtoError("bto_bicgk_mrhs_workspace_bytes", st, L.bto_last_invalid_arg())
+    return out.value
+
+
 def bto_device_status(ws, stream=None):
     out = _c_int(0)
     L = lib()
@@ -206,4 +219,5 @@ def bto_batch_workspace_bytes(descs, tile_cols=0):
 def exported_symbols():
     """Names the binding expects libbto.so to export."""
     return sorted(list(SIGNATURES) + ["bto_version", "bto_status_string", "bto_last_invalid_arg",
-                                      "bto_workspace_bytes", "bto_device_status"])
+                                      "bto_workspace_bytes", "bto_device_status",
+                                      "bto_bicgk_mrhs_workspace_bytes"])

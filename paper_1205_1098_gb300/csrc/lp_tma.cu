@@ -325,7 +325,8 @@ bto_status launch_t(const CUtensorMap& map, const LpArgs& a, int grid, cudaStrea
 }  // namespace
 
 bool encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, size_t esize, const void* base,
-                    int64_t rows, int64_t cols, int64_t ld, uint32_t box_rows, uint32_t box_cols) {
+                    int64_t rows, int64_t cols, int64_t ld, uint32_t box_rows, uint32_t box_cols,
+                    CUtensorMapSwizzle swizzle) {
     EncodeFn fn = encode_fn();
     if (!fn || rows <= 0 || cols <= 0) return false;
     if (!aligned16(base) || ((size_t)ld * esize) % 16 != 0) return false;
@@ -334,7 +335,7 @@ bool encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, size_t esize, c
     const cuuint32_t box[2] = {box_rows, box_cols};
     const cuuint32_t estr[2] = {1, 1};
     return fn(map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -71,6 +71,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// As tma_load_2d, with an L2 cache policy (createpolicy) for the source.
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, int x, int y,
+                                                 uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)),
+          "l"(policy)
+        : "memory");
+}
+
 // Named barrier over `count` threads (a subset of the block).
 __device__ __forceinline__ void named_bar(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
@@ -81,6 +92,18 @@ __device__ __forceinline__ void named_bar(int id, int count) {
 // esize and data type dtype, with a box of box_rows x box_cols.  Returns
 // false if the driver rejects it (alignment, strides) or is unavailable.
 bool encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, size_t esize, const void* base,
-                    int64_t rows, int64_t cols, int64_t ld, uint32_t box_rows, uint32_t box_cols);
+                    int64_t rows, int64_t cols, int64_t ld, uint32_t box_rows, uint32_t box_cols,
+                    CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_NONE);
+
+// Waits for the phase with the given parity, bounded by `limit_ns` only
+// (used to drain copies in flight after an abort).
+__device__ __forceinline__ bool mbar_wait_timed(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
 
 }  // namespace bto

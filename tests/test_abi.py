@@ -91,3 +91,28 @@ def test_validation_without_gpu(L):
     with pytest.raises(bto.BtoError) as e:
         bto.bto_fill_f64(0, 0, 7, 4, 4, 0, 4096, 4, 0)
     assert e.value.arg == 3
+
+
+def test_mrhs_validation_without_gpu(L):
+    # Multi-RHS BICGK: k outside 16..96 or not a multiple of 16, negative
+    # sizes, short leading dimensions, odd BF16 pointers and overlapping
+    # outputs are rejected before any CUDA call.
+    for k in (0, 8, 24, 112):
+        with pytest.raises(bto.BtoError) as e:
+            bto.bto_bicgk_mrhs(64, 64, k, 4096, 64, 8192, 64, 12288, 64, 16384, 64, 32768, 64, 0, 0, 0)
+        assert e.value.arg == 3
+        with pytest.raises(bto.BtoError) as e:
+            bto.bto_bicgk_mrhs_workspace_bytes(64, 64, k)
+        assert e.value.arg == 3
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_bicgk_mrhs(-1, 64, 16, 4096, 64, 8192, 64, 12288, 64, 16384, 64, 32768, 64, 0, 0, 0)
+    assert e.value.arg == 1
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_bicgk_mrhs(64, 64, 16, 4096, 63, 8192, 64, 12288, 64, 16384, 64, 32768, 64, 0, 0, 0)
+    assert e.value.arg == 5   # lda < m
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_bicgk_mrhs(64, 64, 16, 4097, 64, 8192, 64, 12288, 64, 16384, 64, 32768, 64, 0, 0, 0)
+    assert e.value.arg == 4   # A not 2-byte aligned
+    with pytest.raises(bto.BtoError) as e:   # Q overlaps S
+        bto.bto_bicgk_mrhs(64, 64, 16, 4096, 64, 8192, 64, 12288, 64, 16384, 64, 16384 + 64, 64, 0, 0, 0)
+    assert e.value.arg == 10

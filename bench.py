@@ -79,6 +79,16 @@ def flops(k, m, n, N):
             "vadd": 2 * N}[k]
 
 
+# DRAM bytes (read + write) per call, from one ncu capture (--set full) of the
+# same kernels at n = 8192 on a GB300; traffic grows with m n, so the bench
+# scales it to its own size.  Set to None for a kernel changed since then.
+NCU_TRAFFIC_N = 8192
+NCU_TRAFFIC = {
+    "gemver": (537.550080 + 492.885504) * 1e6 + (537.044992 + 8.623104) * 1e6,
+    "atax": (552.754432 + 3.620352) * 1e6,
+}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -705,16 +715,21 @@ def main():
     # Roofline of the dominant kernel (largest share of the step).
     dom = max(KERNELS, key=lambda k: kern[k])
     d = per[dom]
+    traffic = NCU_TRAFFIC.get(dom)
+    if traffic is not None:
+        traffic = round(traffic * (m * n) / NCU_TRAFFIC_N ** 2)
     if d["bound"] == "alu":
         roof = {"kernel": "bto_%s (all launches of one call)" % dom, "bound": "alu",
                 "achieved": d["fp64_tflops"], "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                "frac": d["fp64_frac"], "traffic": None,
+                "frac": d["fp64_frac"], "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read+write of the same launches at n=%d, scaled by m n"
+                                  % NCU_TRAFFIC_N,
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x %d SMs x %.0f MHz" % (sms, sm_max),
                 "hbm_frac_of_%s" % peak_src: d["hbm_frac"]}
     else:
         roof = {"kernel": "bto_%s (all launches of one call)" % dom, "bound": "hbm",
                 "achieved": d["gbs"], "peak": hbm, "unit": "GB/s", "frac": d["hbm_frac"],
-                "traffic": None, "peak_source": peak_src}
+                "traffic": traffic, "peak_source": peak_src}
 
     e2e = None
     if not args.no_e2e:

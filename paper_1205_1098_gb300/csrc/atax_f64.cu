@@ -1,31 +1,36 @@
 // ATAX / BATAX (Table I; Section II, Fig. 1): y <- beta A^T (A x), with the
-// temporary t = A x contracted and A read from device memory once.
+// temporary t = A x contracted (it never reaches device memory as a vector)
+// and A streamed from HBM once.
 //
 // The paper's Max-Fuse result for BATAX partitions the rows (p(i)), fuses
-// the two row loops, and keeps the two inner column loops apart because
-// t_i is complete only after its whole row has been summed (Section III-D,
-// Section IV-A).  On a GPU with column-major A the rows are the strided
-// direction, so the schedule here is a wavefront over row bands:
+// the two row loops, and keeps the two inner column loops apart because t_i
+// is complete only after its whole row has been summed (Section III-D,
+// Section IV-A).  Here a row band plays the role of the fused row loop:
 //
-//   - Block c of a cooperative grid (one block per SM) owns a fixed slice of
-//     columns, and therefore owns y_j for those columns outright: no
-//     cross-block reduction of y is ever needed.
-//   - Rows are processed in bands of TB rows.  For band b every block loads
-//     its TB x (slice) piece of A from device memory into shared memory
-//     (512-byte column segments for TB = 64), forming on the way its partial
-//     t over its columns.
-//   - The partial t of band b goes to a per-band slot; the block that
-//     arrives last (an atomic counter) adds the G partials in block order
-//     and publishes the complete t_b with a release flag.
-//   - Each block then sweeps its shared-memory copy of the band once more,
-//     y_j += sum_i A(i,j) t_i, with threads owning columns.  The band copy
-//     stays resident for nbuf-1 further bands, so the wait for t_b overlaps
-//     the loading of the next bands.
+//   - The cooperative grid (two blocks per SM, so that one block's
+//     arithmetic covers the other's barriers and waits) is cut into NG
+//     groups of S blocks (S = 16 for n <= 65536).  Group g takes the 16-row bands
+//     g, g + NG, g + 2 NG, ...; inside a group, block r owns a fixed slice
+//     of about n / S columns.
+//   - Pass 1 over band b (the first column loop): each thread sums its
+//     columns' 16-row segments (128 contiguous bytes per column) times x_j
+//     into 16 partial t_i; a warp butterfly and the warps, in a fixed order,
+//     give the block's partial of t_b; the S partials meet in a
+//     double-buffered slot in L2 behind per-block release flags, and every
+//     block adds them in rank order, so all blocks hold the same t_b.
+//   - Pass 2 over band b (the second column loop): y_j += sum_i A(i,j) t_i
+//     for the block's columns, re-reading the band while it is still in L2
+//     (two bands per group are in flight: about 80 MB at n = 16384), so HBM
+//     sees A once.
+//   - Pass 1 of band b+1 runs before the wait for t_b, so the exchange
+//     latency is hidden behind a band's worth of arithmetic.
+//   - Each group leaves a partial y over all n columns; a combine adds the NG
+//     partials in group order and scales by beta.
 //
 // Every wait is bounded (about two seconds of %globaltimer, or the limit a
 // test sets): on expiry the block writes BTO_ERR_TIMEOUT into the status
-// word at the start of the workspace and returns, and every other wait then
-// expires too; the host reads the word with bto_device_status.
+// word at the start of the workspace and returns, and the other blocks of
+// its group then expire too; the host reads the word with bto_device_status.
 #include "check.cuh"
 
 namespace bto {
@@ -34,25 +39,24 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int64_t kMaxSlice = 512;        // widest column slice per block
-constexpr int kYPerThread = kMaxSlice / kThreads;
-constexpr int kBatch = 8;             // column segments in flight per warp in phase 1
+constexpr int kTB = 16;                 // band height (rows)
+constexpr int kBlocksPerSM = 2;         // two blocks per SM: one computes while the other waits
+constexpr int kMinGroup = 16;           // blocks per group
+constexpr int64_t kMaxSlice = 4096;     // widest column slice per block (x, y slices in shared memory)
 
 struct AtaxArgs {
     int64_t m, n;
     const double* A; int64_t lda;
     const double* x;
-    double* y;
-    double beta;
-    unsigned* cnt;       // [nb] arrivals
-    unsigned* flag;      // [nb] band ready
-    double* tpart;       // [nb][G][TB]
-    double* tfull;       // [nb][TB]
+    unsigned* flag;      // [G] bands published by each block (sequence number within its group)
+    double* tslot;       // [NG][2][S][kTB] block partials of t
+    double* ypart;       // [NG][ldy] group partials of y
+    int64_t ldy;
     int* status;
-    int64_t nb;
-    int nbuf;
-    int64_t cstride;     // shared-memory column stride (TB + 1)
-    int64_t stall_band;  // fault injection: this band's flag is never published (-1: none)
+    int64_t nb;          // bands
+    int S, NG;
+    int64_t cmax;        // widest column slice
+    int64_t stall_band;  // fault injection: this band's rank-0 partial is never published (-1: none)
     unsigned long long timeout_ns;
 };
 
@@ -74,176 +78,163 @@ __device__ __host__ __forceinline__ int64_t split_at(int64_t n, int64_t parts, i
     return (n / parts) * b + ((n % parts) * b) / parts;
 }
 
-template <int TB, bool VEC2>
-__global__ void __launch_bounds__(kThreads, 1) atax_kernel(const AtaxArgs a) {
-    constexpr int RPL = TB / 32;   // rows per lane in phase 1 (1 or 2)
-    extern __shared__ double sm[];
-    const int G = gridDim.x, c = blockIdx.x;
-    const int64_t c0 = split_at(a.n, G, c), c1 = split_at(a.n, G, c + 1);
-    const int nc = (int)(c1 - c0);
-    const int64_t cmax = (a.n + G - 1) / G;
-    double* bufs = sm;                                   // [nbuf][cmax][cstride]
-    double* tred = bufs + (int64_t)a.nbuf * cmax * a.cstride;   // [kWarps][TB]
-    double* ts = tred + kWarps * TB;                     // [TB]
-    double* rsum = ts + TB;                              // [kThreads] last-arriver scratch
-    __shared__ int s_last, s_abort;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    double yacc[kYPerThread];
+// The 16 values of a column segment starting at row R0 (rows past m read as 0).
+template <bool VEC2>
+__device__ __forceinline__ void load_seg(const double* col, bool whole, int rows, double (&v)[kTB]) {
+    if (VEC2 && whole) {
 #pragma unroll
-    for (int k = 0; k < kYPerThread; k++) yacc[k] = 0.0;
+        for (int i = 0; i < kTB; i += 2) {
+            const double2 t = __ldg(reinterpret_cast<const double2*>(col + i));
+            v[i] = t.x;
+            v[i + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kTB; i++) v[i] = i < rows ? __ldg(col + i) : 0.0;
+    }
+}
+
+// Sums tp[16] over the 32 lanes of a warp by halving exchanges; afterwards
+// lane l holds the warp's sum for row l >> 1 (lanes 2k and 2k+1 agree).
+__device__ __forceinline__ double warp_reduce16(double (&tp)[kTB], int lane) {
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+        const bool upper = (lane & (2 * h)) != 0;      // this lane keeps rows [h, 2h) of each 2h-group
+#pragma unroll
+        for (int i = 0; i < h; i++) {
+            const double send = upper ? tp[i] : tp[i + h];
+            const double recv = __shfl_xor_sync(0xffffffffu, send, 2 * h);
+            tp[i] = (upper ? tp[i + h] : tp[i]) + recv;
+        }
+    }
+    return tp[0] + __shfl_xor_sync(0xffffffffu, tp[0], 1);
+}
+
+template <bool VEC2>
+__global__ void __launch_bounds__(kThreads, kBlocksPerSM) atax_kernel(const AtaxArgs a) {
+    extern __shared__ double sm[];
+    double* xs = sm;                         // [cmax] x over this block's columns
+    double* ys = xs + a.cmax;                // [cmax] y accumulators
+    __shared__ double red[kWarps][kTB];
+    __shared__ double tnext[kTB], ts[kTB];
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x / a.S, r = blockIdx.x % a.S;
+    const int64_t c0 = split_at(a.n, a.S, r), c1 = split_at(a.n, a.S, r + 1);
+    const int nc = (int)(c1 - c0);
+    const int64_t Q = g < a.nb ? (a.nb - g + a.NG - 1) / a.NG : 0;   // bands of this group
+    const bool vec_ok = VEC2;
+
+    for (int jl = threadIdx.x; jl < nc; jl += kThreads) {
+        xs[jl] = __ldg(a.x + c0 + jl);
+        ys[jl] = 0.0;
+    }
     if (threadIdx.x == 0) s_abort = 0;
     __syncthreads();
 
-    const int D = a.nbuf - 1;
-    for (int64_t b = 0; b < a.nb + D; b++) {
-        // ---------------- phase 1: load band b, partial t over this block's columns
-        if (b < a.nb) {
-            const int64_t R0 = b * TB, rend = min(a.m, R0 + TB);
-            double* buf = bufs + (b % a.nbuf) * cmax * a.cstride;
-            double tp[RPL];
+    // Pass 1 over the q-th band of the group: the block's partial t in tnext.
+    auto pass1 = [&](int64_t q) {
+        const int64_t R0 = (g + q * a.NG) * kTB;
+        const int rows = (int)(a.m - R0 < kTB ? a.m - R0 : kTB);
+        const bool whole = rows == kTB;
+        double tp[kTB];
 #pragma unroll
-            for (int k = 0; k < RPL; k++) tp[k] = 0.0;
-            // Columns jl = warp + kWarps*u, in batches of kBatch per warp, so each
-            // warp has kBatch column segments in flight before it consumes any.
-            for (int jb = warp; jb < nc; jb += kWarps * kBatch) {
-                double v[kBatch][RPL], xj[kBatch];
+        for (int i = 0; i < kTB; i++) tp[i] = 0.0;
+#pragma unroll 2
+        for (int jl = threadIdx.x; jl < nc; jl += kThreads) {
+            double v[kTB];
+            load_seg<VEC2>(a.A + (c0 + jl) * a.lda + R0, whole && vec_ok, rows, v);
+            const double xj = xs[jl];
 #pragma unroll
-                for (int u = 0; u < kBatch; u++) {
-                    const int jl = jb + u * kWarps;
-                    xj[u] = 0.0;
-#pragma unroll
-                    for (int k = 0; k < RPL; k++) v[u][k] = 0.0;
-                    if (jl < nc) {
-                        const double* col = a.A + (c0 + jl) * a.lda;
-                        xj[u] = __ldg(a.x + c0 + jl);
-                        if (RPL == 2) {
-                            const int64_t i = R0 + 2 * lane;
-                            if (VEC2 && i + 1 < rend) {
-                                double2 t = __ldg(reinterpret_cast<const double2*>(col + i));
-                                v[u][0] = t.x; v[u][RPL - 1] = t.y;
-                            } else {
-                                if (i < rend) v[u][0] = __ldg(col + i);
-                                if (i + 1 < rend) v[u][RPL - 1] = __ldg(col + i + 1);
-                            }
-                        } else {
-                            const int64_t i = R0 + lane;
-                            if (i < rend) v[u][0] = __ldg(col + i);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kBatch; u++) {
-                    const int jl = jb + u * kWarps;
-                    if (jl < nc) {
-#pragma unroll
-                        for (int k = 0; k < RPL; k++) {
-                            tp[k] = fma(v[u][k], xj[u], tp[k]);
-                            buf[jl * a.cstride + RPL * lane + k] = v[u][k];
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < RPL; k++) tred[warp * TB + RPL * lane + k] = tp[k];
-            __syncthreads();
-            if (threadIdx.x < TB) {
-                double s = tred[threadIdx.x];
-#pragma unroll
-                for (int w = 1; w < kWarps; w++) s += tred[w * TB + threadIdx.x];
-                a.tpart[(b * G + c) * TB + threadIdx.x] = s;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                // The barrier orders the block's partial stores before this
-                // fence; fence + atomic form the release of this band's partial.
-                __threadfence();
-                const unsigned old = atomicAdd(a.cnt + b, 1u);
-                s_last = (old == (unsigned)(G - 1));
-            }
-            __syncthreads();
-            if (s_last) {
-                // Last arrival: t_b = sum over blocks in block order.  Threads
-                // split the blocks into kThreads/TB strided groups; the group
-                // sums are then added in group order.
-                __threadfence();
-                constexpr int P = kThreads / TB;
-                const int row = threadIdx.x % TB, part = threadIdx.x / TB;
-                // Eight independent accumulators keep eight loads in flight.
-                double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-                int cc = part;
-                for (; cc + 7 * P < G; cc += 8 * P) {
-#pragma unroll
-                    for (int u = 0; u < 8; u++) acc[u] += __ldcg(a.tpart + (b * G + cc + u * P) * TB + row);
-                }
-                for (int u = 0; cc < G; cc += P, u++) acc[u] += __ldcg(a.tpart + (b * G + cc) * TB + row);
-                rsum[threadIdx.x] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-                __syncthreads();
-                if (threadIdx.x < TB) {
-                    double t = rsum[threadIdx.x];
-#pragma unroll
-                    for (int p = 1; p < P; p++) t += rsum[p * TB + threadIdx.x];
-                    a.tfull[b * TB + threadIdx.x] = t;
-                }
-                __syncthreads();
-                if (threadIdx.x == 0 && b != a.stall_band) {
-                    __threadfence();
-                    st_release(a.flag + b, 1u);
-                }
-            }
+            for (int i = 0; i < kTB; i++) tp[i] = fma(v[i], xj, tp[i]);
         }
-        // ---------------- phase 2: y += A_band^T t_band for band b - D
-        const int64_t bb = b - D;
-        if (bb >= 0) {
-            if (threadIdx.x == 0) {
-                const unsigned long long t0 = globaltimer();
-                while (ld_acquire(a.flag + bb) == 0u) {
+        const double w = warp_reduce16(tp, lane);
+        if ((lane & 1) == 0) red[warp][lane >> 1] = w;
+        __syncthreads();
+        if (threadIdx.x < kTB) {
+            double t = red[0][threadIdx.x];
+#pragma unroll
+            for (int k = 1; k < kWarps; k++) t += red[k][threadIdx.x];
+            tnext[threadIdx.x] = t;
+        }
+        __syncthreads();
+    };
+    // Publishes tnext as this block's partial of the group's q-th band.
+    auto publish = [&](int64_t q) {
+        double* slot = a.tslot + (((int64_t)g * 2 + (q & 1)) * a.S + r) * kTB;
+        if (threadIdx.x < kTB) slot[threadIdx.x] = tnext[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0 && !(r == 0 && g + q * a.NG == a.stall_band)) {
+            // The barrier orders the partial's stores before the fence; fence +
+            // release store publish it.
+            __threadfence();
+            st_release(a.flag + blockIdx.x, (unsigned)(q + 1));
+        }
+    };
+    // Waits for the group's S partials of its q-th band; ts = their sum in rank order.
+    auto gather = [&](int64_t q) -> bool {
+        if (threadIdx.x == 0) {
+            const unsigned long long t0 = globaltimer();
+            for (int rr = 0; rr < a.S && !s_abort; rr++) {
+                const unsigned* f = a.flag + (int64_t)g * a.S + rr;
+                while (ld_acquire(f) < (unsigned)(q + 1)) {
                     if (globaltimer() - t0 > a.timeout_ns) {
                         atomicExch(a.status, (int)BTO_ERR_TIMEOUT);
                         s_abort = 1;
                         break;
                     }
-                    __nanosleep(200);
+                    __nanosleep(64);
                 }
             }
-            __syncthreads();
-            if (s_abort) return;
-            const int64_t R0 = bb * TB;
-            if (threadIdx.x < TB)
-                ts[threadIdx.x] = (R0 + threadIdx.x < a.m) ? __ldcg(a.tfull + bb * TB + threadIdx.x) : 0.0;
-            __syncthreads();
-            const double* buf = bufs + (bb % a.nbuf) * cmax * a.cstride;
-#pragma unroll
-            for (int k = 0; k < kYPerThread; k++) {
-                const int jl = threadIdx.x + k * kThreads;
-                if (jl < nc) {
-                    // Two interleaved chains (even and odd rows), added in a fixed order.
-                    double e0 = 0.0, e1 = 0.0;
-                    const double* colbuf = buf + jl * a.cstride;
-#pragma unroll 16
-                    for (int i = 0; i < TB; i += 2) {
-                        e0 = fma(colbuf[i], ts[i], e0);
-                        e1 = fma(colbuf[i + 1], ts[i + 1], e1);
-                    }
-                    yacc[k] += e0 + e1;
-                }
-            }
-            __syncthreads();
         }
-    }
+        __syncthreads();
+        if (s_abort) return false;
+        if (threadIdx.x < kTB) {
+            const double* slot = a.tslot + ((int64_t)g * 2 + (q & 1)) * a.S * kTB;
+            double t = __ldcg(slot + threadIdx.x);
+            for (int rr = 1; rr < a.S; rr++) t += __ldcg(slot + rr * kTB + threadIdx.x);
+            ts[threadIdx.x] = t;
+        }
+        __syncthreads();
+        return true;
+    };
+    // Pass 2 over the q-th band: y_j += sum_i A(i,j) t_i.
+    auto pass2 = [&](int64_t q) {
+        const int64_t R0 = (g + q * a.NG) * kTB;
+        const int rows = (int)(a.m - R0 < kTB ? a.m - R0 : kTB);
+        const bool whole = rows == kTB;
+#pragma unroll 2
+        for (int jl = threadIdx.x; jl < nc; jl += kThreads) {
+            double v[kTB];
+            load_seg<VEC2>(a.A + (c0 + jl) * a.lda + R0, whole && vec_ok, rows, v);
+            double e0 = 0.0, e1 = 0.0;
 #pragma unroll
-    for (int k = 0; k < kYPerThread; k++) {
-        const int jl = threadIdx.x + k * kThreads;
-        if (jl < nc) a.y[c0 + jl] = a.beta * yacc[k];
+            for (int i = 0; i < kTB; i += 2) {
+                e0 = fma(v[i], ts[i], e0);
+                e1 = fma(v[i + 1], ts[i + 1], e1);
+            }
+            ys[jl] += e0 + e1;
+        }
+    };
+
+    if (Q > 0) {
+        pass1(0);
+        publish(0);
     }
+    for (int64_t q = 0; q < Q; q++) {
+        if (q + 1 < Q) pass1(q + 1);
+        if (!gather(q)) return;
+        if (q + 1 < Q) publish(q + 1);
+        pass2(q);
+    }
+    __syncthreads();
+    for (int jl = threadIdx.x; jl < nc; jl += kThreads) a.ypart[(int64_t)g * a.ldy + c0 + jl] = ys[jl];
 }
 
-size_t atax_smem(int TB, int nbuf, int64_t cmax) {
-    return ((size_t)nbuf * cmax * (TB + 1) + (size_t)kWarps * TB + TB + kThreads) * sizeof(double);
-}
+size_t atax_smem(int64_t cmax) { return (size_t)2 * cmax * sizeof(double); }
 
-template <int TB, bool VEC2>
-void* atax_fn() { return (void*)atax_kernel<TB, VEC2>; }
+template <bool VEC2>
+void* atax_fn() { return (void*)atax_kernel<VEC2>; }
 
 }  // namespace
 
@@ -252,31 +243,23 @@ AtaxPlan atax_plan(int64_t m, int64_t n, const DeviceInfo& d) {
     p.G = d.sms;
     if (m <= 0 || n <= 0) { p.fused = true; return p; }
     if (!d.coop) return p;
-    // One block per SM: more blocks per band multiply the partials the last
-    // arrival must add, which costs more than the overlap they bring.
-    const int cand[4][2] = {{64, 3}, {64, 2}, {32, 3}, {32, 2}};
-    for (int per_sm = 1; per_sm >= 1; per_sm--) {
-        const int64_t G = (int64_t)d.sms * per_sm;
-        const int64_t cmax = ceil_div(n, G);
-        if (cmax > kMaxSlice) continue;
-        const size_t limit = ((size_t)d.max_smem_optin - 2048) / per_sm;
-        for (auto& cd : cand) {
-            const size_t sz = atax_smem(cd[0], cd[1], cmax);
-            if (sz > limit) continue;
-            void* fn = cd[0] == 64 ? atax_fn<64, true>() : atax_fn<32, false>();
-            int occ = 0;
-            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, sz) != cudaSuccess) {
-                cudaGetLastError();
-                continue;
-            }
-            if (occ < per_sm) continue;
-            p.G = (int)G; p.cmax = cmax; p.TB = cd[0]; p.nbuf = cd[1]; p.smem = sz;
-            p.nb = ceil_div(m, p.TB);
-            p.fused = true;
-            return p;
-        }
+    const int S = (int)std::max<int64_t>(kMinGroup, ceil_div(n, kMaxSlice));
+    const int NG = d.sms * kBlocksPerSM / S;
+    if (NG < 1) return p;
+    const int64_t cmax = ceil_div(n, S);
+    const size_t sz = atax_smem(cmax);
+    void* fn = atax_fn<true>();
+    int occ = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sz) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, sz) != cudaSuccess) {
+        cudaGetLastError();
+        return p;
     }
+    if (occ < kBlocksPerSM) return p;
+    p.G = NG * S; p.S = S; p.NG = NG; p.cmax = cmax; p.TB = kTB; p.smem = sz;
+    p.nb = ceil_div(m, kTB);
+    p.ldy = round_up(n, 32);
+    p.fused = true;
     return p;
 }
 
@@ -331,21 +314,20 @@ bto_status atax_impl(int64_t m, int64_t n, double beta, const double* A, int64_t
         CombineJob jy = {y, n, a.spart, pl.lds, pl.NR, beta, nullptr, 0, 0, 0.0, nullptr, 0.0};
         return launch_combine(&jy, 1, st);
     }
-    // Zero the status word, the counters and the flags.
-    if (cudaMemsetAsync(w, 0, L.off[0] + 2 * ap.nb * sizeof(unsigned), st) != cudaSuccess)
+    // Zero the status word and the per-block flags.
+    if (cudaMemsetAsync(w, 0, L.off[0] + (size_t)ap.G * sizeof(unsigned), st) != cudaSuccess)
         return BTO_ERR_CUDA;
     AtaxArgs a{};
-    a.m = m; a.n = n; a.A = A; a.lda = lda; a.x = x; a.y = y; a.beta = beta;
-    a.cnt = reinterpret_cast<unsigned*>(w + L.off[0]);
-    a.flag = a.cnt + ap.nb;
-    a.tpart = reinterpret_cast<double*>(w + L.off[1]);
-    a.tfull = reinterpret_cast<double*>(w + L.off[2]);
+    a.m = m; a.n = n; a.A = A; a.lda = lda; a.x = x;
+    a.flag = reinterpret_cast<unsigned*>(w + L.off[0]);
+    a.tslot = reinterpret_cast<double*>(w + L.off[1]);
+    a.ypart = reinterpret_cast<double*>(w + L.off[2]);
+    a.ldy = ap.ldy;
     a.status = reinterpret_cast<int*>(w);
-    a.nb = ap.nb; a.nbuf = ap.nbuf; a.cstride = ap.TB + 1;
+    a.nb = ap.nb; a.S = ap.S; a.NG = ap.NG; a.cmax = ap.cmax;
     a.stall_band = stall_band; a.timeout_ns = timeout_ns;
     const bool vec2 = aligned16(A) && (lda % 2 == 0);
-    void* fn = ap.TB == 64 ? (vec2 ? atax_fn<64, true>() : atax_fn<64, false>())
-                           : atax_fn<32, false>();
+    void* fn = vec2 ? atax_fn<true>() : atax_fn<false>();
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ap.smem) != cudaSuccess)
         return BTO_ERR_CUDA;
     int occ = 0;
@@ -355,7 +337,9 @@ bto_status atax_impl(int64_t m, int64_t n, double beta, const double* A, int64_t
     void* args[] = {(void*)&a};
     if (cudaLaunchCooperativeKernel(fn, dim3(ap.G), dim3(kThreads), args, ap.smem, st) != cudaSuccess)
         return BTO_ERR_CUDA;
-    return BTO_OK;
+    // y = beta * (sum of the group partials, in group order).
+    CombineJob jy = {y, n, a.ypart, ap.ldy, ap.NG, beta, nullptr, 0, 0, 0.0, nullptr, 0.0};
+    return launch_combine(&jy, 1, st);
 }
 
 }  // namespace

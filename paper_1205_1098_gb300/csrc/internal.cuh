@@ -124,11 +124,13 @@ bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, cudaStream_t
 // Rows are cut into bands of TB rows; block c of a cooperative grid of G
 // blocks owns a fixed slice of columns (so it owns those entries of y).
 struct AtaxPlan {
-    int G = 0;          // blocks (one per SM)
+    int G = 0;          // blocks (one per SM, a multiple of S)
+    int S = 0;          // blocks per group
+    int NG = 0;         // groups
     int TB = 0;         // band height (rows)
-    int nbuf = 0;       // band slices resident in shared memory
     int64_t nb = 0;     // number of bands
     int64_t cmax = 0;   // widest column slice
+    int64_t ldy = 0;    // leading dimension of the group partials of y
     size_t smem = 0;    // dynamic shared memory per block
     bool fused = false; // false: the slices do not fit; the two-pass form runs
 };

@@ -44,9 +44,9 @@ bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type, const D
             if (form == BTO_FORM_FUSED) {
                 const AtaxPlan ap = atax_plan(m, n, d);
                 if (ap.fused) {
-                    L.off[0] = region(cur, (size_t)2 * ap.nb * sizeof(unsigned));          // counters, flags
-                    L.off[1] = region(cur, (size_t)ap.nb * ap.G * ap.TB * sizeof(double)); // block partials of t
-                    L.off[2] = region(cur, (size_t)ap.nb * ap.TB * sizeof(double));        // t per band
+                    L.off[0] = region(cur, (size_t)std::max(ap.G, 1) * sizeof(unsigned));             // per-block flags
+                    L.off[1] = region(cur, (size_t)ap.NG * 2 * ap.S * ap.TB * sizeof(double));       // t partial slots
+                    L.off[2] = region(cur, (size_t)ap.NG * std::max<int64_t>(ap.ldy, 1) * sizeof(double)); // y partials
                     break;
                 }
             }

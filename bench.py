@@ -615,6 +615,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-only", type=float, default=0.0, help="profiling runs: only serving, for this many s")
     ap.add_argument("--batched-only", action="store_true", help="profiling runs: only the batched form")
+    ap.add_argument("--batched-count", type=int, default=4096, help="instances in the batched form")
     ap.add_argument("--mrhs-only", type=int, default=0, help="profiling runs: only multi-RHS BICGK with this k")
     ap.add_argument("--no-mrhs", action="store_true")
     ap.add_argument("--precision-only", type=int, default=0,
@@ -640,7 +641,7 @@ def main():
         build.build()
         import paper_1205_1098_gb300 as bto
         hbm, _, _ = load_peaks()
-        print(json.dumps({"batched_form": batched_form(torch, bto, hbm, args.steps)}))
+        print(json.dumps({"batched_form": batched_form(torch, bto, hbm, args.steps, count=args.batched_count)}))
         return
     if args.mrhs_only:
         import torch

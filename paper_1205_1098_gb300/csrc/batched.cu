@@ -154,6 +154,55 @@ __device__ __forceinline__ void store8(TA* col, int64_t R0, int64_t m, int lane,
     }
 }
 
+// ---------------------------------------------------------------- copy ring
+// Matrices whose columns allow 16-byte copies stream through a per-warp ring
+// of kStages batches in shared memory, filled with cp.async kStages - 1
+// batches ahead of use (about 12 KB in flight per warp instead of the 4 KB a
+// register prefetch can hold).  A batch is up to kBatchCols column slots of
+// one 256-row chunk.  Each lane copies, and later reads, only its own rows
+// of every slot (the chunks brow() gives it), so a lane's own
+// cp.async.wait_group orders its copies before its reads: no barrier is
+// needed.  Rows past m are zero-filled by the copy.
+constexpr int kStages = 4;
+constexpr int kBatchCols = 4;
+constexpr int kMaxTile = 1024;     // widest column panel (tile_cols)
+
+template <typename TA>
+constexpr int ring_elems() { return kStages * kBatchCols * kRows; }
+
+__device__ __forceinline__ void cp16_zfill(void* dst, const void* src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_ring() { asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 2) : "memory"); }
+
+// The lane's 8 rows of column `col` (chunk rows R0 .. R0+255) into a 256-row slot.
+template <typename TA>
+__device__ __forceinline__ void cp_col(TA* slot, const TA* col, int64_t R0, int64_t m, int lane) {
+    constexpr int V = 16 / sizeof(TA);
+#pragma unroll
+    for (int h = 0; h < 8 / V; h++) {
+        const int r = brow<TA>(lane, h * V);
+        const int64_t i = R0 + r;
+        const int64_t left = m - i;
+        const int valid = left <= 0 ? 0 : (left >= V ? V : (int)left);
+        cp16_zfill(slot + r, valid > 0 ? (const void*)(col + i) : (const void*)col, valid * (int)sizeof(TA));
+    }
+}
+
+// The lane's 8 rows of a slot, as FP32.
+template <typename TA>
+__device__ __forceinline__ void read_col(const TA* slot, int lane, float (&a)[8]) {
+    constexpr int V = 16 / sizeof(TA);
+#pragma unroll
+    for (int h = 0; h < 8 / V; h++) {
+        const uint4 t = *reinterpret_cast<const uint4*>(slot + brow<TA>(lane, h * V));
+#pragma unroll
+        for (int q = 0; q < V; q++) a[h * V + q] = unpack<TA>(t, q);
+    }
+}
+
 template <typename TA, bool COHERENT>
 __device__ __forceinline__ void load_rows(const float* v, int64_t R0, int64_t m, int lane, float (&o)[8]) {
 #pragma unroll
@@ -202,7 +251,8 @@ __device__ __forceinline__ void fold(float (&hi)[8], float (&lo)[8], float (&t)[
 //   IT_GESUMMV : row partials of A x and B x.
 template <int KIND, typename TA>
 __device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstInfo& info, int panel, int64_t c0, int64_t c1,
-                           float* red, float* red2, float* shi, float* slo, float2* qpart, const float* tbuf) {
+                           float* red, float* red2, float* shi, float* slo, float2* qpart, const float* tbuf,
+                           TA* ring) {
     constexpr bool HAS_Q = (KIND == IT_BICGK || KIND == IT_GESUMMV);
     constexpr bool HAS_S = (KIND == IT_BICGK || KIND == IT_GEMVER1 || KIND == IT_ATAX2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -214,6 +264,32 @@ __device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstIn
     const float* xin = d.in[0];
     for (int k = threadIdx.x; k < ncols; k += kThreads) { shi[k] = 0.0f; slo[k] = 0.0f; }
     __syncthreads();
+    // Columns loaded ahead of use: four (two for GESUMMV, which loads two matrices).
+    constexpr int KU = KIND == IT_GESUMMV ? 2 : 4;
+    // Copy-ring schedule: batch = (chunk, warp group, step of KU columns), in loop order.
+    const int ngw = ncols > 16 * warp ? (int)((ncols - 16 * warp + 16 * kWarps - 1) / (16 * kWarps)) : 0;
+    const int nbat = vec ? (int)((m + kRows - 1) / kRows) * ngw * (16 / KU) : 0;
+    int bi = 0, iss = 0, ic = 0, ig = 0, ij = 0;
+    auto issue = [&]() {
+        if (iss < nbat) {
+            const int64_t R0i = (int64_t)ic * kRows, g0i = c0 + 16 * warp + 16 * kWarps * ig;
+            const int nci = (int)((c1 - g0i) < 16 ? (c1 - g0i) : 16);
+            TA* st = ring + (iss % kStages) * (kBatchCols * kRows);
+#pragma unroll
+            for (int u = 0; u < KU; u++) {
+                const int jj = KU * ij + u;
+                if (jj < nci) {
+                    cp_col<TA>(st + u * kRows, A + (g0i + jj) * d.lda, R0i, m, lane);
+                    if (KIND == IT_GESUMMV) cp_col<TA>(st + (KU + u) * kRows, B2 + (g0i + jj) * d.ldb, R0i, m, lane);
+                }
+            }
+            if (++ij == 16 / KU) { ij = 0; if (++ig == ngw) { ig = 0; ++ic; } }
+        }
+        cp_commit();
+        iss++;
+    };
+    if (vec)
+        for (int k = 0; k < kStages - 1; k++) issue();
     for (int64_t R0 = 0; R0 < m; R0 += kRows) {
         float rv[8], u1r[8], u2r[8], qhi[8], qlo[8], q2hi[8], q2lo[8];
         if (KIND == IT_BICGK) load_rows<TA, false>(d.in[1], R0, m, lane, rv);
@@ -230,17 +306,29 @@ __device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstIn
             float sl[16], qt[8], q2t[8];
 #pragma unroll
             for (int k = 0; k < 8; k++) { qt[k] = 0.0f; q2t[k] = 0.0f; }
-            // Columns loaded ahead of use: four (two for GESUMMV, which loads two matrices).
-            constexpr int KU = KIND == IT_GESUMMV ? 2 : 4;
 #pragma unroll
             for (int jb = 0; jb < 16; jb += KU) {
                 float av[KU][8], bv[KU][8];
+                if (vec) {
+                    // Batch bi is in the ring once at most kStages - 2 newer batches are pending.
+                    cp_wait_ring();
+                    const TA* st = ring + (bi % kStages) * (kBatchCols * kRows);
 #pragma unroll
-                for (int u = 0; u < KU; u++)
-                    if (jb + u < nc) {
-                        load8<TA, false>(A + (g0 + jb + u) * d.lda, R0, m, lane, vec, av[u]);
-                        if (KIND == IT_GESUMMV) load8<TA, false>(B2 + (g0 + jb + u) * d.ldb, R0, m, lane, vec, bv[u]);
-                    }
+                    for (int u = 0; u < KU; u++)
+                        if (jb + u < nc) {
+                            read_col<TA>(st + u * kRows, lane, av[u]);
+                            if (KIND == IT_GESUMMV) read_col<TA>(st + (KU + u) * kRows, lane, bv[u]);
+                        }
+                    bi++;
+                    issue();     // refills the slot of batch bi - 1, read in the previous step
+                } else {
+#pragma unroll
+                    for (int u = 0; u < KU; u++)
+                        if (jb + u < nc) {
+                            load8<TA, false>(A + (g0 + jb + u) * d.lda, R0, m, lane, vec, av[u]);
+                            if (KIND == IT_GESUMMV) load8<TA, false>(B2 + (g0 + jb + u) * d.ldb, R0, m, lane, vec, bv[u]);
+                        }
+                }
 #pragma unroll
                 for (int u = 0; u < KU; u++) {
                     const int jj = jb + u;
@@ -329,7 +417,8 @@ __device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstIn
 //   IT_GEMVER2 : w = alpha B x (B and x written by stage one: coherent loads).
 //   IT_ATAX1   : t = A x into the workspace.
 template <int KIND, typename TA>
-__device__ __forceinline__ void row_item(const bto_batch_desc& d, const InstInfo& info, int64_t R0, float* red, float* tbuf) {
+__device__ __forceinline__ void row_item(const bto_batch_desc& d, const InstInfo& info, int64_t R0, float* red, float* tbuf,
+                                         TA* ring) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t m = d.m, n = d.n;
     const bool vec = info.vec != 0;
@@ -339,17 +428,51 @@ __device__ __forceinline__ void row_item(const bto_batch_desc& d, const InstInfo
     float qhi[8], qlo[8], qt[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) { qhi[k] = 0.0f; qlo[k] = 0.0f; qt[k] = 0.0f; }
+    // Copy-ring schedule (see cp_col): batch = (warp group, step of 4 columns).
+    // cp.async.cg reads through L2, so GEMVER's B written by stage one is seen.
+    const int ngw = n > 16 * warp ? (int)((n - 16 * warp + 16 * kWarps - 1) / (16 * kWarps)) : 0;
+    const int nbat = vec ? ngw * 4 : 0;
+    int bi = 0, iss = 0;
+    auto issue = [&]() {
+        if (iss < nbat) {
+            const int64_t g0i = 16 * warp + 16 * kWarps * (iss >> 2);
+            const int nci = (int)((n - g0i) < 16 ? (n - g0i) : 16);
+            TA* st = ring + (iss % kStages) * (kBatchCols * kRows);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int jj = 4 * (iss & 3) + u;
+                if (jj < nci) cp_col<TA>(st + u * kRows, M + (g0i + jj) * ld, R0, m, lane);
+            }
+        }
+        cp_commit();
+        iss++;
+    };
+    if (vec)
+        for (int k = 0; k < kStages - 1; k++) issue();
     for (int64_t g0 = 16 * warp; g0 < n; g0 += 16 * kWarps) {
         const int nc = (int)((n - g0) < 16 ? (n - g0) : 16);
 #pragma unroll
         for (int jb = 0; jb < 16; jb += 4) {
             float av[4][8], xj[4];
+            if (vec) {
+                cp_wait_ring();
+                const TA* st = ring + (bi % kStages) * (kBatchCols * kRows);
 #pragma unroll
-            for (int u = 0; u < 4; u++)
-                if (jb + u < nc) {
-                    load8<TA, KIND == IT_GEMVER2>(M + (g0 + jb + u) * ld, R0, m, lane, vec, av[u]);
-                    xj[u] = KIND == IT_GEMVER2 ? __ldcg(v + g0 + jb + u) : __ldg(v + g0 + jb + u);
-                }
+                for (int u = 0; u < 4; u++)
+                    if (jb + u < nc) {
+                        read_col<TA>(st + u * kRows, lane, av[u]);
+                        xj[u] = KIND == IT_GEMVER2 ? __ldcg(v + g0 + jb + u) : __ldg(v + g0 + jb + u);
+                    }
+                bi++;
+                issue();
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (jb + u < nc) {
+                        load8<TA, KIND == IT_GEMVER2>(M + (g0 + jb + u) * ld, R0, m, lane, vec, av[u]);
+                        xj[u] = KIND == IT_GEMVER2 ? __ldcg(v + g0 + jb + u) : __ldg(v + g0 + jb + u);
+                    }
+            }
 #pragma unroll
             for (int u = 0; u < 4; u++)
                 if (jb + u < nc) {
@@ -379,19 +502,19 @@ __host__ __device__ inline int family_of(int kind) {
 
 template <typename TA, int FAM>
 __device__ void run_item(const Item& item, const bto_batch_desc& d, const InstInfo& info, int tile_cols,
-                         float* red, float* red2, float* shi, float* slo, float2* qpart, float* tbuf) {
+                         float* red, float* red2, float* shi, float* slo, float2* qpart, float* tbuf, TA* ring) {
     const int panel = tile_cols ? (int)(item.lo / tile_cols) : 0;
     if (FAM == 0) {
         switch (item.kind) {
-            case IT_BICGK: panel_item<IT_BICGK, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf); break;
-            case IT_GEMVER1: panel_item<IT_GEMVER1, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf); break;
-            case IT_GEMVER2: row_item<IT_GEMVER2, TA>(d, info, item.lo, red, tbuf); break;
+            case IT_BICGK: panel_item<IT_BICGK, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf, ring); break;
+            case IT_GEMVER1: panel_item<IT_GEMVER1, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf, ring); break;
+            case IT_GEMVER2: row_item<IT_GEMVER2, TA>(d, info, item.lo, red, tbuf, ring); break;
         }
     } else {
         switch (item.kind) {
-            case IT_ATAX2: panel_item<IT_ATAX2, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf); break;
-            case IT_GESUMMV: panel_item<IT_GESUMMV, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf); break;
-            case IT_ATAX1: row_item<IT_ATAX1, TA>(d, info, item.lo, red, tbuf); break;
+            case IT_ATAX2: panel_item<IT_ATAX2, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf, ring); break;
+            case IT_GESUMMV: panel_item<IT_GESUMMV, TA>(d, info, panel, item.lo, item.hi, red, red2, shi, slo, qpart, tbuf, ring); break;
+            case IT_ATAX1: row_item<IT_ATAX1, TA>(d, info, item.lo, red, tbuf, ring); break;
         }
     }
 }
@@ -412,6 +535,8 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(char* ws) {
     float* red2 = sm + 2 * kWarps * kRows;
     float* shi = red2 + 2 * kWarps * kRows;
     float* slo = shi + h->tile_cols;
+    // This warp's copy ring, after the fixed regions (16-byte aligned).
+    TA* ring = reinterpret_cast<TA*>(sm + 4 * kWarps * kRows + 2 * kMaxTile) + (threadIdx.x >> 5) * ring_elems<TA>();
     __shared__ int s_item, s_ok, s_last;
     const int nitems = h->qstart[Q + 1] - h->qstart[Q];
     while (true) {
@@ -436,7 +561,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(char* ws) {
             }
             __syncthreads();
         }
-        if (!stage2 || s_ok) run_item<TA, FAM>(item, d, info, h->tile_cols, red, red2, shi, slo, qpart, tbuf);
+        if (!stage2 || s_ok) run_item<TA, FAM>(item, d, info, h->tile_cols, red, red2, shi, slo, qpart, tbuf, ring);
         if (stage2) continue;
         // Publish this stage-one item (release); the last panel of a split
         // BICGK or GESUMMV adds the row partials in panel order.
@@ -483,8 +608,8 @@ __global__ void batch_reset_kernel(char* ws) {
     if (threadIdx.x == 0) *reinterpret_cast<int*>(ws) = 0;
 }
 
-constexpr int kMaxTile = 1024;
-constexpr size_t kSmemBytes = (4 * kWarps * kRows + 2 * kMaxTile) * sizeof(float);
+constexpr size_t kSmemBytes = (4 * kWarps * kRows + 2 * kMaxTile) * sizeof(float) +
+                              (size_t)kWarps * ring_elems<float>() * sizeof(float);
 
 struct Plan {
     Header h{};

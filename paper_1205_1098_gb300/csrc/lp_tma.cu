@@ -162,9 +162,14 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
             }
 #pragma unroll
             for (int k = 0; k < 16; k++) sl[k] = 0.0f;
-            int gs = 0;                 // stage within the butterfly group
-            int64_t gbase = c0;         // first column of the group
-            for (int64_t cs = c0; cs < c1; cs += kBoxC, g++) {
+            // Butterfly groups of GroupStages stages; the stage loop is unrolled so
+            // that sl[] is indexed by constants (and stays in registers).
+            constexpr int GS = Cfg<TA>::GroupStages;
+            for (int64_t gbase = c0; gbase < c1; gbase += (int64_t)GS * kBoxC) {
+#pragma unroll
+            for (int gs = 0; gs < GS; gs++) {
+              const int64_t cs = gbase + (int64_t)gs * kBoxC;
+              if (cs < c1) {
                 const int slot = (int)(g % S);
                 bool have = true;
                 if (!*s_abort_p && !mbar_wait_bounded(&full[slot], (uint32_t)((g / S) & 1), kWaitNs, s_abort_p)) {
@@ -232,8 +237,9 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
                 }
                 __syncwarp();
                 if (lane == 0 && have) mbar_arrive(&empty[slot]);
-                gs++;
-                if (gs == Cfg<TA>::GroupStages || cs + kBoxC >= c1) {
+                g++;
+              }
+            }
                     if (HAS_Q) {
 #pragma unroll
                         for (int k = 0; k < kRPT; k++) {
@@ -256,9 +262,6 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
 #pragma unroll
                         for (int k = 0; k < 16; k++) sl[k] = 0.0f;
                     }
-                    gs = 0;
-                    gbase = cs + kBoxC;
-                }
             }
             if (HAS_Q) {
                 // Add the eight warps' row sums (each warp saw other columns) in FP64.

@@ -302,7 +302,10 @@ __device__ __forceinline__ double strided_sum(const double* P, int64_t ld, int K
 #pragma unroll
         for (int u = 0; u < 4; u++) acc[u] += __ldg(P + (int64_t)(k + u * kCombWarps) * ld + i);
     }
-    for (int u = 0; k < K; k += kCombWarps, u++) acc[u] += __ldg(P + (int64_t)k * ld + i);
+    // At most three partials remain; unrolled so acc[] stays in registers.
+#pragma unroll
+    for (int u = 0; u < 3; u++)
+        if (k + u * kCombWarps < K) acc[u] += __ldg(P + (int64_t)(k + u * kCombWarps) * ld + i);
     return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 

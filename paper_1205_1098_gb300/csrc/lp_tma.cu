@@ -66,6 +66,23 @@ constexpr int box_cols() { return Cfg<TA>::BoxC; }
 template <int V>
 __device__ __forceinline__ int trow(int lane, int k) { return (k / V) * (32 * V) + lane * V + (k % V); }
 
+// The V values of a 16-byte shared-memory read as FP32: one bit operation
+// per BF16 value (the high half of a 32-bit word is already an FP32 bit
+// pattern; the low half is shifted up).
+template <typename TA>
+__device__ __forceinline__ void unpack16(const uint4& raw, float* out) {
+    const unsigned w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (sizeof(TA) == 4) {
+            out[k] = __uint_as_float(w[k]);
+        } else {
+            out[2 * k] = __uint_as_float(w[k] << 16);
+            out[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+        }
+    }
+}
+
 template <typename TA, int MODE>
 __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_constant__ CUtensorMap tmA,
                                                               const LpArgs a) {
@@ -137,7 +154,8 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
 
     // ---------------- consumers
     TA* Bout = static_cast<TA*>(a.Bout);
-    long long g = 0;
+    int slot = 0;            // ring slot of the next stage
+    uint32_t ph = 0;         // parity of its use (stage index / S, mod 2)
     for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int64_t tt = a.reverse ? (a.ntiles - 1 - t) : t;
         const int64_t cb = tt / a.NR, rb = tt % a.NR;
@@ -170,29 +188,26 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
             for (int gs = 0; gs < GS; gs++) {
               const int64_t cs = gbase + (int64_t)gs * kBoxC;
               if (cs < c1) {
-                const int slot = (int)(g % S);
                 bool have = true;
-                if (!*s_abort_p && !mbar_wait_bounded(&full[slot], (uint32_t)((g / S) & 1), kWaitNs, s_abort_p)) {
+                if (!*s_abort_p && !mbar_wait_bounded(&full[slot], ph, kWaitNs, s_abort_p)) {
                     if (lane == 0) atomicExch(a.status, (int)BTO_ERR_TIMEOUT);
                     *s_abort_p = 1;
                 }
                 if (*s_abort_p) have = false;
                 const TA* buf = ring + (size_t)slot * kBoxR * kBoxC;
+                const int lc0 = (int)(cs - c0);      // tile-local column of the stage's first column
 #pragma unroll
                 for (int cc = 0; cc < CPW; cc++) {
                     const int c = CPW * warp + cc;
-                    const int64_t col = cs + c;
-                    if (have && col < c1) {
+                    const int lc = lc0 + c;
+                    if (have && lc < ncols) {
+                        const int64_t col = c0 + lc;
                         float av[kRPT];
 #pragma unroll
-                        for (int h = 0; h < kRPT / V; h++) {
-                            const uint4 raw = *reinterpret_cast<const uint4*>(buf + c * kBoxR + h * 32 * V + lane * V);
-                            const TA* e = reinterpret_cast<const TA*>(&raw);
-#pragma unroll
-                            for (int q = 0; q < V; q++) av[h * V + q] = to_f<TA>(e[q]);
-                        }
+                        for (int h = 0; h < kRPT / V; h++)
+                            unpack16<TA>(*reinterpret_cast<const uint4*>(buf + c * kBoxR + h * 32 * V + lane * V), av + h * V);
                         if (MODE == LP_G1) {
-                            const float v1j = sv1[col - c0], v2j = sv2[col - c0];
+                            const float v1j = sv1[lc], v2j = sv2[lc];
                             TA bq[kRPT];
                             float bf[kRPT];
 #pragma unroll
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
                             sl[CPW * gs + cc] = acc;
                         } else {
                             if (HAS_Q) {
-                                const float pj = sp[col - c0];
+                                const float pj = sp[lc];
 #pragma unroll
                                 for (int k = 0; k < kRPT; k++) qt[k] = fmaf(av[k], pj, qt[k]);
                             }
@@ -237,7 +252,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
                 }
                 __syncwarp();
                 if (lane == 0 && have) mbar_arrive(&empty[slot]);
-                g++;
+                if (++slot == S) { slot = 0; ph ^= 1u; }
               }
             }
                     if (HAS_Q) {

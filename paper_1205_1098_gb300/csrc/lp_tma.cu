@@ -11,8 +11,10 @@
 // on), so 6-8 stages of the matrix are in flight per SM without holding any
 // registers.  The arithmetic is that of the load-instruction sweep:
 //   A p   : FP32 FMA chains over 16 columns per row, folded into TwoSum pairs;
-//   A^T r : 8-row FMA chains per column, a 16-column transposing butterfly
-//           across the warp, folded into TwoSum pairs in shared memory;
+//   A^T r : per column two 4-row FMA chains (even and odd rows), a 16-column
+//           transposing butterfly across the warp, folded into TwoSum pairs
+//           in shared memory;
+// FMAs on pairs of rows use the packed FP32 instructions (__ffma2_rn).
 // tiles end in (hi, lo) FP32 pairs that a fixed-order FP64 combine adds.
 // Every mbarrier wait is bounded by %globaltimer (2 s) and by a shared abort
 // flag: on expiry the block records BTO_ERR_TIMEOUT in the status word,
@@ -65,6 +67,15 @@ constexpr int box_cols() { return Cfg<TA>::BoxC; }
 // per 16-byte read.
 template <int V>
 __device__ __forceinline__ int trow(int lane, int k) { return (k / V) * (32 * V) + lane * V + (k % V); }
+
+// sum_k a[k] r[k] over a lane's 8 rows as two interleaved FMA chains (even
+// and odd rows) in packed FP32 instructions, added at the end.
+__device__ __forceinline__ float dot8(const float (&a)[kRPT], const float (&r)[kRPT]) {
+    float2 acc = __fmul2_rn(make_float2(a[0], a[1]), make_float2(r[0], r[1]));
+#pragma unroll
+    for (int k = 2; k < kRPT; k += 2) acc = __ffma2_rn(make_float2(a[k], a[k + 1]), make_float2(r[k], r[k + 1]), acc);
+    return acc.x + acc.y;
+}
 
 // The V values of a 16-byte shared-memory read as FP32: one bit operation
 // per BF16 value (the high half of a 32-bit word is already an FP32 bit
@@ -211,9 +222,16 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
                             TA bq[kRPT];
                             float bf[kRPT];
 #pragma unroll
-                            for (int k = 0; k < kRPT; k++) {
-                                bq[k] = from_f<TA>(fmaf(u2r[k], v2j, fmaf(u1r[k], v1j, av[k])));
+                            for (int k = 0; k < kRPT; k += 2) {
+                                // Two rows per packed FMA; per element the same two FMAs as before.
+                                const float2 t = __ffma2_rn(make_float2(u2r[k], u2r[k + 1]), make_float2(v2j, v2j),
+                                                            __ffma2_rn(make_float2(u1r[k], u1r[k + 1]),
+                                                                       make_float2(v1j, v1j),
+                                                                       make_float2(av[k], av[k + 1])));
+                                bq[k] = from_f<TA>(t.x);
+                                bq[k + 1] = from_f<TA>(t.y);
                                 bf[k] = to_f<TA>(bq[k]);
+                                bf[k + 1] = to_f<TA>(bq[k + 1]);
                             }
                             TA* bcol = Bout + col * a.ldb;
 #pragma unroll
@@ -231,22 +249,19 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
                                         if (i + q < r1) bcol[i + q] = bq[h * V + q];
                                 }
                             }
-                            float acc = bf[0] * rv[0];
-#pragma unroll
-                            for (int k = 1; k < kRPT; k++) acc = fmaf(bf[k], rv[k], acc);
-                            sl[CPW * gs + cc] = acc;
+                            sl[CPW * gs + cc] = dot8(bf, rv);
                         } else {
                             if (HAS_Q) {
                                 const float pj = sp[lc];
 #pragma unroll
-                                for (int k = 0; k < kRPT; k++) qt[k] = fmaf(av[k], pj, qt[k]);
+                                for (int k = 0; k < kRPT; k += 2) {
+                                    const float2 t = __ffma2_rn(make_float2(av[k], av[k + 1]), make_float2(pj, pj),
+                                                                make_float2(qt[k], qt[k + 1]));
+                                    qt[k] = t.x;
+                                    qt[k + 1] = t.y;
+                                }
                             }
-                            if (HAS_S) {
-                                float acc = av[0] * rv[0];
-#pragma unroll
-                                for (int k = 1; k < kRPT; k++) acc = fmaf(av[k], rv[k], acc);
-                                sl[CPW * gs + cc] = acc;
-                            }
+                            if (HAS_S) sl[CPW * gs + cc] = dot8(av, rv);
                         }
                     }
                 }

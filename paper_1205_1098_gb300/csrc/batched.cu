@@ -235,6 +235,25 @@ __device__ __forceinline__ void stash_rows(float* red, int warp, int lane, const
     }
 }
 
+// t[k] += a[k] * x for a lane's 8 rows, two rows per packed FP32 FMA.
+__device__ __forceinline__ void fma8(const float (&a)[8], float x, float (&t)[8]) {
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        const float2 r = __ffma2_rn(make_float2(a[k], a[k + 1]), make_float2(x, x), make_float2(t[k], t[k + 1]));
+        t[k] = r.x;
+        t[k + 1] = r.y;
+    }
+}
+
+// sum_k a[k] r[k] over a lane's 8 rows: two interleaved chains (even and odd
+// rows) in packed FP32 instructions, added at the end.
+__device__ __forceinline__ float dot8(const float (&a)[8], const float (&r)[8]) {
+    float2 acc = __fmul2_rn(make_float2(a[0], a[1]), make_float2(r[0], r[1]));
+#pragma unroll
+    for (int k = 2; k < 8; k += 2) acc = __ffma2_rn(make_float2(a[k], a[k + 1]), make_float2(r[k], r[k + 1]), acc);
+    return acc.x + acc.y;
+}
+
 __device__ __forceinline__ void fold(float (&hi)[8], float (&lo)[8], float (&t)[8]) {
 #pragma unroll
     for (int k = 0; k < 8; k++) {
@@ -336,29 +355,27 @@ __device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstIn
                         const int64_t j = g0 + jj;
                         if (HAS_Q) {
                             const float pj = __ldg(xin + j);
-#pragma unroll
-                            for (int k = 0; k < 8; k++) qt[k] = fmaf(av[u][k], pj, qt[k]);
-                            if (KIND == IT_GESUMMV) {
-#pragma unroll
-                                for (int k = 0; k < 8; k++) q2t[k] = fmaf(bv[u][k], pj, q2t[k]);
-                            }
+                            fma8(av[u], pj, qt);
+                            if (KIND == IT_GESUMMV) fma8(bv[u], pj, q2t);
                         }
                         if (KIND == IT_GEMVER1) {
                             const float v1j = __ldg(d.in[1] + j), v2j = __ldg(d.in[3] + j);
                             TA bq[8];
 #pragma unroll
-                            for (int k = 0; k < 8; k++) {
-                                bq[k] = from_f<TA>(fmaf(u2r[k], v2j, fmaf(u1r[k], v1j, av[u][k])));
+                            for (int k = 0; k < 8; k += 2) {
+                                // Two rows per packed FMA; per element the same two FMAs.
+                                const float2 t = __ffma2_rn(make_float2(u2r[k], u2r[k + 1]), make_float2(v2j, v2j),
+                                                            __ffma2_rn(make_float2(u1r[k], u1r[k + 1]),
+                                                                       make_float2(v1j, v1j),
+                                                                       make_float2(av[u][k], av[u][k + 1])));
+                                bq[k] = from_f<TA>(t.x);
+                                bq[k + 1] = from_f<TA>(t.y);
                                 av[u][k] = to_f<TA>(bq[k]);     // x uses the stored B
+                                av[u][k + 1] = to_f<TA>(bq[k + 1]);
                             }
                             store8<TA>(Bo + j * d.ldb, R0, m, lane, vec, bq);
                         }
-                        if (HAS_S) {
-                            float acc = av[u][0] * rv[0];
-#pragma unroll
-                            for (int k = 1; k < 8; k++) acc = fmaf(av[u][k], rv[k], acc);
-                            sl[jj] = acc;
-                        }
+                        if (HAS_S) sl[jj] = dot8(av[u], rv);
                     } else if (HAS_S) {
                         sl[jj] = 0.0f;
                     }
@@ -475,10 +492,7 @@ __device__ __forceinline__ void row_item(const bto_batch_desc& d, const InstInfo
             }
 #pragma unroll
             for (int u = 0; u < 4; u++)
-                if (jb + u < nc) {
-#pragma unroll
-                    for (int k = 0; k < 8; k++) qt[k] = fmaf(av[u][k], xj[u], qt[k]);
-                }
+                if (jb + u < nc) fma8(av[u], xj[u], qt);
         }
         fold(qhi, qlo, qt);
     }

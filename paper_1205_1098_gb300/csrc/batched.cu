@@ -285,24 +285,28 @@ __device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstIn
     __syncthreads();
     // Columns loaded ahead of use: four (two for GESUMMV, which loads two matrices).
     constexpr int KU = KIND == IT_GESUMMV ? 2 : 4;
-    // Copy-ring schedule: batch = (chunk, warp group, step of KU columns), in loop order.
-    const int ngw = ncols > 16 * warp ? (int)((ncols - 16 * warp + 16 * kWarps - 1) / (16 * kWarps)) : 0;
-    const int nbat = vec ? (int)((m + kRows - 1) / kRows) * ngw * (16 / KU) : 0;
-    int bi = 0, iss = 0, ic = 0, ig = 0, ij = 0;
+    constexpr int GB = 16 / KU;                 // batches per 16-column butterfly group
+    // Columns are dealt to the warps in batches of KU: warp w takes batches
+    // w, w + 8, w + 16, ... of the panel, so the warps' shares differ by at
+    // most one batch (whole 16-column groups left warps idle on narrow panels).
+    const int nbt = (int)((ncols + KU - 1) / KU);
+    const int nbw = nbt > warp ? (nbt - warp + kWarps - 1) / kWarps : 0;
+    // Copy-ring schedule: batch = (chunk, this warp's batch t), in loop order.
+    const int nbat = vec ? (int)((m + kRows - 1) / kRows) * nbw : 0;
+    int bi = 0, iss = 0, ic = 0, it = 0;
     auto issue = [&]() {
         if (iss < nbat) {
-            const int64_t R0i = (int64_t)ic * kRows, g0i = c0 + 16 * warp + 16 * kWarps * ig;
-            const int nci = (int)((c1 - g0i) < 16 ? (c1 - g0i) : 16);
+            const int64_t R0i = (int64_t)ic * kRows, cbi = c0 + (int64_t)KU * (warp + kWarps * it);
+            const int nci = (int)((c1 - cbi) < KU ? (c1 - cbi) : KU);
             TA* st = ring + (iss % kStages) * (kBatchCols * kRows);
 #pragma unroll
             for (int u = 0; u < KU; u++) {
-                const int jj = KU * ij + u;
-                if (jj < nci) {
-                    cp_col<TA>(st + u * kRows, A + (g0i + jj) * d.lda, R0i, m, lane);
-                    if (KIND == IT_GESUMMV) cp_col<TA>(st + (KU + u) * kRows, B2 + (g0i + jj) * d.ldb, R0i, m, lane);
+                if (u < nci) {
+                    cp_col<TA>(st + u * kRows, A + (cbi + u) * d.lda, R0i, m, lane);
+                    if (KIND == IT_GESUMMV) cp_col<TA>(st + (KU + u) * kRows, B2 + (cbi + u) * d.ldb, R0i, m, lane);
                 }
             }
-            if (++ij == 16 / KU) { ij = 0; if (++ig == ngw) { ig = 0; ++ic; } }
+            if (++it == nbw) { it = 0; ++ic; }
         }
         cp_commit();
         iss++;
@@ -320,13 +324,22 @@ __device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstIn
         if (KIND == IT_ATAX2) load_rows<TA, true>(tbuf + info.toff, R0, m, lane, rv);
 #pragma unroll
         for (int k = 0; k < 8; k++) { qhi[k] = 0.0f; qlo[k] = 0.0f; q2hi[k] = 0.0f; q2lo[k] = 0.0f; }
-        for (int64_t g0 = c0 + 16 * warp; g0 < c1; g0 += 16 * kWarps) {
-            const int nc = (int)((c1 - g0) < 16 ? (c1 - g0) : 16);
+        for (int t0 = 0; t0 < nbw; t0 += GB) {
             float sl[16], qt[8], q2t[8];
 #pragma unroll
             for (int k = 0; k < 8; k++) { qt[k] = 0.0f; q2t[k] = 0.0f; }
 #pragma unroll
-            for (int jb = 0; jb < 16; jb += KU) {
+            for (int tt = 0; tt < GB; tt++) {
+                const int t = t0 + tt;
+                if (t >= nbw) {
+                    if (HAS_S) {
+#pragma unroll
+                        for (int u = 0; u < KU; u++) sl[KU * tt + u] = 0.0f;
+                    }
+                    continue;
+                }
+                const int64_t cb = c0 + (int64_t)KU * (warp + kWarps * t);
+                const int nc = (int)((c1 - cb) < KU ? (c1 - cb) : KU);
                 float av[KU][8], bv[KU][8];
                 if (vec) {
                     // Batch bi is in the ring once at most kStages - 2 newer batches are pending.
@@ -334,7 +347,7 @@ __device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstIn
                     const TA* st = ring + (bi % kStages) * (kBatchCols * kRows);
 #pragma unroll
                     for (int u = 0; u < KU; u++)
-                        if (jb + u < nc) {
+                        if (u < nc) {
                             read_col<TA>(st + u * kRows, lane, av[u]);
                             if (KIND == IT_GESUMMV) read_col<TA>(st + (KU + u) * kRows, lane, bv[u]);
                         }
@@ -343,16 +356,16 @@ __device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstIn
                 } else {
 #pragma unroll
                     for (int u = 0; u < KU; u++)
-                        if (jb + u < nc) {
-                            load8<TA, false>(A + (g0 + jb + u) * d.lda, R0, m, lane, vec, av[u]);
-                            if (KIND == IT_GESUMMV) load8<TA, false>(B2 + (g0 + jb + u) * d.ldb, R0, m, lane, vec, bv[u]);
+                        if (u < nc) {
+                            load8<TA, false>(A + (cb + u) * d.lda, R0, m, lane, vec, av[u]);
+                            if (KIND == IT_GESUMMV) load8<TA, false>(B2 + (cb + u) * d.ldb, R0, m, lane, vec, bv[u]);
                         }
                 }
 #pragma unroll
                 for (int u = 0; u < KU; u++) {
-                    const int jj = jb + u;
-                    if (jj < nc) {
-                        const int64_t j = g0 + jj;
+                    const int jj = KU * tt + u;
+                    if (u < nc) {
+                        const int64_t j = cb + u;
                         if (HAS_Q) {
                             const float pj = __ldg(xin + j);
                             fma8(av[u], pj, qt);
@@ -364,12 +377,12 @@ __device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstIn
 #pragma unroll
                             for (int k = 0; k < 8; k += 2) {
                                 // Two rows per packed FMA; per element the same two FMAs.
-                                const float2 t = __ffma2_rn(make_float2(u2r[k], u2r[k + 1]), make_float2(v2j, v2j),
-                                                            __ffma2_rn(make_float2(u1r[k], u1r[k + 1]),
-                                                                       make_float2(v1j, v1j),
-                                                                       make_float2(av[u][k], av[u][k + 1])));
-                                bq[k] = from_f<TA>(t.x);
-                                bq[k + 1] = from_f<TA>(t.y);
+                                const float2 t2 = __ffma2_rn(make_float2(u2r[k], u2r[k + 1]), make_float2(v2j, v2j),
+                                                             __ffma2_rn(make_float2(u1r[k], u1r[k + 1]),
+                                                                        make_float2(v1j, v1j),
+                                                                        make_float2(av[u][k], av[u][k + 1])));
+                                bq[k] = from_f<TA>(t2.x);
+                                bq[k + 1] = from_f<TA>(t2.y);
                                 av[u][k] = to_f<TA>(bq[k]);     // x uses the stored B
                                 av[u][k + 1] = to_f<TA>(bq[k + 1]);
                             }
@@ -384,12 +397,16 @@ __device__ __forceinline__ void panel_item(const bto_batch_desc& d, const InstIn
             if (HAS_Q) fold(qhi, qlo, qt);
             if (KIND == IT_GESUMMV) fold(q2hi, q2lo, q2t);
             if (HAS_S) {
+                // Lane l < 16 holds slot l of the group: batch t0 + l / KU, column l % KU of it.
                 const float cs = butterfly16(sl, lane);
-                if (lane < nc) {
-                    const int64_t o = g0 + lane - c0;
-                    float s2, e2;
-                    two_sum(shi[o], cs, s2, e2);
-                    shi[o] = s2; slo[o] += e2;
+                const int t = t0 + lane / KU;
+                if (lane < 16 && t < nbw) {
+                    const int64_t o = (int64_t)KU * (warp + kWarps * t) + lane % KU;
+                    if (o < ncols) {
+                        float s2, e2;
+                        two_sum(shi[o], cs, s2, e2);
+                        shi[o] = s2; slo[o] += e2;
+                    }
                 }
             }
         }
@@ -445,56 +462,54 @@ __device__ __forceinline__ void row_item(const bto_batch_desc& d, const InstInfo
     float qhi[8], qlo[8], qt[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) { qhi[k] = 0.0f; qlo[k] = 0.0f; qt[k] = 0.0f; }
-    // Copy-ring schedule (see cp_col): batch = (warp group, step of 4 columns).
+    // Columns are dealt to the warps in batches of 4 (warp w takes batches
+    // w, w + 8, ...); the copy ring follows the same order (see cp_col).
     // cp.async.cg reads through L2, so GEMVER's B written by stage one is seen.
-    const int ngw = n > 16 * warp ? (int)((n - 16 * warp + 16 * kWarps - 1) / (16 * kWarps)) : 0;
-    const int nbat = vec ? ngw * 4 : 0;
+    const int nbt = (int)((n + 3) / 4);
+    const int nbw = nbt > warp ? (nbt - warp + kWarps - 1) / kWarps : 0;
+    const int nbat = vec ? nbw : 0;
     int bi = 0, iss = 0;
     auto issue = [&]() {
         if (iss < nbat) {
-            const int64_t g0i = 16 * warp + 16 * kWarps * (iss >> 2);
-            const int nci = (int)((n - g0i) < 16 ? (n - g0i) : 16);
+            const int64_t cbi = 4 * (int64_t)(warp + kWarps * iss);
+            const int nci = (int)((n - cbi) < 4 ? (n - cbi) : 4);
             TA* st = ring + (iss % kStages) * (kBatchCols * kRows);
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int jj = 4 * (iss & 3) + u;
-                if (jj < nci) cp_col<TA>(st + u * kRows, M + (g0i + jj) * ld, R0, m, lane);
-            }
+            for (int u = 0; u < 4; u++)
+                if (u < nci) cp_col<TA>(st + u * kRows, M + (cbi + u) * ld, R0, m, lane);
         }
         cp_commit();
         iss++;
     };
     if (vec)
         for (int k = 0; k < kStages - 1; k++) issue();
-    for (int64_t g0 = 16 * warp; g0 < n; g0 += 16 * kWarps) {
-        const int nc = (int)((n - g0) < 16 ? (n - g0) : 16);
-#pragma unroll
-        for (int jb = 0; jb < 16; jb += 4) {
-            float av[4][8], xj[4];
-            if (vec) {
-                cp_wait_ring();
-                const TA* st = ring + (bi % kStages) * (kBatchCols * kRows);
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (jb + u < nc) {
-                        read_col<TA>(st + u * kRows, lane, av[u]);
-                        xj[u] = KIND == IT_GEMVER2 ? __ldcg(v + g0 + jb + u) : __ldg(v + g0 + jb + u);
-                    }
-                bi++;
-                issue();
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (jb + u < nc) {
-                        load8<TA, KIND == IT_GEMVER2>(M + (g0 + jb + u) * ld, R0, m, lane, vec, av[u]);
-                        xj[u] = KIND == IT_GEMVER2 ? __ldcg(v + g0 + jb + u) : __ldg(v + g0 + jb + u);
-                    }
-            }
+    for (int t = 0; t < nbw; t++) {
+        const int64_t cb = 4 * (int64_t)(warp + kWarps * t);
+        const int nc = (int)((n - cb) < 4 ? (n - cb) : 4);
+        float av[4][8], xj[4];
+        if (vec) {
+            cp_wait_ring();
+            const TA* st = ring + (bi % kStages) * (kBatchCols * kRows);
 #pragma unroll
             for (int u = 0; u < 4; u++)
-                if (jb + u < nc) fma8(av[u], xj[u], qt);
+                if (u < nc) {
+                    read_col<TA>(st + u * kRows, lane, av[u]);
+                    xj[u] = KIND == IT_GEMVER2 ? __ldcg(v + cb + u) : __ldg(v + cb + u);
+                }
+            bi++;
+            issue();
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (u < nc) {
+                    load8<TA, KIND == IT_GEMVER2>(M + (cb + u) * ld, R0, m, lane, vec, av[u]);
+                    xj[u] = KIND == IT_GEMVER2 ? __ldcg(v + cb + u) : __ldg(v + cb + u);
+                }
         }
-        fold(qhi, qlo, qt);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (u < nc) fma8(av[u], xj[u], qt);
+        if ((t & 3) == 3 || t + 1 == nbw) fold(qhi, qlo, qt);   // every 16 columns, as the panel sweep
     }
     stash_rows<TA>(red, warp, lane, qhi, qlo);
     __syncthreads();

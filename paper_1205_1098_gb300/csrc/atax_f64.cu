@@ -290,11 +290,14 @@ bto_status atax_impl(int64_t m, int64_t n, double beta, const double* A, int64_t
     cudaStream_t st = (cudaStream_t)stream;
     char* w = static_cast<char*>(ws);
     if (n == 0) return BTO_OK;
+    const AtaxPlan ap = atax_plan(m, n, d);
+    // The status word reads BTO_OK after every form; the group-band kernel
+    // clears it below together with its flags.
+    if ((m == 0 || !ap.fused) && cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
     if (m == 0) {   // y = beta * (empty sum)
         CombineJob j = {y, n, nullptr, 0, 0, beta, nullptr, 0, 0, 0.0, nullptr, 0.0};
         return launch_combine(&j, 1, st);
     }
-    const AtaxPlan ap = atax_plan(m, n, d);
     if (!ap.fused) {
         // Slices too wide for shared memory: t = A x into the workspace, then
         // y = beta A^T t (A is read twice).

@@ -222,6 +222,10 @@ mrhs_tma_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ 
     const bool qdb = 6 * k <= (int)kTmemCols;
 
     if (threadIdx.x == 0) {
+        // This call's status starts at BTO_OK (a timeout needs a second of waiting).
+        if (blockIdx.x == 0) *a.status = BTO_OK;
+        // The combine may be scheduled now; it waits for this grid to finish.
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         for (int s = 0; s < NS; s++) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int b = 0; b < 2; b++) { mbar_init(&qfull[b], 1); mbar_init(&qempty[b], 4); }
         mbar_init(&sfull, 1);
@@ -428,6 +432,8 @@ __global__ void __launch_bounds__(kLdgThreads, 1) mrhs_ldg_kernel(const MrhsArgs
     const bool qdb = 6 * k <= (int)kTmemCols;
 
     if (threadIdx.x == 0) {
+        if (blockIdx.x == 0) *a.status = BTO_OK;
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         for (int s = 0; s < NS; s++) mbar_init(&bars[s], 1);
         *abortp = 0;
         fence_mbar_init();
@@ -537,6 +543,9 @@ __global__ void __launch_bounds__(kCombThreads)
 mrhs_combine(const float* __restrict__ qpart, const float* __restrict__ spart, int64_t m, int64_t n, int k,
              int NP, int64_t ldqp, int64_t nrt, int64_t U, int G, int qblocks, float* Q, int64_t ldq, float* S,
              int64_t lds) {
+    // Launched as a programmatic dependent of the main kernel: wait until it
+    // has finished and its partials are visible.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int j = blockIdx.y;
     const bool isq = (int)blockIdx.x < qblocks;
     const int64_t e0 = (int64_t)(isq ? blockIdx.x : blockIdx.x - qblocks) * kCombSpan;
@@ -676,7 +685,6 @@ extern "C" bto_status bto_bicgk_mrhs(int64_t m, int64_t n, int64_t k, const uint
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
     char* w = static_cast<char*>(ws);
-    if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
     float* qpart = reinterpret_cast<float*>(w + 256);
     float* spart = reinterpret_cast<float*>(w + 256 + pl.q_bytes);
     if (pl.NP > 0) {
@@ -702,9 +710,20 @@ extern "C" bto_status bto_bicgk_mrhs(int64_t m, int64_t n, int64_t k, const uint
         }
         if (cudaGetLastError() != cudaSuccess) return BTO_ERR_CUDA;
         const int qblocks = (int)ceil_div(m, kCombSpan), sblocks = (int)ceil_div(n, kCombSpan);
-        mrhs_combine<<<dim3(qblocks + sblocks, (unsigned)k), kCombThreads, 0, st>>>(
-            qpart, spart, m, n, (int)k, pl.NP, pl.ldqp, pl.nrt, pl.U, pl.G, qblocks, Q, ldq, S, lds);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(qblocks + sblocks, (unsigned)k);
+        cfg.blockDim = dim3(kCombThreads);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, mrhs_combine, (const float*)qpart, (const float*)spart, m, n, (int)k, pl.NP,
+                               pl.ldqp, pl.nrt, pl.U, pl.G, qblocks, Q, ldq, S, lds) != cudaSuccess)
+            return BTO_ERR_CUDA;
     } else {
+        if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
         // An empty sum: Q = 0 (n = 0) and S = 0 (m = 0).
         for (int64_t j = 0; j < k; j++) {
             if (m > 0 && cudaMemsetAsync(Q + j * ldq, 0, (size_t)m * 4, st) != cudaSuccess) return BTO_ERR_CUDA;

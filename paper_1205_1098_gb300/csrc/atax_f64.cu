@@ -39,7 +39,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kTB = 16;                 // band height (rows)
+constexpr int kTB = 16;                 // band height (rows) the plan uses
+constexpr int kLook = 1;                // bands of lookahead the plan uses
 constexpr int kBlocksPerSM = 2;         // two blocks per SM: one computes while the other waits
 constexpr int kMinGroup = 16;           // blocks per group
 constexpr int64_t kMaxSlice = 4096;     // widest column slice per block (x, y slices in shared memory)
@@ -49,7 +50,7 @@ struct AtaxArgs {
     const double* A; int64_t lda;
     const double* x;
     unsigned* flag;      // [G] bands published by each block (sequence number within its group)
-    double* tslot;       // [NG][2][S][kTB] block partials of t
+    double* tslot;       // [NG][2 D][S][TB] block partials of t
     double* ypart;       // [NG][ldy] group partials of y
     int64_t ldy;
     int* status;
@@ -78,27 +79,29 @@ __device__ __host__ __forceinline__ int64_t split_at(int64_t n, int64_t parts, i
     return (n / parts) * b + ((n % parts) * b) / parts;
 }
 
-// The 16 values of a column segment starting at row R0 (rows past m read as 0).
-template <bool VEC2>
-__device__ __forceinline__ void load_seg(const double* col, bool whole, int rows, double (&v)[kTB]) {
+// The TB values of a column segment starting at row R0 (rows past m read as 0).
+template <int TB, bool VEC2>
+__device__ __forceinline__ void load_seg(const double* col, bool whole, int rows, double (&v)[TB]) {
     if (VEC2 && whole) {
 #pragma unroll
-        for (int i = 0; i < kTB; i += 2) {
+        for (int i = 0; i < TB; i += 2) {
             const double2 t = __ldg(reinterpret_cast<const double2*>(col + i));
             v[i] = t.x;
             v[i + 1] = t.y;
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < kTB; i++) v[i] = i < rows ? __ldg(col + i) : 0.0;
+        for (int i = 0; i < TB; i++) v[i] = i < rows ? __ldg(col + i) : 0.0;
     }
 }
 
-// Sums tp[16] over the 32 lanes of a warp by halving exchanges; afterwards
-// lane l holds the warp's sum for row l >> 1 (lanes 2k and 2k+1 agree).
-__device__ __forceinline__ double warp_reduce16(double (&tp)[kTB], int lane) {
+// Sums tp[TB] (TB = 8 or 16) over the 32 lanes of a warp by halving
+// exchanges; afterwards lane l holds the warp's sum for row (l >> 1) mod TB
+// (the lanes that share a row agree).
+template <int TB>
+__device__ __forceinline__ double warp_reduce(double (&tp)[TB], int lane) {
 #pragma unroll
-    for (int h = 8; h >= 1; h >>= 1) {
+    for (int h = TB / 2; h >= 1; h >>= 1) {
         const bool upper = (lane & (2 * h)) != 0;      // this lane keeps rows [h, 2h) of each 2h-group
 #pragma unroll
         for (int i = 0; i < h; i++) {
@@ -107,16 +110,20 @@ __device__ __forceinline__ double warp_reduce16(double (&tp)[kTB], int lane) {
             tp[i] = (upper ? tp[i + h] : tp[i]) + recv;
         }
     }
-    return tp[0] + __shfl_xor_sync(0xffffffffu, tp[0], 1);
+    double w = tp[0] + __shfl_xor_sync(0xffffffffu, tp[0], 1);
+    if (TB == 8) w += __shfl_xor_sync(0xffffffffu, w, 16);
+    return w;
 }
 
-template <bool VEC2>
+template <int TB, int D, bool VEC2>
 __global__ void __launch_bounds__(kThreads, kBlocksPerSM) atax_kernel(const AtaxArgs a) {
+    constexpr int NSL = 2 * D;               // partial slots per group (see publish)
     extern __shared__ double sm[];
     double* xs = sm;                         // [cmax] x over this block's columns
     double* ys = xs + a.cmax;                // [cmax] y accumulators
-    __shared__ double red[kWarps][kTB];
-    __shared__ double tnext[kTB], ts[kTB];
+    __shared__ double red[kWarps][TB];
+    __shared__ double tnext[TB], ts[TB];
+    __shared__ double gbuf[kThreads];        // a round of gathered partials
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x / a.S, r = blockIdx.x % a.S;
@@ -134,24 +141,24 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) atax_kernel(const Atax
 
     // Pass 1 over the q-th band of the group: the block's partial t in tnext.
     auto pass1 = [&](int64_t q) {
-        const int64_t R0 = (g + q * a.NG) * kTB;
-        const int rows = (int)(a.m - R0 < kTB ? a.m - R0 : kTB);
-        const bool whole = rows == kTB;
-        double tp[kTB];
+        const int64_t R0 = (g + q * a.NG) * TB;
+        const int rows = (int)(a.m - R0 < TB ? a.m - R0 : TB);
+        const bool whole = rows == TB;
+        double tp[TB];
 #pragma unroll
-        for (int i = 0; i < kTB; i++) tp[i] = 0.0;
+        for (int i = 0; i < TB; i++) tp[i] = 0.0;
 #pragma unroll 2
         for (int jl = threadIdx.x; jl < nc; jl += kThreads) {
-            double v[kTB];
-            load_seg<VEC2>(a.A + (c0 + jl) * a.lda + R0, whole && vec_ok, rows, v);
+            double v[TB];
+            load_seg<TB, VEC2>(a.A + (c0 + jl) * a.lda + R0, whole && vec_ok, rows, v);
             const double xj = xs[jl];
 #pragma unroll
-            for (int i = 0; i < kTB; i++) tp[i] = fma(v[i], xj, tp[i]);
+            for (int i = 0; i < TB; i++) tp[i] = fma(v[i], xj, tp[i]);
         }
-        const double w = warp_reduce16(tp, lane);
-        if ((lane & 1) == 0) red[warp][lane >> 1] = w;
+        const double w = warp_reduce<TB>(tp, lane);
+        if ((lane & 1) == 0 && (lane >> 1) < TB) red[warp][lane >> 1] = w;
         __syncthreads();
-        if (threadIdx.x < kTB) {
+        if (threadIdx.x < TB) {
             double t = red[0][threadIdx.x];
 #pragma unroll
             for (int k = 1; k < kWarps; k++) t += red[k][threadIdx.x];
@@ -161,55 +168,66 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) atax_kernel(const Atax
     };
     // Publishes tnext as this block's partial of the group's q-th band.
     auto publish = [&](int64_t q) {
-        double* slot = a.tslot + (((int64_t)g * 2 + (q & 1)) * a.S + r) * kTB;
-        if (threadIdx.x < kTB) slot[threadIdx.x] = tnext[threadIdx.x];
+        double* slot = a.tslot + (((int64_t)g * NSL + q % NSL) * a.S + r) * TB;
+        if (threadIdx.x < TB) slot[threadIdx.x] = tnext[threadIdx.x];
         __syncthreads();
         if (threadIdx.x == 0 && !(r == 0 && g + q * a.NG == a.stall_band)) {
-            // The barrier orders the partial's stores before the fence; fence +
-            // release store publish it.
-            __threadfence();
+            // The barrier orders the partial's stores (threads 0..TB-1) before
+            // this release store, which is cumulative: a peer that acquires the
+            // flag sees them.
             st_release(a.flag + blockIdx.x, (unsigned)(q + 1));
         }
     };
-    // Waits for the group's S partials of its q-th band; ts = their sum in rank order.
+    // Waits for the group's S partials of its q-th band; ts = their sum in rank
+    // order.  S threads poll the S flags at once, and all threads fetch the
+    // partials in one round into shared memory (kThreads / TB ranks per
+    // round): no chain of dependent L2 round trips.
     auto gather = [&](int64_t q) -> bool {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < a.S) {
+            const unsigned* f = a.flag + (int64_t)g * a.S + threadIdx.x;
             const unsigned long long t0 = globaltimer();
-            for (int rr = 0; rr < a.S && !s_abort; rr++) {
-                const unsigned* f = a.flag + (int64_t)g * a.S + rr;
-                while (ld_acquire(f) < (unsigned)(q + 1)) {
-                    if (globaltimer() - t0 > a.timeout_ns) {
-                        atomicExch(a.status, (int)BTO_ERR_TIMEOUT);
-                        s_abort = 1;
-                        break;
-                    }
-                    __nanosleep(64);
+            volatile int* abortp = &s_abort;
+            while (ld_acquire(f) < (unsigned)(q + 1)) {
+                if (*abortp) break;
+                if (globaltimer() - t0 > a.timeout_ns) {
+                    atomicExch(a.status, (int)BTO_ERR_TIMEOUT);
+                    *abortp = 1;
+                    break;
                 }
+                __nanosleep(32);
             }
         }
         __syncthreads();
         if (s_abort) return false;
-        if (threadIdx.x < kTB) {
-            const double* slot = a.tslot + ((int64_t)g * 2 + (q & 1)) * a.S * kTB;
-            double t = __ldcg(slot + threadIdx.x);
-            for (int rr = 1; rr < a.S; rr++) t += __ldcg(slot + rr * kTB + threadIdx.x);
-            ts[threadIdx.x] = t;
+        const double* slot = a.tslot + ((int64_t)g * NSL + q % NSL) * a.S * TB;
+        constexpr int RPR = kThreads / TB;          // ranks per round
+        double t = 0.0;
+        for (int rr0 = 0; rr0 < a.S; rr0 += RPR) {
+            const int rr = rr0 + threadIdx.x / TB;
+            gbuf[threadIdx.x] = rr < a.S ? __ldcg(slot + (int64_t)rr * TB + threadIdx.x % TB) : 0.0;
+            __syncthreads();
+            if (threadIdx.x < TB) {
+                const int nr = a.S - rr0 < RPR ? a.S - rr0 : RPR;
+                for (int k = 0; k < nr; k++) t = (rr0 + k == 0) ? gbuf[threadIdx.x] : t + gbuf[k * TB + threadIdx.x];
+            }
+            __syncthreads();
         }
+        if (threadIdx.x < TB) ts[threadIdx.x] = t;
         __syncthreads();
         return true;
     };
     // Pass 2 over the q-th band: y_j += sum_i A(i,j) t_i.
     auto pass2 = [&](int64_t q) {
-        const int64_t R0 = (g + q * a.NG) * kTB;
-        const int rows = (int)(a.m - R0 < kTB ? a.m - R0 : kTB);
-        const bool whole = rows == kTB;
+        const int64_t R0 = (g + q * a.NG) * TB;
+        const int rows = (int)(a.m - R0 < TB ? a.m - R0 : TB);
+        const bool whole = rows == TB;
 #pragma unroll 2
         for (int jl = threadIdx.x; jl < nc; jl += kThreads) {
-            double v[kTB];
-            load_seg<VEC2>(a.A + (c0 + jl) * a.lda + R0, whole && vec_ok, rows, v);
+            double v[TB];
+            load_seg<TB, VEC2>(a.A + (c0 + jl) * a.lda + R0, whole && vec_ok, rows, v);
             double e0 = 0.0, e1 = 0.0;
 #pragma unroll
-            for (int i = 0; i < kTB; i += 2) {
+            for (int i = 0; i < TB; i += 2) {
                 e0 = fma(v[i], ts[i], e0);
                 e1 = fma(v[i + 1], ts[i + 1], e1);
             }
@@ -217,14 +235,18 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) atax_kernel(const Atax
         }
     };
 
-    if (Q > 0) {
-        pass1(0);
-        publish(0);
+    // Pass 1 runs D bands ahead of the exchange.  The partial of band q + D
+    // goes to slot (q + D) mod 2D, last used by band q - D: every peer read
+    // that slot in its gather(q - D), before it published band q, and this
+    // block has seen all peers publish band q (gather(q)) before it writes.
+    for (int64_t q0 = 0; q0 < D && q0 < Q; q0++) {
+        pass1(q0);
+        publish(q0);
     }
     for (int64_t q = 0; q < Q; q++) {
-        if (q + 1 < Q) pass1(q + 1);
+        if (q + D < Q) pass1(q + D);
         if (!gather(q)) return;
-        if (q + 1 < Q) publish(q + 1);
+        if (q + D < Q) publish(q + D);
         pass2(q);
     }
     __syncthreads();
@@ -234,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) atax_kernel(const Atax
 size_t atax_smem(int64_t cmax) { return (size_t)2 * cmax * sizeof(double); }
 
 template <bool VEC2>
-void* atax_fn() { return (void*)atax_kernel<VEC2>; }
+void* atax_fn() { return (void*)atax_kernel<kTB, kLook, VEC2>; }
 
 }  // namespace
 
@@ -256,7 +278,7 @@ AtaxPlan atax_plan(int64_t m, int64_t n, const DeviceInfo& d) {
         return p;
     }
     if (occ < kBlocksPerSM) return p;
-    p.G = NG * S; p.S = S; p.NG = NG; p.cmax = cmax; p.TB = kTB; p.smem = sz;
+    p.G = NG * S; p.S = S; p.NG = NG; p.cmax = cmax; p.TB = kTB; p.D = kLook; p.smem = sz;
     p.nb = ceil_div(m, kTB);
     p.ldy = round_up(n, 32);
     p.fused = true;

@@ -128,6 +128,7 @@ struct AtaxPlan {
     int S = 0;          // blocks per group
     int NG = 0;         // groups
     int TB = 0;         // band height (rows)
+    int D = 0;          // bands of lookahead (2 D partial slots per group)
     int64_t nb = 0;     // number of bands
     int64_t cmax = 0;   // widest column slice
     int64_t ldy = 0;    // leading dimension of the group partials of y

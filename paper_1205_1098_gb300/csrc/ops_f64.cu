@@ -45,7 +45,7 @@ bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type, const D
                 const AtaxPlan ap = atax_plan(m, n, d);
                 if (ap.fused) {
                     L.off[0] = region(cur, (size_t)std::max(ap.G, 1) * sizeof(unsigned));             // per-block flags
-                    L.off[1] = region(cur, (size_t)ap.NG * 2 * ap.S * ap.TB * sizeof(double));       // t partial slots
+                    L.off[1] = region(cur, (size_t)ap.NG * 2 * ap.D * ap.S * ap.TB * sizeof(double));  // t partial slots
                     L.off[2] = region(cur, (size_t)ap.NG * std::max<int64_t>(ap.ldy, 1) * sizeof(double)); // y partials
                     break;
                 }

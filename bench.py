@@ -247,7 +247,7 @@ def timed_steps(torch, suite, steps, warmup, form, dist, per_kernel=True):
 def e2e_steps(torch, bto, steps, warmup, m, n, N):
     """Same suite through the public API from pinned host buffers: every step
     copies its inputs host->device, runs the fused kernels and reads every
-    output back."""
+    output back; copies in both directions overlap the kernels."""
     import synth
     pin = dict(dtype=torch.float64, pin_memory=True)
     hA = torch.empty(m * n, **pin)
@@ -289,30 +289,69 @@ def e2e_steps(torch, bto, steps, warmup, m, n, N):
     d2h = sum(t.numel() * 8 for t in outs_h.values()) + sum(t.numel() * 8 for t in outs_big_h.values()) + \
         hBout.numel() * 8
 
-    def step():
-        suite.A.copy_(hA, non_blocking=True)
-        suite.B2.copy_(hB, non_blocking=True)
-        for k, t in hv.items():
-            suite.vec[k].copy_(t, non_blocking=True)
-        for k, t in hbig.items():
-            suite.big[k].copy_(t, non_blocking=True)
-        for k in KERNELS:
-            suite.call(k, 0)
-        for k, t in outs_h.items():
-            t.copy_(suite.r if k == "r" else suite.vec[k], non_blocking=True)
-        for k, t in outs_big_h.items():
-            t.copy_(suite.big[k], non_blocking=True)
-        hBout.copy_(suite.Bout, non_blocking=True)
+    # Copies overlap the kernels: inputs go host->device on their own stream in
+    # the order the kernels need them, each kernel waits for its own inputs
+    # only, and results go back on a third stream as soon as they exist
+    # (GEMVER's 2 GiB B while the other matrix kernels run).  A step starts
+    # after the previous one has finished, so no buffer is reused early.
+    sC = torch.cuda.current_stream()
+    sH = torch.cuda.Stream()
+    sD = torch.cuda.Stream()
 
-    st = torch.cuda.current_stream()
+    def rec(stream):
+        e = torch.cuda.Event()
+        e.record(stream)
+        return e
+
+    def step():
+        sH.wait_stream(sC)
+        sH.wait_stream(sD)
+        with torch.cuda.stream(sH):
+            for k, t in hbig.items():
+                suite.big[k].copy_(t, non_blocking=True)
+            e_big = rec(sH)
+            for k, t in hv.items():
+                suite.vec[k].copy_(t, non_blocking=True)
+            suite.A.copy_(hA, non_blocking=True)
+            e_a = rec(sH)
+            suite.B2.copy_(hB, non_blocking=True)
+            e_b = rec(sH)
+        sC.wait_event(e_big)
+        for k in ("axpydot", "waxpby", "vadd"):
+            suite.call(k, 0)
+        sD.wait_event(rec(sC))
+        with torch.cuda.stream(sD):
+            for k, t in outs_big_h.items():
+                t.copy_(suite.big[k], non_blocking=True)
+            outs_h["r"].copy_(suite.r, non_blocking=True)
+        sC.wait_event(e_a)
+        suite.call("gemver", 0)
+        sD.wait_event(rec(sC))
+        with torch.cuda.stream(sD):
+            hBout.copy_(suite.Bout, non_blocking=True)
+            for k in ("gx", "gw"):
+                outs_h[k].copy_(suite.vec[k], non_blocking=True)
+        for k in ("bicgk", "atax", "dgemv", "dgemvt"):
+            suite.call(k, 0)
+        sC.wait_event(e_b)
+        suite.call("gesummv", 0)
+        sD.wait_event(rec(sC))
+        with torch.cuda.stream(sD):
+            for k, t in outs_h.items():
+                if k not in ("r", "gx", "gw"):
+                    t.copy_(suite.vec[k], non_blocking=True)
+
+    st = sC
     for _ in range(warmup):
         step()
+    sC.wait_stream(sD)
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(st)
     for _ in range(steps):
         step()
+    sC.wait_stream(sD)
     t1.record(st)
     torch.cuda.synchronize()
     return t0.elapsed_time(t1) / steps, h2d, d2h

@@ -716,6 +716,7 @@ def main():
     from paper_1205_1098_gb300 import build
     build.build()
     import paper_1205_1098_gb300 as bto
+    from paper_1205_1098_gb300 import replicas
 
     m = n = args.n
     N = args.nvec
@@ -728,12 +729,8 @@ def main():
         ms, kern = timed_steps(torch, suite, args.steps, args.warmup, 0, dist)
     clocks = clk.summary()
     # max over ranks
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     step_bytes = suite_bytes(m, n, N)
-    value = world * step_bytes / (ms * 1e-3) / 1e9
+    value, ms = replicas.job_rate(torch, dist, step_bytes, ms, device="cuda")
 
     per = {}
     for k in KERNELS:
@@ -779,11 +776,8 @@ def main():
         del suite
         torch.cuda.empty_cache()
         ems, h2d, d2h = e2e_steps(torch, bto, max(2, args.steps // 3), 1, m, n, N)
-        if dist:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": round(world * step_bytes / (ems * 1e-3) / 1e9, 2), "unit": "GB/s",
+        evalue, ems = replicas.job_rate(torch, dist, step_bytes, ems, device="cuda")
+        e2e = {"value": round(evalue, 2), "unit": "GB/s",
                "ms_per_step": round(ems, 3), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     prec = None

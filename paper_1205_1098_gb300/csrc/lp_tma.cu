@@ -179,16 +179,27 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
             if (MODE == LP_G1) { sv1[k] = __ldg(a.v1 + c0 + k); sv2[k] = __ldg(a.v2 + c0 + k); }
         }
         named_bar(1, kConsumers);
+        // Row vectors of the next chunk are loaded one chunk ahead, so their
+        // latency overlaps the current chunk's stages.
+        float rvn[kRPT], u1n[kRPT], u2n[kRPT];
+        auto load_rows = [&](int64_t R) {
+#pragma unroll
+            for (int k = 0; k < kRPT; k++) {
+                const int64_t i = R + trow<V>(lane, k);
+                rvn[k] = (HAS_S && i < r1) ? __ldg(a.r + i) : 0.0f;
+                u1n[k] = (MODE == LP_G1 && i < r1) ? __ldg(a.u1 + i) : 0.0f;
+                u2n[k] = (MODE == LP_G1 && i < r1) ? __ldg(a.u2 + i) : 0.0f;
+            }
+        };
+        load_rows(r0);
         for (int64_t R0 = r0; R0 < r1; R0 += kBoxR) {
             float rv[kRPT], u1r[kRPT], u2r[kRPT], qhi[kRPT], qlo[kRPT], qt[kRPT], sl[16];
 #pragma unroll
             for (int k = 0; k < kRPT; k++) {
-                const int64_t i = R0 + trow<V>(lane, k);
-                rv[k] = (HAS_S && i < r1) ? __ldg(a.r + i) : 0.0f;
-                u1r[k] = (MODE == LP_G1 && i < r1) ? __ldg(a.u1 + i) : 0.0f;
-                u2r[k] = (MODE == LP_G1 && i < r1) ? __ldg(a.u2 + i) : 0.0f;
+                rv[k] = rvn[k]; u1r[k] = u1n[k]; u2r[k] = u2n[k];
                 qhi[k] = 0.0f; qlo[k] = 0.0f; qt[k] = 0.0f;
             }
+            if (R0 + kBoxR < r1) load_rows(R0 + kBoxR);
 #pragma unroll
             for (int k = 0; k < 16; k++) sl[k] = 0.0f;
             // Butterfly groups of GroupStages stages; the stage loop is unrolled so

@@ -120,9 +120,10 @@ struct LpArgs {
 // load-instruction sweep instead.
 bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, cudaStream_t st, bto_status* out);
 
-// ------------------------------------------------------------ ATAX wavefront
-// Rows are cut into bands of TB rows; block c of a cooperative grid of G
-// blocks owns a fixed slice of columns (so it owns those entries of y).
+// ------------------------------------------------------------ ATAX group bands
+// A cooperative grid of G blocks is cut into NG groups of S; group g takes
+// the bands of TB rows g, g + NG, ...; block r of a group owns a fixed slice
+// of about n / S columns.  Each group leaves a partial y over all columns.
 struct AtaxPlan {
     int G = 0;          // blocks (one per SM, a multiple of S)
     int S = 0;          // blocks per group

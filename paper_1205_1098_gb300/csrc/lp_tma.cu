@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
                     }
             }
             if (HAS_Q) {
-                // Add the eight warps' row sums (each warp saw other columns) in FP64.
+                // Add the eight warps' row sums (each warp saw other columns).
 #pragma unroll
                 for (int k = 0; k < kRPT; k++) {
                     qred[warp * kBoxR + trow<V>(lane, k)] = qhi[k];

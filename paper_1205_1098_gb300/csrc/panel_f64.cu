@@ -169,11 +169,17 @@ __device__ __host__ __forceinline__ int64_t row_split_at(int64_t m, int64_t part
     return (split_at(m, parts, b) / 64) * 64;
 }
 
-// Blocks per SM: the single-product modes fit in 128 registers and run two
-// blocks per SM, so one block's load latency overlaps the other's
-// arithmetic; the two-product modes need more registers than that.
+// Blocks per SM and columns loaded ahead.  Every mode runs two blocks per SM
+// (128 registers), so one block's latency is covered by the other's FP64
+// arithmetic; the two-product modes load one column ahead to fit, which
+// measured faster than four columns ahead at one block per SM (GEMVER's
+// first pass 2.20 -> 2.00 ms, BICGK 1.07 -> 0.98 ms, GESUMMV 1.13 -> 0.97 ms
+// at n = 16384): with FP64 the bound, a second resident block hides more
+// latency than loads issued early.
 template <int MODE>
-struct BlocksPerSM { static constexpr int value = (MODE == PM_Q || MODE == PM_S) ? 2 : 1; };
+struct BlocksPerSM { static constexpr int value = 2; };
+template <int MODE>
+struct ColsAhead { static constexpr int value = (MODE == PM_Q || MODE == PM_S) ? kU : 1; };
 
 template <int MODE, int VEC>
 __global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kernel(const PanelArgs a) {
@@ -208,12 +214,13 @@ __global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kern
             for (int64_t g0 = c0; g0 < c1; g0 += kGroup) {
                 const int nc = (int)((c1 - g0) < kGroup ? (c1 - g0) : kGroup);
                 double sl[kGroup];
+                constexpr int KU = ColsAhead<MODE>::value;
 #pragma unroll
-                for (int jb = 0; jb < kGroup; jb += kU) {
-                    // Issue the loads of kU columns before consuming any of them.
-                    double av[kU][kRPT], bv[kU][kRPT], pj[kU], v1j[kU], v2j[kU];
+                for (int jb = 0; jb < kGroup; jb += KU) {
+                    // Issue the loads of KU columns before consuming any of them.
+                    double av[KU][kRPT], bv[KU][kRPT], pj[KU], v1j[KU], v2j[KU];
 #pragma unroll
-                    for (int u = 0; u < kU; u++) {
+                    for (int u = 0; u < KU; u++) {
                         const int jj = jb + u;
                         if (jj < nc) {
                             const int64_t j = g0 + jj;
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kern
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < kU; u++) {
+                    for (int u = 0; u < KU; u++) {
                         const int jj = jb + u;
                         if (jj < nc) {
                             const int64_t j = g0 + jj;

@@ -12,14 +12,19 @@
 //     groups of S blocks (S = 16 for n <= 65536).  Group g takes the 16-row bands
 //     g, g + NG, g + 2 NG, ...; inside a group, block r owns a fixed slice
 //     of about n / S columns.
-//   - Pass 1 over band b (the first column loop): each thread sums its
-//     columns' 16-row segments (128 contiguous bytes per column) times x_j
-//     into 16 partial t_i; a warp butterfly and the warps, in a fixed order,
-//     give the block's partial of t_b; the S partials meet in a
+//   - Pass 1 over band b (the first column loop): lane l of a warp owns the
+//     row pair 2 (l mod 8), 2 (l mod 8) + 1 of the band and every fourth of
+//     the warp's columns, so a warp load covers four whole 128-byte column
+//     segments and each lane keeps two partial t_i; two exchanges across the
+//     column lanes and the warps, in a fixed order, give the block's partial
+//     of t_b.  FP64 arithmetic is the bound on this part (2 FMA per clock per
+//     SM), so the mapping keeps the adds outside the FMAs to four per lane
+//     per band.  The S partials meet in a
 //     double-buffered slot in L2 behind per-block release flags, and every
 //     block adds them in rank order, so all blocks hold the same t_b.
 //   - Pass 2 over band b (the second column loop): y_j += sum_i A(i,j) t_i
-//     for the block's columns, re-reading the band while it is still in L2
+//     for the block's columns (one thread per column, the FMAs chained onto
+//     y_j), re-reading the band while it is still in L2
 //     (two bands per group are in flight: about 80 MB at n = 16384), so HBM
 //     sees A once.
 //   - Pass 1 of band b+1 runs before the wait for t_b, so the exchange
@@ -95,26 +100,6 @@ __device__ __forceinline__ void load_seg(const double* col, bool whole, int rows
     }
 }
 
-// Sums tp[TB] (TB = 8 or 16) over the 32 lanes of a warp by halving
-// exchanges; afterwards lane l holds the warp's sum for row (l >> 1) mod TB
-// (the lanes that share a row agree).
-template <int TB>
-__device__ __forceinline__ double warp_reduce(double (&tp)[TB], int lane) {
-#pragma unroll
-    for (int h = TB / 2; h >= 1; h >>= 1) {
-        const bool upper = (lane & (2 * h)) != 0;      // this lane keeps rows [h, 2h) of each 2h-group
-#pragma unroll
-        for (int i = 0; i < h; i++) {
-            const double send = upper ? tp[i] : tp[i + h];
-            const double recv = __shfl_xor_sync(0xffffffffu, send, 2 * h);
-            tp[i] = (upper ? tp[i + h] : tp[i]) + recv;
-        }
-    }
-    double w = tp[0] + __shfl_xor_sync(0xffffffffu, tp[0], 1);
-    if (TB == 8) w += __shfl_xor_sync(0xffffffffu, w, 16);
-    return w;
-}
-
 template <int TB, int D, bool VEC2>
 __global__ void __launch_bounds__(kThreads, kBlocksPerSM) atax_kernel(const AtaxArgs a) {
     constexpr int NSL = 2 * D;               // partial slots per group (see publish)
@@ -144,19 +129,37 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) atax_kernel(const Atax
         const int64_t R0 = (g + q * a.NG) * TB;
         const int rows = (int)(a.m - R0 < TB ? a.m - R0 : TB);
         const bool whole = rows == TB;
-        double tp[TB];
-#pragma unroll
-        for (int i = 0; i < TB; i++) tp[i] = 0.0;
-#pragma unroll 2
-        for (int jl = threadIdx.x; jl < nc; jl += kThreads) {
-            double v[TB];
-            load_seg<TB, VEC2>(a.A + (c0 + jl) * a.lda + R0, whole && vec_ok, rows, v);
-            const double xj = xs[jl];
-#pragma unroll
-            for (int i = 0; i < TB; i++) tp[i] = fma(v[i], xj, tp[i]);
+        constexpr int RP = TB / 2;              // row pairs per band = lanes per column
+        constexpr int CPW = 32 / RP;            // columns a warp covers per load
+        const int rp = lane % RP;
+        const int i0 = 2 * rp;
+        const int jb = warp * CPW + lane / RP;
+        double t0 = 0.0, t1 = 0.0;
+        // The two loops differ only in how a row pair is loaded; keeping the
+        // test outside lets the eight-fold unrolled loads issue together.
+        if (whole && vec_ok) {
+#pragma unroll 8
+            for (int jl = jb; jl < nc; jl += kWarps * CPW) {
+                const double2 v = __ldg(reinterpret_cast<const double2*>(a.A + (c0 + jl) * a.lda + R0 + i0));
+                const double xj = xs[jl];
+                t0 = fma(v.x, xj, t0);
+                t1 = fma(v.y, xj, t1);
+            }
+        } else {
+#pragma unroll 4
+            for (int jl = jb; jl < nc; jl += kWarps * CPW) {
+                const double* col = a.A + (c0 + jl) * a.lda + R0 + i0;
+                const double xj = xs[jl];
+                t0 = fma(i0 < rows ? __ldg(col) : 0.0, xj, t0);
+                t1 = fma(i0 + 1 < rows ? __ldg(col + 1) : 0.0, xj, t1);
+            }
         }
-        const double w = warp_reduce<TB>(tp, lane);
-        if ((lane & 1) == 0 && (lane >> 1) < TB) red[warp][lane >> 1] = w;
+#pragma unroll
+        for (int h = RP; h < 32; h *= 2) {
+            t0 += __shfl_xor_sync(0xffffffffu, t0, h);
+            t1 += __shfl_xor_sync(0xffffffffu, t1, h);
+        }
+        if (lane < RP) { red[warp][i0] = t0; red[warp][i0 + 1] = t1; }
         __syncthreads();
         if (threadIdx.x < TB) {
             double t = red[0][threadIdx.x];
@@ -221,17 +224,17 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSM) atax_kernel(const Atax
         const int64_t R0 = (g + q * a.NG) * TB;
         const int rows = (int)(a.m - R0 < TB ? a.m - R0 : TB);
         const bool whole = rows == TB;
+        double tr[TB];
+#pragma unroll
+        for (int i = 0; i < TB; i++) tr[i] = ts[i];
 #pragma unroll 2
         for (int jl = threadIdx.x; jl < nc; jl += kThreads) {
             double v[TB];
             load_seg<TB, VEC2>(a.A + (c0 + jl) * a.lda + R0, whole && vec_ok, rows, v);
-            double e0 = 0.0, e1 = 0.0;
+            double e = ys[jl];
 #pragma unroll
-            for (int i = 0; i < TB; i += 2) {
-                e0 = fma(v[i], ts[i], e0);
-                e1 = fma(v[i + 1], ts[i + 1], e1);
-            }
-            ys[jl] += e0 + e1;
+            for (int i = 0; i < TB; i++) e = fma(v[i], tr[i], e);
+            ys[jl] = e;
         }
     };
 

@@ -169,9 +169,9 @@ bto_status bto_vadd(int64_t n, const double *w, const double *y, const double *z
                     double *x, bto_stream_t stream);
 
 /* ------------------------------------------- reduced-precision storage form
- * BICGK and GEMVER (Table I) with the matrix stored in FP32 or BF16 to cut
- * the bytes of this bandwidth-bound path (the paper's kernels are FP64; this
- * form has no counterpart there).  a_type is BTO_F32 or BTO_BF16 (raw BF16
+ * BICGK, GEMVER, ATAX and GESUMMV (Table I) with the matrices stored in FP32
+ * or BF16 to cut the bytes of this bandwidth-bound path (the paper's kernels
+ * are FP64; this form has no counterpart there).  a_type is BTO_F32 or BTO_BF16 (raw BF16
  * bits, as uint16).  Vectors and outputs are FP32.  Arithmetic is FP32 with
  * compensated accumulation: products are summed in short FP32 FMA chains
  * (16 columns for A p, 8 rows for A^T r) that are folded into TwoSum
@@ -194,6 +194,22 @@ bto_status bto_gemver_ex(int64_t m, int64_t n, float alpha, float beta, int a_ty
                          const float *u2, const float *v2, const float *y, const float *z,
                          void *B, int64_t ldb, float *x, float *w,
                          void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* BATAX (Section II, Fig. 1): y <- beta A^T (A x), A m x n (lda) of type
+ * a_type; x: n, y: n (output).  Two sweeps: t = A x is formed and rounded to
+ * FP32 in the workspace, then y = beta A^T t, so A is read twice (the FP64
+ * form's single-read kernel pays an exchange between blocks that only an
+ * arithmetic-bound sweep can hide). */
+bto_status bto_atax_ex(int64_t m, int64_t n, float beta, int a_type, const void *A, int64_t lda,
+                       const float *x, float *y, void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* GESUMMV (Table I): y <- alpha A x + beta B x, A and B m x n (lda, ldb) of
+ * type a_type; x: n, y: m (output).  One sweep per matrix; a single combine
+ * adds both scaled sums in FP64 and rounds once. */
+bto_status bto_gesummv_ex(int64_t m, int64_t n, float alpha, float beta, int a_type,
+                          const void *A, int64_t lda, const void *B, int64_t ldb,
+                          const float *x, float *y, void *ws, size_t ws_bytes,
+                          bto_stream_t stream);
 
 /* ------------------------------------------------------------ batched form
  * Many independent, uneven BICGK, GEMVER, ATAX and GESUMMV instances
@@ -241,6 +257,79 @@ bto_status bto_batch_prepare(int count, const bto_batch_desc *descs, int tile_co
 
 /* Runs a prepared batch on `stream` (a reset kernel and the persistent kernel). */
 bto_status bto_batch_run(void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* Plans and launches a batch in one call: the plan is copied into ws
+ * (status word and counters zeroed, so no reset kernel runs) through
+ * `staging` when it is pinned host memory of at least the plan's size (the
+ * caller keeps it unchanged until the stream has passed the copy), else
+ * through a pageable copy that the call waits for; then only the kernels of
+ * the non-empty queues are launched, each grid no larger than its items, so
+ * that a small batch leaves the other SMs to other streams.  Same results as
+ * bto_batch_prepare + bto_batch_run.  Not for graph capture when staging is
+ * NULL (the call waits). */
+bto_status bto_batch_submit(int count, const bto_batch_desc *descs, int tile_cols, void *ws,
+                            size_t ws_bytes, void *staging, size_t staging_bytes,
+                            bto_stream_t stream);
+
+/* ------------------------------------------------------------ serving runtime
+ * Continuous batching of BICGK, ATAX, GEMVER and GESUMMV requests (Table I)
+ * over resident operands, scheduled by a native polling loop on the calling
+ * thread (no counterpart in the paper).  Requests arrive at their times t
+ * (seconds after the call starts; non-decreasing); each is an n x n problem
+ * on the leading block of a resident nmax x nmax matrix of its storage type
+ * (ld nmax) and prefixes of the resident vectors, with FP32 outputs.
+ *   - A request with n >= direct_n (direct_n > 0) runs alone through
+ *     bto_bicgk_ex / bto_gemver_ex / bto_atax_ex / bto_gesummv_ex.
+ *   - Otherwise requests from the head of the arrival queue form a batch
+ *     (at most max_batch, stopping before a direct one) launched with the
+ *     batched form's plan-and-submit path (tile_cols as there).
+ *   - A launch goes to a free slot (one per caller stream); launches on
+ *     different slots overlap on the device.
+ *   - Outputs, GEMVER's B and workspaces are carved from the caller's device
+ *     arena (the HBM budget): admission waits while they do not fit; a request
+ *     that cannot fit with nothing in flight ends with BTO_ERR_BUDGET.
+ * A request's path and arithmetic depend on the request alone, so its
+ * results are the same bits alone and in any mix.  Outputs of finished
+ * requests are released unless keep_results (then res->out give their arena
+ * offsets, valid until the arena is reused).  Returns BTO_OK, or the first
+ * launch or device status that was not BTO_OK (every request still ends). */
+typedef struct bto_serve_req {
+    double t;            /* arrival, seconds after the start of the call          */
+    int32_t op;          /* BTO_OP_BICGK, BTO_OP_ATAX, BTO_OP_GEMVER, BTO_OP_GESUMMV */
+    int32_t a_type;      /* BTO_F32 or BTO_BF16: which resident matrices           */
+    int64_t n;           /* 1 <= n <= nmax                                         */
+} bto_serve_req;
+
+typedef struct bto_serve_res {
+    double admit;        /* seconds after the start: launched (-1: never)                  */
+    double done;         /* seconds after the start: completion observed (-1: never)       */
+    int64_t out[3];      /* arena byte offsets: outputs 0 and 1 (as bto_batch_desc.out),     */
+                         /* GEMVER's B (n x n, ld n, storage type); -1 where none           */
+    int32_t status;      /* BTO_OK, the device status of its launch, or BTO_ERR_BUDGET     */
+    int32_t direct;      /* 1: served alone by a bto_*_ex entry point                      */
+} bto_serve_res;
+
+typedef struct bto_serve_cfg {
+    const void *A[2][2];          /* [F32, BF16][A, GESUMMV's B]: nmax x nmax, ld nmax          */
+    const float *vec[6];          /* resident vectors (>= nmax): inputs in bto_batch_desc order */
+    void *arena;                  /* device memory, 256-byte aligned: the HBM budget             */
+    void *staging;                /* pinned host memory, 256-byte aligned (or NULL)              */
+    const bto_stream_t *streams;  /* nstreams launch slots                                       */
+    size_t arena_bytes, staging_bytes;
+    int64_t nmax, direct_n;
+    double max_wall;              /* stop admitting after this many seconds (0: no limit)        */
+    float alpha, beta;            /* GEMVER, GESUMMV: alpha, beta; ATAX: beta                    */
+    int32_t nstreams;             /* 1..64                                                       */
+    int32_t max_batch, tile_cols, keep_results;
+} bto_serve_cfg;
+
+typedef struct bto_serve_stats {
+    int64_t served, batches, direct, rejected;
+    double wall_s, peak_bytes;    /* run time; high-water mark of the arena in use */
+} bto_serve_stats;
+
+bto_status bto_serve_run(const bto_serve_cfg *cfg, int64_t count, const bto_serve_req *req,
+                         bto_serve_res *res, bto_serve_stats *stats);
 
 /* ------------------------------------------------- multi-right-hand-side BICGK
  * The BICGK kernel of Table I with k right-hand sides at once (the paper has

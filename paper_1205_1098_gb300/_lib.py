@@ -42,8 +42,11 @@ SIGNATURES = {
     "bto_bicgk_noalloc": "iipipppps",
     "bto_bicgk_ex": "iikpipppppzs",
     "bto_gemver_ex": "iiffkpipppppppipppzs",
+    "bto_atax_ex": "iifkpipppzs",
+    "bto_gesummv_ex": "iiffkpipipppzs",
     "bto_batch_prepare": "kpkpzs",
     "bto_batch_run": "pzs",
+    "bto_batch_submit": "kpkpzpzs",
     "bto_bicgk_mrhs": "iiipipipipipipzs",
 }
 _KIND = {"i": _c_i64, "u": _c_u64, "d": _c_f64, "f": ctypes.c_float, "p": _c_ptr, "z": _c_size,
@@ -216,8 +219,50 @@ def bto_batch_workspace_bytes(descs, tile_cols=0):
     return out.value
 
 
+class ServeReq(ctypes.Structure):
+    """bto_serve_req of include/bto.h."""
+    _fields_ = [("t", ctypes.c_double), ("op", ctypes.c_int32), ("a_type", ctypes.c_int32), ("n", ctypes.c_int64)]
+
+
+class ServeRes(ctypes.Structure):
+    """bto_serve_res of include/bto.h."""
+    _fields_ = [("admit", ctypes.c_double), ("done", ctypes.c_double), ("out", ctypes.c_int64 * 3),
+                ("status", ctypes.c_int32), ("direct", ctypes.c_int32)]
+
+
+class ServeCfg(ctypes.Structure):
+    """bto_serve_cfg of include/bto.h."""
+    _fields_ = [("A", (ctypes.c_void_p * 2) * 2), ("vec", ctypes.c_void_p * 6), ("arena", ctypes.c_void_p),
+                ("staging", ctypes.c_void_p), ("streams", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
+                ("staging_bytes", ctypes.c_size_t), ("nmax", ctypes.c_int64), ("direct_n", ctypes.c_int64),
+                ("max_wall", ctypes.c_double), ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
+                ("nstreams", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("tile_cols", ctypes.c_int32),
+                ("keep_results", ctypes.c_int32)]
+
+
+class ServeStats(ctypes.Structure):
+    """bto_serve_stats of include/bto.h."""
+    _fields_ = [("served", ctypes.c_int64), ("batches", ctypes.c_int64), ("direct", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("wall_s", ctypes.c_double), ("peak_bytes", ctypes.c_double)]
+
+
+def bto_serve_run(cfg, count, reqs, res, stats):
+    """Runs the serving loop over reqs[:count]; returns its status (BTO_OK or the
+    first launch or device status that was not), raising only for invalid
+    arguments."""
+    L = lib()
+    L.bto_serve_run.argtypes = [ctypes.c_void_p, _c_i64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.bto_serve_run.restype = _c_int
+    st = L.bto_serve_run(ctypes.addressof(cfg), int(count), ctypes.cast(reqs, ctypes.c_void_p),
+                         ctypes.cast(res, ctypes.c_void_p), ctypes.addressof(stats))
+    if st in (BTO_ERR_INVALID_VALUE, BTO_ERR_WORKSPACE):
+        raise BtoError("bto_serve_run", st, L.bto_last_invalid_arg())
+    return st
+
+
 def exported_symbols():
     """Names the binding expects libbto.so to export."""
     return sorted(list(SIGNATURES) + ["bto_version", "bto_status_string", "bto_last_invalid_arg",
                                       "bto_workspace_bytes", "bto_device_status",
-                                      "bto_bicgk_mrhs_workspace_bytes"])
+                                      "bto_bicgk_mrhs_workspace_bytes", "bto_batch_workspace_bytes",
+                                      "bto_serve_run"])

@@ -642,6 +642,7 @@ constexpr size_t kSmemBytes = (4 * kWarps * kRows + 2 * kMaxTile) * sizeof(float
 
 struct Plan {
     Header h{};
+    std::vector<bto_batch_desc> descs;
     std::vector<InstInfo> info;
     std::vector<Item> items;
 };
@@ -673,7 +674,9 @@ bool valid_desc(const bto_batch_desc& d) {
 }
 
 bool make_plan(int count, const bto_batch_desc* descs, int tile_cols, Plan* P, int* bad_desc) {
+    P->descs.assign(descs, descs + count);
     P->info.resize(count);
+    P->items.clear();
     std::vector<std::pair<double, Item>> first, second;
     int64_t qsize = 0, tsize = 0;
     for (int i = 0; i < count; i++) {
@@ -756,7 +759,99 @@ bool make_plan(int count, const bto_batch_desc* descs, int tile_cols, Plan* P, i
 
 bool check_tile(int tile_cols) { return tile_cols >= 16 && tile_cols <= kMaxTile && tile_cols % 16 == 0; }
 
+// Resident blocks per SM of the persistent kernels (set up once).
+int batch_occupancy() {
+    static int occ = 0;
+    if (occ == 0) {
+        int o = 0;
+        if (cudaFuncSetAttribute(batch_kernel<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
+            cudaFuncSetAttribute(batch_kernel<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
+            cudaFuncSetAttribute(batch_kernel<__nv_bfloat16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
+            cudaFuncSetAttribute(batch_kernel<__nv_bfloat16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, batch_kernel<float, 0>, kThreads, kSmemBytes) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        occ = std::max(o, 1);
+    }
+    return occ;
+}
+
+// The plan's device image: status word, header, descriptors, instance
+// records, items and, when `counters`, the zeroed counters (which then need
+// no reset kernel).
+size_t image_bytes(const Plan& P, bool counters) {
+    return (size_t)P.h.off_counters + (counters ? (size_t)P.h.counters_bytes : 0);
+}
+
+void write_image(const Plan& P, char* img, bool counters) {
+    std::memset(img, 0, image_bytes(P, counters));
+    std::memcpy(img + kHeaderOff, &P.h, sizeof(Header));
+    const size_t count = P.descs.size();
+    if (count) std::memcpy(img + P.h.off_desc, P.descs.data(), count * sizeof(bto_batch_desc));
+    if (count) std::memcpy(img + P.h.off_info, P.info.data(), P.info.size() * sizeof(InstInfo));
+    if (!P.items.empty()) std::memcpy(img + P.h.off_items, P.items.data(), P.items.size() * sizeof(Item));
+}
+
+bto_status submit_plan(const Plan& P, void* ws, size_t ws_bytes, void* staging, size_t staging_bytes,
+                       cudaStream_t st) {
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < (size_t)P.h.total) return BTO_ERR_WORKSPACE;
+    DeviceInfo dinf;
+    if (!device_info(&dinf)) return BTO_ERR_CUDA;
+    const int occ = batch_occupancy();
+    if (occ == 0) return BTO_ERR_CUDA;
+    const size_t nb = image_bytes(P, true);
+    if (staging && staging_bytes >= nb) {
+        // Pinned staging that the caller keeps until the stream has passed
+        // this copy: no host wait.
+        write_image(P, static_cast<char*>(staging), true);
+        if (cudaMemcpyAsync(ws, staging, nb, cudaMemcpyHostToDevice, st) != cudaSuccess) return BTO_ERR_CUDA;
+    } else {
+        std::vector<char> img(nb);
+        write_image(P, img.data(), true);
+        if (cudaMemcpyAsync(ws, img.data(), nb, cudaMemcpyHostToDevice, st) != cudaSuccess) return BTO_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return BTO_ERR_CUDA;
+    }
+    // Only the queues that hold items, each grid no larger than its items:
+    // a small batch leaves the other SMs to work on other streams.
+    char* w = static_cast<char*>(ws);
+    const int64_t full = (int64_t)dinf.sms * occ;
+    for (int q = 0; q < kQueues; q++) {
+        const int64_t ni = P.h.qstart[q + 1] - P.h.qstart[q];
+        if (ni == 0) continue;
+        const int grid = (int)std::min<int64_t>(full, ni);
+        switch (q) {
+            case 0: batch_kernel<float, 0><<<grid, kThreads, kSmemBytes, st>>>(w); break;
+            case 1: batch_kernel<float, 1><<<grid, kThreads, kSmemBytes, st>>>(w); break;
+            case 2: batch_kernel<__nv_bfloat16, 0><<<grid, kThreads, kSmemBytes, st>>>(w); break;
+            default: batch_kernel<__nv_bfloat16, 1><<<grid, kThreads, kSmemBytes, st>>>(w); break;
+        }
+    }
+    return launch_status();
+}
+
 }  // namespace
+
+struct BatchPlan {
+    Plan p;
+};
+
+BatchPlan* batch_plan_create() { return new BatchPlan(); }
+void batch_plan_destroy(BatchPlan* b) { delete b; }
+
+bool batch_plan_build(BatchPlan* b, int count, const bto_batch_desc* descs, int tile_cols, size_t* ws_bytes) {
+    int bad = -1;
+    if (count < 0 || (count > 0 && !descs) || !check_tile(tile_cols)) return false;
+    if (!make_plan(count, descs, tile_cols, &b->p, &bad)) return false;
+    *ws_bytes = (size_t)b->p.h.total;
+    return true;
+}
+
+bto_status batch_plan_submit(const BatchPlan* b, void* ws, size_t ws_bytes, void* staging, size_t staging_bytes,
+                             cudaStream_t st) {
+    return submit_plan(b->p, ws, ws_bytes, staging, staging_bytes, st);
+}
+
 }  // namespace bto
 
 using namespace bto;
@@ -790,12 +885,10 @@ extern "C" bto_status bto_batch_prepare(int count, const bto_batch_desc* descs, 
         set_invalid_arg(4);
         return BTO_ERR_WORKSPACE;
     }
-    // Stage the plan in one host image and copy it with one transfer.
-    std::vector<char> img((size_t)P.h.off_counters, 0);
-    std::memcpy(img.data() + kHeaderOff, &P.h, sizeof(Header));
-    if (count) std::memcpy(img.data() + P.h.off_desc, descs, (size_t)count * sizeof(bto_batch_desc));
-    if (count) std::memcpy(img.data() + P.h.off_info, P.info.data(), P.info.size() * sizeof(InstInfo));
-    if (!P.items.empty()) std::memcpy(img.data() + P.h.off_items, P.items.data(), P.items.size() * sizeof(Item));
+    // Stage the plan in one host image and copy it with one transfer; the
+    // counters are reset by bto_batch_run's first kernel.
+    std::vector<char> img(image_bytes(P, false));
+    write_image(P, img.data(), false);
     if (cudaMemcpyAsync(ws, img.data(), img.size(), cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess)
         return BTO_ERR_CUDA;
     // The host image is released on return: wait for the copy to leave it.
@@ -809,18 +902,11 @@ extern "C" bto_status bto_batch_run(void* ws, size_t ws_bytes, bto_stream_t stre
     if (ws_bytes < 1024) { set_invalid_arg(2); return BTO_ERR_WORKSPACE; }
     DeviceInfo dinf;
     if (!device_info(&dinf)) return BTO_ERR_CUDA;
-    static int occ = 0;
-    if (occ == 0) {
-        if (cudaFuncSetAttribute(batch_kernel<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
-            cudaFuncSetAttribute(batch_kernel<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
-            cudaFuncSetAttribute(batch_kernel<__nv_bfloat16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
-            cudaFuncSetAttribute(batch_kernel<__nv_bfloat16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel<float, 0>, kThreads, kSmemBytes) != cudaSuccess)
-            return BTO_ERR_CUDA;
-    }
+    const int occ = batch_occupancy();
+    if (occ == 0) return BTO_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     char* w = static_cast<char*>(ws);
-    const int grid = dinf.sms * std::max(occ, 1);
+    const int grid = dinf.sms * occ;
     batch_reset_kernel<<<1, 256, 0, st>>>(w);
     if (cudaGetLastError() != cudaSuccess) return BTO_ERR_CUDA;
     // One kernel per queue, in order; a kernel whose queue is empty exits at once.
@@ -829,4 +915,20 @@ extern "C" bto_status bto_batch_run(void* ws, size_t ws_bytes, bto_stream_t stre
     batch_kernel<__nv_bfloat16, 0><<<grid, kThreads, kSmemBytes, st>>>(w);
     batch_kernel<__nv_bfloat16, 1><<<grid, kThreads, kSmemBytes, st>>>(w);
     return launch_status();
+}
+
+extern "C" bto_status bto_batch_submit(int count, const bto_batch_desc* descs, int tile_cols, void* ws,
+                                       size_t ws_bytes, void* staging, size_t staging_bytes,
+                                       bto_stream_t stream) {
+    clear_invalid_arg();
+    if (count < 0) { set_invalid_arg(1); return BTO_ERR_INVALID_VALUE; }
+    if (count > 0 && !descs) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
+    if (tile_cols == 0) tile_cols = 128;
+    if (!check_tile(tile_cols)) { set_invalid_arg(3); return BTO_ERR_INVALID_VALUE; }
+    Plan P;
+    int bad = -1;
+    if (!make_plan(count, descs, tile_cols, &P, &bad)) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
+    const bto_status e = submit_plan(P, ws, ws_bytes, staging, staging_bytes, (cudaStream_t)stream);
+    if (e == BTO_ERR_WORKSPACE) set_invalid_arg(4);
+    return e;
 }

@@ -101,7 +101,24 @@ __host__ __device__ inline int64_t lp_row_at(int64_t m, int64_t NR, int64_t rb) 
 inline int64_t lp_col_unit(int a_type) { return a_type == BTO_BF16 ? 32 : 16; }
 PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type);
 
-enum LpMode { LP_QS = 0, LP_Q = 1, LP_G1 = 2 };
+// Batched form, planned once and submitted (the serving runtime's path).
+struct BatchPlan;
+BatchPlan* batch_plan_create();
+void batch_plan_destroy(BatchPlan* b);
+// Validates `count` descriptors and builds their work list; *ws_bytes is the
+// workspace the plan needs.  False on an invalid descriptor or tile width.
+bool batch_plan_build(BatchPlan* b, int count, const bto_batch_desc* descs, int tile_cols, size_t* ws_bytes);
+// Copies the plan (status word and counters zeroed) into ws, through the
+// pinned `staging` buffer when it is large enough (the caller keeps it until
+// the stream has passed the copy) or a pageable copy that is waited for, and
+// launches the kernels of the non-empty queues, each grid at most its items.
+bto_status batch_plan_submit(const BatchPlan* b, void* ws, size_t ws_bytes, void* staging, size_t staging_bytes,
+                             cudaStream_t st);
+
+// Sweeps of the reduced-precision form: q = A p and s = A^T r together
+// (BICGK), q alone, GEMVER's first pass (B, B^T y), s alone (ATAX's second
+// pass).
+enum LpMode { LP_QS = 0, LP_Q = 1, LP_G1 = 2, LP_S = 3 };
 
 struct LpArgs {
     int64_t m, n;

@@ -1,5 +1,6 @@
-// TMA-fed sweep of the reduced-precision storage form (BICGK and both GEMVER
-// passes with A or B in FP32/BF16).
+// TMA-fed sweep of the reduced-precision storage form (BICGK, both GEMVER
+// passes, and the q-only and s-only sweeps that ATAX and GESUMMV are made of,
+// with the matrices in FP32/BF16).
 //
 // Each stage is a 256-row x 16-column box of the matrix, copied by the tensor
 // memory accelerator (cp.async.bulk.tensor) into a ring of shared-memory
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_const
     constexpr int kBoxC = Cfg<TA>::BoxC;
     constexpr int CPW = Cfg<TA>::CPW;
     constexpr bool HAS_Q = (MODE == LP_QS || MODE == LP_Q);
-    constexpr bool HAS_S = (MODE == LP_QS || MODE == LP_G1);
+    constexpr bool HAS_S = (MODE == LP_QS || MODE == LP_G1 || MODE == LP_S);
     extern __shared__ __align__(1024) unsigned char smem[];
     TA* ring = reinterpret_cast<TA*>(smem);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes<TA>());
@@ -402,7 +403,7 @@ PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type) {
 
 bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, cudaStream_t st, bto_status* out) {
     const size_t es = a_type == BTO_F32 ? 4 : 2;
-    const void* base = (mode == LP_Q || mode == LP_QS || mode == LP_G1) ? a.A : nullptr;
+    const void* base = a.A;
     CUtensorMap map;
     const CUtensorMapDataType dt = a_type == BTO_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     // In place (B == A) the B stores of one stage must not overwrite elements
@@ -419,12 +420,14 @@ bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, cudaStream_t
             case LP_QS: *out = launch_t<float, LP_QS>(map, a, grid, st); return true;
             case LP_Q: *out = launch_t<float, LP_Q>(map, a, grid, st); return true;
             case LP_G1: *out = launch_t<float, LP_G1>(map, a, grid, st); return true;
+            case LP_S: *out = launch_t<float, LP_S>(map, a, grid, st); return true;
         }
     } else {
         switch (mode) {
             case LP_QS: *out = launch_t<__nv_bfloat16, LP_QS>(map, a, grid, st); return true;
             case LP_Q: *out = launch_t<__nv_bfloat16, LP_Q>(map, a, grid, st); return true;
             case LP_G1: *out = launch_t<__nv_bfloat16, LP_G1>(map, a, grid, st); return true;
+            case LP_S: *out = launch_t<__nv_bfloat16, LP_S>(map, a, grid, st); return true;
         }
     }
     return false;

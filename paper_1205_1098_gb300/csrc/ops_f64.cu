@@ -16,10 +16,11 @@ size_t region(size_t& cur, size_t bytes) {
 
 bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type, const DeviceInfo& d,
                      WsLayout* out) {
-    // Reduced-precision storage exists for the fused BICGK and GEMVER forms
-    // (bto_bicgk_ex, bto_gemver_ex); their partials are FP64 like the FP64 form's.
+    // Reduced-precision storage exists for the fused BICGK, GEMVER, ATAX and
+    // GESUMMV forms (bto_*_ex); their partials take the FP64 form's space.
     if (a_type != BTO_F64 &&
-        !(form == BTO_FORM_FUSED && (op == BTO_OP_BICGK || op == BTO_OP_GEMVER)))
+        !(form == BTO_FORM_FUSED && (op == BTO_OP_BICGK || op == BTO_OP_GEMVER || op == BTO_OP_ATAX ||
+                                     op == BTO_OP_GESUMMV)))
         return BTO_ERR_UNSUPPORTED;
     WsLayout L;
     size_t cur = WS_HEADER;
@@ -41,7 +42,7 @@ bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type, const D
             if (form == BTO_FORM_FUSED) L.off[1] = region(cur, qp);
             break;
         case BTO_OP_ATAX:
-            if (form == BTO_FORM_FUSED) {
+            if (form == BTO_FORM_FUSED && a_type == BTO_F64) {
                 const AtaxPlan ap = atax_plan(m, n, d);
                 if (ap.fused) {
                     L.off[0] = region(cur, (size_t)std::max(ap.G, 1) * sizeof(unsigned));             // per-block flags

@@ -93,7 +93,7 @@ __device__ __forceinline__ void lp_load_vec(const float* v, int64_t R0, int64_t 
 template <typename TA, int MODE, int V>
 __global__ void __launch_bounds__(kThreads, 1) lp_panel_kernel(const LpArgs a) {
     constexpr bool HAS_Q = (MODE == LP_QS || MODE == LP_Q);
-    constexpr bool HAS_S = (MODE == LP_QS || MODE == LP_G1);
+    constexpr bool HAS_S = (MODE == LP_QS || MODE == LP_G1 || MODE == LP_S);
     extern __shared__ float sws[];   // [2][kWarps][tcmax]: hi, lo per warp and column
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t tcmax = a.tcmax;
@@ -225,28 +225,38 @@ __global__ void __launch_bounds__(kThreads, 1) lp_panel_kernel(const LpArgs a) {
 // compensated (hi, lo) FP32 pair; the pairs are converted and added in FP64
 // in a fixed order (8 warps over the partials of 32 outputs, merged in warp
 // order), and the result is rounded once to FP32.
+// A second set of partials P2 (K2 of them, scaled by a2) may be added:
+// out = a1 sum P + a2 sum P2 (GESUMMV's two products), each sum formed as
+// above and the two scaled sums added in FP64 before the one rounding.
 constexpr int kCW = 8;
 __global__ void __launch_bounds__(kCW * 32) lp_combine_kernel(float* out, int64_t len, const double* P,
                                                              int64_t ld, int K, double a1, const float* v,
-                                                             double b) {
-    __shared__ double red[kCW][32];
+                                                             double b, const double* P2, int K2, double a2) {
+    __shared__ double red[2][kCW][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nblk = (len + 31) / 32;
     for (int64_t bI = blockIdx.x; bI < nblk; bI += gridDim.x) {
         const int64_t i = bI * 32 + lane;
-        double acc = 0.0;
-        if (i < len)
+        double acc = 0.0, acc2 = 0.0;
+        if (i < len) {
             for (int k = w; k < K; k += kCW) {
                 const float2 h = __ldg(reinterpret_cast<const float2*>(P) + (int64_t)k * ld + i);
                 acc += (double)h.x + (double)h.y;
             }
-        red[w][lane] = acc;
+            for (int k = w; k < K2; k += kCW) {
+                const float2 h = __ldg(reinterpret_cast<const float2*>(P2) + (int64_t)k * ld + i);
+                acc2 += (double)h.x + (double)h.y;
+            }
+        }
+        red[0][w][lane] = acc;
+        red[1][w][lane] = acc2;
         __syncthreads();
         if (w == 0 && i < len) {
-            double s = red[0][lane];
+            double s = red[0][0][lane], s2 = red[1][0][lane];
 #pragma unroll
-            for (int q = 1; q < kCW; q++) s += red[q][lane];
+            for (int q = 1; q < kCW; q++) { s += red[0][q][lane]; s2 += red[1][q][lane]; }
             double o = a1 * s;
+            if (K2 > 0) o = fma(a2, s2, o);
             if (v) o = fma(b, (double)v[i], o);
             out[i] = (float)o;
         }
@@ -255,10 +265,11 @@ __global__ void __launch_bounds__(kCW * 32) lp_combine_kernel(float* out, int64_
 }
 
 bto_status lp_combine(float* out, int64_t len, const double* P, int64_t ld, int K, double a1,
-                      const float* v, double b, int sms, cudaStream_t st) {
+                      const float* v, double b, int sms, cudaStream_t st, const double* P2 = nullptr,
+                      int K2 = 0, double a2 = 0.0) {
     if (len <= 0) return BTO_OK;
     const int64_t blocks = std::min<int64_t>(ceil_div(len, 32), (int64_t)sms * 8);
-    lp_combine_kernel<<<(int)blocks, kCW * 32, 0, st>>>(out, len, P, ld, K, a1, v, b);
+    lp_combine_kernel<<<(int)blocks, kCW * 32, 0, st>>>(out, len, P, ld, K, a1, v, b, P2, K2, a2);
     return launch_status();
 }
 
@@ -294,12 +305,14 @@ bto_status lp_launch(int a_type, int mode, const LpArgs& a, const PanelPlan& pl,
             case LP_QS: return lp_launch_t<float, LP_QS>(a, pl, vec, st);
             case LP_Q: return lp_launch_t<float, LP_Q>(a, pl, vec, st);
             case LP_G1: return lp_launch_t<float, LP_G1>(a, pl, vec, st);
+            case LP_S: return lp_launch_t<float, LP_S>(a, pl, vec, st);
         }
     } else {
         switch (mode) {
             case LP_QS: return lp_launch_t<__nv_bfloat16, LP_QS>(a, pl, vec, st);
             case LP_Q: return lp_launch_t<__nv_bfloat16, LP_Q>(a, pl, vec, st);
             case LP_G1: return lp_launch_t<__nv_bfloat16, LP_G1>(a, pl, vec, st);
+            case LP_S: return lp_launch_t<__nv_bfloat16, LP_S>(a, pl, vec, st);
         }
     }
     return BTO_ERR_INVALID_VALUE;
@@ -403,4 +416,92 @@ extern "C" bto_status bto_gemver_ex(int64_t m, int64_t n, float alpha, float bet
     b.ntiles = pl.ntiles; b.reverse = 1; b.tcmax = pl.TCmax; b.cu = a.cu; b.status = a.status;
     if ((e = lp_launch(a_type, LP_Q, b, pl, st)) != BTO_OK) return e;               // B x
     return lp_combine(w, m, b.qpart, pl.ldq, pl.NC, (double)alpha, nullptr, 0.0, d.sms, st);
+}
+
+// ATAX / BATAX (Table I; Section II, Fig. 1) in the reduced-precision storage
+// form: t = A x by the q-only sweep and its combine (t in FP32 in the
+// workspace), then y = beta A^T t by the s-only sweep, tiles in reverse order
+// so that the first tiles of the second sweep find the last ones of the
+// first in L2.  A is read twice; the FP64 form's single-read group-band
+// kernel trades that read for an exchange between blocks, which pays off
+// only where arithmetic, not bandwidth, is the bound.
+extern "C" bto_status bto_atax_ex(int64_t m, int64_t n, float beta, int a_type, const void* A, int64_t lda,
+                                  const float* x, float* y, void* ws, size_t ws_bytes, bto_stream_t stream) {
+    clear_invalid_arg();
+    Check c;
+    c.size(1, m); c.size(2, n);
+    if (a_type != BTO_F32 && a_type != BTO_BF16) c.fail(4);
+    if (!c.ok()) return c.finish();
+    const size_t es = a_type == BTO_F32 ? 4 : 2;
+    const size_t Ab = mat_extent_bytes(m, n, lda, es);
+    c.ptr(5, A, m > 0 && n > 0, es); c.ld(6, lda, m);
+    c.ptr(7, x, n > 0, 4); c.ptr(8, y, n > 0, 4);
+    c.disjoint(8, y, fbytes(n), A, Ab); c.disjoint(8, y, fbytes(n), x, fbytes(n));
+    DeviceInfo d; WsLayout L;
+    if (c.ok()) {
+        if (!device_info(&d)) return BTO_ERR_CUDA;
+        if (ws_layout(BTO_OP_ATAX, BTO_FORM_FUSED, m, n, a_type, d, &L) != BTO_OK) return BTO_ERR_CUDA;
+        c.ws(9, ws, ws_bytes, L);
+    }
+    if (!c.ok()) return c.finish();
+    cudaStream_t st = (cudaStream_t)stream;
+    const PanelPlan pl = lp_plan(m, n, d.sms, a_type);
+    char* w = static_cast<char*>(ws);
+    if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
+    if (n == 0) return BTO_OK;
+    float* t = reinterpret_cast<float*>(w + L.off[0]);
+    LpArgs a{};
+    a.m = m; a.n = n; a.A = A; a.lda = lda; a.p = x;
+    a.tcmax = pl.TCmax; a.cu = lp_col_unit(a_type); a.status = reinterpret_cast<int*>(w);
+    a.qpart = reinterpret_cast<double*>(w + L.off[1]); a.spart = reinterpret_cast<double*>(w + L.off[2]);
+    a.ldq = pl.ldq; a.lds = pl.lds; a.NR = pl.NR; a.NC = pl.NC; a.ntiles = pl.ntiles;
+    bto_status e = lp_launch(a_type, LP_Q, a, pl, st);                               // A x
+    if (e != BTO_OK) return e;
+    if ((e = lp_combine(t, m, a.qpart, pl.ldq, pl.NC, 1.0, nullptr, 0.0, d.sms, st)) != BTO_OK) return e;
+    a.p = nullptr; a.r = t; a.reverse = 1;
+    if ((e = lp_launch(a_type, LP_S, a, pl, st)) != BTO_OK) return e;                // A^T t
+    return lp_combine(y, n, a.spart, pl.lds, pl.NR, (double)beta, nullptr, 0.0, d.sms, st);
+}
+
+// GESUMMV (Table I) in the reduced-precision storage form: a q-only sweep
+// over each matrix, then one combine forms alpha (A x) + beta (B x) in FP64
+// from both sets of partials and rounds once.
+extern "C" bto_status bto_gesummv_ex(int64_t m, int64_t n, float alpha, float beta, int a_type, const void* A,
+                                     int64_t lda, const void* B, int64_t ldb, const float* x, float* y,
+                                     void* ws, size_t ws_bytes, bto_stream_t stream) {
+    clear_invalid_arg();
+    Check c;
+    c.size(1, m); c.size(2, n);
+    if (a_type != BTO_F32 && a_type != BTO_BF16) c.fail(5);
+    if (!c.ok()) return c.finish();
+    const size_t es = a_type == BTO_F32 ? 4 : 2;
+    const size_t Ab = mat_extent_bytes(m, n, lda, es), Bb = mat_extent_bytes(m, n, ldb, es);
+    c.ptr(6, A, m > 0 && n > 0, es); c.ld(7, lda, m);
+    c.ptr(8, B, m > 0 && n > 0, es); c.ld(9, ldb, m);
+    c.ptr(10, x, n > 0, 4); c.ptr(11, y, m > 0, 4);
+    c.disjoint(11, y, fbytes(m), A, Ab); c.disjoint(11, y, fbytes(m), B, Bb);
+    c.disjoint(11, y, fbytes(m), x, fbytes(n));
+    DeviceInfo d; WsLayout L;
+    if (c.ok()) {
+        if (!device_info(&d)) return BTO_ERR_CUDA;
+        if (ws_layout(BTO_OP_GESUMMV, BTO_FORM_FUSED, m, n, a_type, d, &L) != BTO_OK) return BTO_ERR_CUDA;
+        c.ws(12, ws, ws_bytes, L);
+    }
+    if (!c.ok()) return c.finish();
+    cudaStream_t st = (cudaStream_t)stream;
+    const PanelPlan pl = lp_plan(m, n, d.sms, a_type);
+    char* w = static_cast<char*>(ws);
+    if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
+    LpArgs a{};
+    a.m = m; a.n = n; a.A = A; a.lda = lda; a.p = x;
+    a.tcmax = pl.TCmax; a.cu = lp_col_unit(a_type); a.status = reinterpret_cast<int*>(w);
+    a.qpart = reinterpret_cast<double*>(w + L.off[0]);
+    a.ldq = pl.ldq; a.lds = pl.lds; a.NR = pl.NR; a.NC = pl.NC; a.ntiles = pl.ntiles;
+    bto_status e = lp_launch(a_type, LP_Q, a, pl, st);                               // A x
+    if (e != BTO_OK) return e;
+    LpArgs b = a;
+    b.A = B; b.lda = ldb; b.qpart = reinterpret_cast<double*>(w + L.off[1]); b.reverse = 1;
+    if ((e = lp_launch(a_type, LP_Q, b, pl, st)) != BTO_OK) return e;                // B x
+    return lp_combine(y, m, a.qpart, pl.ldq, pl.NC, (double)alpha, nullptr, 0.0, d.sms, st, b.qpart, pl.NC,
+                      (double)beta);
 }

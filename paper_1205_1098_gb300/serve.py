@@ -1,28 +1,25 @@
-"""Serving loop: continuous batching of GEMVER/BiCGK/ATAX/GESUMMV requests.
+"""Serving: continuous batching of GEMVER/BiCGK/ATAX/GESUMMV requests.
 
 Requests arrive as a seeded Poisson process.  Each names a kernel, a size n
 and a storage type (FP32 or BF16) for its matrix; operands are resident on
 the device (the leading n x n block of an 8192 x 8192 matrix of that type, and
 prefixes of resident vectors), so no request moves its inputs over the host
-link.  The loop:
+link.  The scheduling loop is libbto's native bto_serve_run: arrivals join a
+FIFO; whenever one of `streams` launch slots is free, the head of the FIFO
+is launched, either alone through its single-instance reduced-precision
+entry point (n >= `direct_n`: one large matrix spread over every SM) or as a
+batch of up to `max_batch` requests through the batched form (continuous
+batching: requests that arrive while earlier launches run join the next
+one, and launches on different slots overlap); outputs, GEMVER's B and the
+workspaces come from a device arena of `budget_bytes` (the HBM budget),
+and admission waits while they do not fit.  Python's part is the resident
+operands, the arena, the trace and the statistics.
 
-  * moves arrived requests into a FIFO;
-  * admits requests from the head of the FIFO while their outputs (including
-    GEMVER's B) plus the batch workspace fit the HBM budget, up to `max_batch`
-    per batch, whenever one of `streams` launch slots is free: requests that
-    arrive while earlier batches are on the GPU join the next batch
-    (continuous batching), and batches on different streams overlap;
-  * launches each batch with bto_batch_prepare / bto_batch_run on its stream
-    and records an event;
-  * polls the events, stamps each finished request's completion time, and
-    releases its memory from the budget.
-
-Latency is completion minus arrival (host clock).  Throughput counts each
-finished request's compulsory bytes.  All device work runs in libbto's
-kernels; this module only schedules.
+Latency is completion minus arrival (the loop's clock).  Throughput counts
+each finished request's compulsory bytes.
 """
-import collections
-import time
+import ctypes
+import gc
 
 import numpy as np
 import torch
@@ -61,12 +58,12 @@ def compulsory_bytes(op, n, dtype):
 
 
 class Server:
-    def __init__(self, budget_bytes=40e9, streams=4, max_batch=64, tile_cols=256, seed=4, device=None):
-        import synth
+    def __init__(self, budget_bytes=40e9, streams=4, max_batch=64, tile_cols=256, seed=4, device=None,
+                 direct_n=1024, staging_bytes=4 << 20):
         self.budget = float(budget_bytes)
-        self.used = 0.0
         self.max_batch = max_batch
         self.tile_cols = tile_cols
+        self.direct_n = direct_n
         self.streams = [torch.cuda.Stream(device=device) for _ in range(streams)]
         f32 = dict(dtype=torch.float32, device="cuda")
         # Resident operands: two matrices per storage type and the vector pool.
@@ -84,124 +81,78 @@ class Server:
             v = torch.empty(NMAX, **f32)
             L.bto_fill_f32(seed, 100 + aid, 0, NMAX, 1, 0, v, NMAX, None)
             self.vecs.append(v)
+        # The budget is one device arena; plans and status words go through pinned staging.
+        self.arena = torch.empty(int(budget_bytes), dtype=torch.uint8, device="cuda")
+        self.staging = torch.empty(int(staging_bytes), dtype=torch.uint8, pin_memory=True)
+        self._handles = (ctypes.c_void_p * streams)(*[s.cuda_stream for s in self.streams])
         torch.cuda.synchronize()
 
-    # ------------------------------------------------------------ requests
-    def _outputs(self, r):
-        n, op = r["n"], r["op"]
-        f32 = dict(dtype=torch.float32, device="cuda")
-        outs = {"bicgk": [n, n], "gemver": [n, n], "atax": [n], "gesummv": [n]}[op]
-        r["out"] = [torch.empty(ln, **f32) for ln in outs]
-        mem = 4.0 * sum(outs)
-        if op == "gemver":
-            dt = torch.float32 if r["dtype"] == "f32" else torch.int16
-            r["B"] = torch.empty(n * n, dtype=dt, device="cuda")
-            mem += r["B"].numel() * r["B"].element_size()
-        return mem
+    def _cfg(self, keep_results, max_wall):
+        c = L.ServeCfg()
+        for ti, t in enumerate(("f32", "bf16")):
+            for k in range(2):
+                c.A[ti][k] = self.mats[t][k].data_ptr()
+        for k in range(6):
+            c.vec[k] = self.vecs[k].data_ptr()
+        c.arena, c.arena_bytes = self.arena.data_ptr(), self.arena.numel()
+        c.staging, c.staging_bytes = self.staging.data_ptr(), self.staging.numel()
+        c.streams, c.nstreams = ctypes.addressof(self._handles), len(self.streams)
+        c.nmax, c.direct_n = NMAX, int(self.direct_n or 0)
+        c.max_wall = float(max_wall or 0.0)
+        c.alpha, c.beta = ALPHA, BETA
+        c.max_batch, c.tile_cols, c.keep_results = self.max_batch, self.tile_cols, int(bool(keep_results))
+        return c
 
-    def _fill_desc(self, d, r):
-        n, op, t = r["n"], r["op"], r["dtype"]
-        d.op, d.a_type = OPCODE[op], 1 if t == "f32" else 2
-        d.m = d.n = n
-        d.lda = d.ldb = NMAX
-        d.alpha, d.beta = ALPHA, BETA
-        d.A = self.mats[t][0].data_ptr()
-        if op == "gesummv":
-            d.B = self.mats[t][1].data_ptr()
-        elif op == "gemver":
-            d.ldb = n
-            d.B = r["B"].data_ptr()
-        nin = {"bicgk": 2, "gemver": 6, "atax": 1, "gesummv": 1}[op]
-        for k in range(nin):
-            d.in_[k] = self.vecs[k].data_ptr()
-        for k, o in enumerate(r["out"]):
-            d.out[k] = o.data_ptr()
+    def _view(self, off, count, dtype):
+        nb = count * torch.empty((), dtype=dtype).element_size()
+        return self.arena[off:off + nb].view(dtype).clone()
 
-    def _launch(self, batch, stream):
-        descs = (L.BatchDesc * len(batch))()
-        for d, r in zip(descs, batch):
-            self._fill_desc(d, r)
-        nb = L.bto_batch_workspace_bytes(descs, self.tile_cols)
-        ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
-        with torch.cuda.stream(stream):
-            L.bto_batch_prepare(len(batch), descs, self.tile_cols, ws, nb, stream)
-            L.bto_batch_run(ws, nb, stream)
-            ev = torch.cuda.Event()
-            ev.record(stream)
-        return ws, nb, ev
-
-    # ------------------------------------------------------------ the loop
     def run(self, trace, keep_results=False, max_wall=None):
-        """Serves `trace`; returns stats and, if asked, every request's outputs."""
+        """Serves `trace` (requests sorted by arrival time); returns stats and the
+        finished requests (with copies of their outputs if `keep_results`).
+
+        Python's cyclic garbage collector is paused for the call: a collection
+        over many request records would otherwise delay the next one.
+        """
+        n_req = len(trace)
+        reqs = (L.ServeReq * max(n_req, 1))()
+        for i, r in enumerate(trace):
+            reqs[i].t, reqs[i].op, reqs[i].n = r["t"], OPCODE[r["op"]], r["n"]
+            reqs[i].a_type = L.BTO_F32 if r["dtype"] == "f32" else L.BTO_BF16
+        res = (L.ServeRes * max(n_req, 1))()
+        stats = L.ServeStats()
+        cfg = self._cfg(keep_results, max_wall)
         torch.cuda.synchronize()
-        pending = collections.deque()
-        waiting = collections.deque(trace)
-        inflight = []            # (requests, ws, ws_bytes, event, stream index)
-        free = list(range(len(self.streams)))
-        done, nbytes, batches, peak = [], 0, 0, 0.0
-        t0 = time.perf_counter()
-        deadline = None if max_wall is None else t0 + max_wall
-        while waiting or pending or inflight:
-            now = time.perf_counter() - t0
-            while waiting and waiting[0]["t"] <= now:
-                pending.append(waiting.popleft())
-            # Completions.
-            still = []
-            for (reqs, ws, wsb, ev, si) in inflight:
-                if ev.query():
-                    tc = time.perf_counter() - t0
-                    for r in reqs:
-                        r["done"] = tc
-                        nbytes += compulsory_bytes(r["op"], r["n"], r["dtype"])
-                        self.used -= r["mem"]
-                        if not keep_results:
-                            r.pop("out", None)
-                            r.pop("B", None)
-                        done.append(r)
-                    self.used -= wsb
-                    r0 = reqs[0]
-                    r0.setdefault("_status", L.bto_device_status(ws, self.streams[si]))
-                    free.append(si)
-                else:
-                    still.append((reqs, ws, wsb, ev, si))
-            inflight = still
-            # Admission into a new batch on a free stream.
-            if free and pending:
-                batch = []
-                while pending and len(batch) < self.max_batch:
-                    r = pending[0]
-                    need = 4.0 * 6 * r["n"] + (r["n"] * r["n"] * (2 if r["dtype"] == "bf16" else 4)
-                                              if r["op"] == "gemver" else 0) + 64e6
-                    if self.used + need > self.budget and (batch or inflight):
-                        break            # wait for memory to free up
-                    # (a request larger than the whole budget runs alone when nothing else is admitted)
-                    pending.popleft()
-                    r["mem"] = self._outputs(r)
-                    self.used += r["mem"]
-                    peak = max(peak, self.used)
-                    r["admit"] = time.perf_counter() - t0
-                    batch.append(r)
-                if batch:
-                    si = free.pop()
-                    ws, wsb, ev = self._launch(batch, self.streams[si])
-                    self.used += wsb
-                    peak = max(peak, self.used)
-                    inflight.append((batch, ws, wsb, ev, si))
-                    batches += 1
-            elif not inflight and not pending and waiting:
-                # Idle until the next arrival.
-                wait = waiting[0]["t"] - (time.perf_counter() - t0)
-                if wait > 0:
-                    time.sleep(min(wait, 1e-4))
-            if deadline is not None and time.perf_counter() > deadline:
-                break
-        wall = time.perf_counter() - t0
-        lat = np.array([r["done"] - r["t"] for r in done]) if done else np.zeros(1)
-        status = [r["_status"] for r in done if "_status" in r]
+        gc_was_on = gc.isenabled()
+        gc.collect()
+        gc.disable()
+        try:
+            status = L.bto_serve_run(cfg, n_req, reqs, res, stats)
+        finally:
+            if gc_was_on:
+                gc.enable()
+        done, nbytes, statuses = [], 0, []
+        for i, r in enumerate(trace):
+            x = res[i]
+            if x.done < 0 or x.status == L.BTO_ERR_BUDGET:
+                continue
+            d = dict(r, admit=x.admit, done=x.done, direct=bool(x.direct), _status=x.status)
+            statuses.append(x.status)
+            nbytes += compulsory_bytes(r["op"], r["n"], r["dtype"])
+            if keep_results:
+                n = r["n"]
+                d["out"] = [self._view(x.out[k], n, torch.float32) for k in range(2) if x.out[k] >= 0]
+                if r["op"] == "gemver":
+                    d["B"] = self._view(x.out[2], n * n, torch.float32 if r["dtype"] == "f32" else torch.int16)
+            done.append(d)
+        wall = stats.wall_s
+        lat = np.array([d["done"] - d["t"] for d in done]) if done else np.zeros(1)
         return {
-            "requests": len(done), "batches": batches, "wall_s": wall,
-            "offered_rate": len(trace) / max(trace[-1]["t"], 1e-9) if trace else 0.0,
+            "requests": len(done), "batches": int(stats.batches), "direct": int(stats.direct),
+            "rejected": int(stats.rejected), "wall_s": wall,
+            "offered_rate": n_req / max(trace[-1]["t"], 1e-9) if trace else 0.0,
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_ms": float(lat.mean() * 1e3), "gbs": nbytes / wall / 1e9,
-            "status_ok": all(s == 0 for s in status), "peak_bytes": peak, "budget_bytes": self.budget,
+            "mean_ms": float(lat.mean() * 1e3), "gbs": nbytes / max(wall, 1e-9) / 1e9,
+            "status_ok": status == L.BTO_OK and all(s == 0 for s in statuses),
+            "peak_bytes": float(stats.peak_bytes), "budget_bytes": self.budget,
         }, done

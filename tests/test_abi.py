@@ -116,3 +116,67 @@ def test_mrhs_validation_without_gpu(L):
     with pytest.raises(bto.BtoError) as e:   # Q overlaps S
         bto.bto_bicgk_mrhs(64, 64, 16, 4096, 64, 8192, 64, 12288, 64, 16384, 64, 16384 + 64, 64, 0, 0, 0)
     assert e.value.arg == 10
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structures have the C layout (gcc on the header)."""
+    structs = {
+        "bto_batch_desc": (_lib.BatchDesc, {"in": "in_"}),
+        "bto_serve_req": (_lib.ServeReq, {}),
+        "bto_serve_res": (_lib.ServeRes, {}),
+        "bto_serve_cfg": (_lib.ServeCfg, {}),
+        "bto_serve_stats": (_lib.ServeStats, {}),
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bto.h"', "int main(void) {"]
+    for cname, (cls, rename) in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        back = {v: k for k, v in rename.items()}
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, back.get(fname, fname)))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, (cls, _) in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_serve_validation_without_gpu(L):
+    cfg = _lib.ServeCfg()
+    stats = _lib.ServeStats()
+    reqs = (_lib.ServeReq * 2)()
+    res = (_lib.ServeRes * 2)()
+    streams = (ctypes.c_void_p * 1)(0)
+
+    def run():
+        try:
+            _lib.bto_serve_run(cfg, 2, reqs, res, stats)
+        except bto.BtoError as e:
+            return e.status, e.arg
+        return None
+
+    assert run() == (bto.BTO_ERR_INVALID_VALUE, 1)           # no streams, no arena
+    cfg.nstreams, cfg.streams = 1, ctypes.addressof(streams)
+    cfg.arena, cfg.arena_bytes = 1 << 20, 1 << 30
+    cfg.max_batch, cfg.tile_cols, cfg.nmax = 8, 256, 1024
+    cfg.A[0][0] = cfg.A[0][1] = 1 << 21
+    for k in range(6):
+        cfg.vec[k] = 1 << 22
+    cfg.tile_cols = 100
+    assert run() == (bto.BTO_ERR_INVALID_VALUE, 1)           # tile width not a multiple of 16
+    cfg.tile_cols = 256
+    reqs[0].t, reqs[0].op, reqs[0].a_type, reqs[0].n = 0.0, 0, bto.BTO_F32, 64
+    reqs[1].t, reqs[1].op, reqs[1].a_type, reqs[1].n = 0.0, 9, bto.BTO_F32, 64
+    assert run() == (bto.BTO_ERR_INVALID_VALUE, 3)           # unknown op
+    reqs[1].op, reqs[1].n = 2, 4096
+    assert run() == (bto.BTO_ERR_INVALID_VALUE, 3)           # n > nmax
+    reqs[1].n, reqs[1].a_type = 64, bto.BTO_BF16
+    assert run() == (bto.BTO_ERR_INVALID_VALUE, 3)           # no resident BF16 matrix
+    reqs[1].a_type, reqs[0].t = bto.BTO_F32, 1.0
+    assert run() == (bto.BTO_ERR_INVALID_VALUE, 3)           # arrivals out of order

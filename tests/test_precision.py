@@ -157,6 +157,75 @@ def test_gemver_ex_column_scaled(t):
         assert relerr(g, o) <= TOL_LP, (k, relerr(g, o))
 
 
+def run_atax_ex(t, m, n, lda, kind=synth.KIND_UNIFORM, seed=2, beta=1.25, scale=None):
+    A64 = synth.matrix(seed, 0, m, n, lda=lda, kind=kind, scale=scale)
+    Aq, Adq = quantize(A64, t)
+    xv = f32vec(seed, 1, n, kind)
+    dA, dx = dev_stored(Aq, t), dev(xv, torch.float32)
+    y = out32(n)
+    wk, nb = ws("atax", 0, m, n, TYPES[t])
+    bto.bto_atax_ex(m, n, beta, TYPES[t], p(dA), lda, p(dx), y.ptr(), p(wk), nb, None)
+    sync()
+    yo = O.atax(m, n, beta, Adq[:m] if m else np.zeros((1, n)), xv.astype(np.float64))
+    return y.host(), yo
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "%dx%d_ld%d" % s)
+@pytest.mark.parametrize("t", sorted(TYPES))
+def test_atax_ex(t, shape):
+    g, o = run_atax_ex(t, *shape)
+    assert relerr(g, o) <= TOL_LP, relerr(g, o)
+
+
+@pytest.mark.parametrize("t", sorted(TYPES))
+def test_atax_ex_integer_exact(t):
+    # n = 100 keeps every FP32 partial of the second sweep below 2^24.
+    g, o = run_atax_ex(t, 300, 100, 304, kind=synth.KIND_INTEGER, beta=-2.0)
+    assert np.array_equal(g.astype(np.float64), o)
+
+
+@pytest.mark.parametrize("t", sorted(TYPES))
+def test_atax_ex_column_scaled(t):
+    cs = synth.colscale(6, 1300)
+    g, o = run_atax_ex(t, 1700, 1300, 1700, seed=6, scale=cs)
+    assert relerr(g, o) <= TOL_LP, relerr(g, o)
+
+
+def run_gesummv_ex(t, m, n, lda, kind=synth.KIND_UNIFORM, seed=2, alpha=1.5, beta=-0.75, scale=None):
+    A64 = synth.matrix(seed, 0, m, n, lda=lda, kind=kind, scale=scale)
+    B64 = synth.matrix(seed, 1, m, n, lda=lda, kind=kind, scale=scale)
+    (Aq, Adq), (Bq, Bdq) = quantize(A64, t), quantize(B64, t)
+    xv = f32vec(seed, 2, n, kind)
+    dA, dB, dx = dev_stored(Aq, t), dev_stored(Bq, t), dev(xv, torch.float32)
+    y = out32(m)
+    wk, nb = ws("gesummv", 0, m, n, TYPES[t])
+    bto.bto_gesummv_ex(m, n, alpha, beta, TYPES[t], p(dA), lda, p(dB), lda, p(dx), y.ptr(), p(wk), nb, None)
+    sync()
+    z = np.zeros((1, n))
+    yo = O.gesummv(m, n, alpha, Adq[:m] if m else z, beta, Bdq[:m] if m else z, xv.astype(np.float64))
+    return y.host(), yo
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "%dx%d_ld%d" % s)
+@pytest.mark.parametrize("t", sorted(TYPES))
+def test_gesummv_ex(t, shape):
+    g, o = run_gesummv_ex(t, *shape)
+    assert relerr(g, o) <= TOL_LP, relerr(g, o)
+
+
+@pytest.mark.parametrize("t", sorted(TYPES))
+def test_gesummv_ex_integer_exact(t):
+    g, o = run_gesummv_ex(t, 300, 517, 304, kind=synth.KIND_INTEGER, alpha=2.0, beta=-3.0)
+    assert np.array_equal(g.astype(np.float64), o)
+
+
+@pytest.mark.parametrize("t", sorted(TYPES))
+def test_gesummv_ex_column_scaled(t):
+    cs = synth.colscale(7, 1100)
+    g, o = run_gesummv_ex(t, 900, 1100, 904, seed=7, scale=cs)
+    assert relerr(g, o) <= TOL_LP, relerr(g, o)
+
+
 # ------------------------------------------------------------ n = 32768 (sampled)
 NF = 32768
 

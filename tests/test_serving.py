@@ -83,7 +83,59 @@ def test_serving_budget_is_respected(server):
     trace = make_trace(seed=5, rate=20000.0, duration=0.0, nmin=512, nmax=2048, count=120)
     small = Server.__new__(Server)
     small.__dict__.update(server.__dict__)
-    small.budget, small.used = 0.25e9, 0.0
+    small.budget = 0.25e9
+    small.arena = server.arena[:int(small.budget)]
     stats, done = small.run(trace)
+    assert stats["requests"] == len(trace) and stats["status_ok"] and stats["rejected"] == 0
+    assert 0 < stats["peak_bytes"] <= small.budget
+
+
+def test_serving_rejects_what_cannot_fit(server):
+    """A request whose outputs exceed the whole budget ends with BTO_ERR_BUDGET;
+    the others are served."""
+    from paper_1205_1098_gb300.serve import Server
+    small = Server.__new__(Server)
+    small.__dict__.update(server.__dict__)
+    small.budget = 2 << 20
+    small.arena = server.arena[:small.budget]
+    trace = [dict(id=0, t=0.0, op="bicgk", n=256, dtype="f32"),
+             dict(id=1, t=0.0, op="gemver", n=1024, dtype="f32"),     # B alone is 4 MiB
+             dict(id=2, t=0.0, op="atax", n=300, dtype="bf16")]
+    stats, done = small.run(trace)
+    assert stats["rejected"] == 1 and stats["requests"] == 2 and stats["status_ok"]
+    assert sorted(d["id"] for d in done) == [0, 2]
+
+
+def test_serving_direct_path_alone_vs_mix_and_oracle(server):
+    """Requests with n >= direct_n run alone through the single-instance
+    entry points while smaller ones are batched around them."""
+    from paper_1205_1098_gb300.serve import make_trace
+    trace = make_trace(seed=9, rate=20000.0, duration=0.0, nmin=512, nmax=4096, count=48)
+    server.direct_n, saved = 2048, server.direct_n
+    try:
+        stats, done = server.run(copy.deepcopy(trace), keep_results=True)
+    finally:
+        server.direct_n = saved
     assert stats["requests"] == len(trace) and stats["status_ok"]
-    assert stats["peak_bytes"] <= small.budget
+    assert stats["direct"] > 0 and stats["batches"] > 0
+    byid = {r["id"]: r for r in done}
+    picked = {}
+    for r in trace:
+        if r["n"] >= 2048 and r["op"] not in picked:
+            picked[r["op"]] = r
+    assert len(picked) >= 3, picked.keys()
+    for r in picked.values():
+        got = byid[r["id"]]
+        for k, ro in enumerate(_oracle(got)):
+            g = got["out"][k].cpu().numpy().astype(np.float64)
+            assert relerr(g, ro) <= 1e-6, (r, k, relerr(g, ro))
+        server.direct_n = 2048
+        try:
+            _, alone = server.run([dict(r, t=0.0)], keep_results=True)
+        finally:
+            server.direct_n = saved
+        assert alone[0]["direct"]
+        for k in range(len(got["out"])):
+            assert torch.equal(alone[0]["out"][k], got["out"][k]), (r, k)
+        if r["op"] == "gemver":
+            assert torch.equal(alone[0]["B"], got["B"]), r

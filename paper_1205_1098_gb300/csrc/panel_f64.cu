@@ -175,7 +175,10 @@ __device__ __host__ __forceinline__ int64_t row_split_at(int64_t m, int64_t part
 // measured faster than four columns ahead at one block per SM (GEMVER's
 // first pass 2.20 -> 2.00 ms, BICGK 1.07 -> 0.98 ms, GESUMMV 1.13 -> 0.97 ms
 // at n = 16384): with FP64 the bound, a second resident block hides more
-// latency than loads issued early.
+// latency than loads issued early.  The q-only mode has its own loop (two
+// buffers of two columns taking turns); three or four blocks per SM were
+// slower for it.  The same loop for the s-only mode measured no faster than
+// its four-column bursts.
 template <int MODE>
 struct BlocksPerSM { static constexpr int value = 2; };
 template <int MODE>
@@ -211,6 +214,38 @@ __global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kern
 #pragma unroll
             for (int k = 0; k < kRPT; k++) { qacc[k] = 0.0; qacc2[k] = 0.0; }
 
+            if (MODE == PM_Q) {
+                // q alone: two buffers of two columns each take turns, the loads
+                // of one issued before the other's FMAs, so each warp keeps loads
+                // in flight while it computes (a burst of four columns followed by
+                // their FMAs left the loads' latency exposed).  Columns are added
+                // in the same order as before.
+                double xa[2][kRPT], xb[2][kRPT], pa[2] = {0.0, 0.0}, pb[2] = {0.0, 0.0};
+                auto fetch = [&](int64_t j, double (&x)[2][kRPT], double (&pv)[2]) {
+#pragma unroll
+                    for (int u = 0; u < 2; u++)
+                        if (j + u < c1) {
+                            load_col<VEC>(a.A + (j + u) * a.lda, R0, r1, warp, lane, x[u]);
+                            pv[u] = __ldg(a.p + j + u);
+                        }
+                };
+                auto use = [&](int64_t j, const double (&x)[2][kRPT], const double (&pv)[2]) {
+#pragma unroll
+                    for (int u = 0; u < 2; u++)
+                        if (j + u < c1) {
+#pragma unroll
+                            for (int k = 0; k < kRPT; k++) qacc[k] = fma(x[u][k], pv[u], qacc[k]);
+                        }
+                };
+                fetch(c0, xa, pa);
+#pragma unroll 1
+                for (int64_t j = c0; j < c1; j += 4) {
+                    fetch(j + 2, xb, pb);
+                    use(j, xa, pa);
+                    fetch(j + 4, xa, pa);
+                    use(j + 2, xb, pb);
+                }
+            } else
             for (int64_t g0 = c0; g0 < c1; g0 += kGroup) {
                 const int nc = (int)((c1 - g0) < kGroup ? (c1 - g0) : kGroup);
                 double sl[kGroup];

@@ -79,6 +79,18 @@ class Batch:
             self.host.append((Ad[:m] if m else np.zeros((1, n)), B2d[:m] if B2d is not None and m else None, ins, A64[:m]))
             self.outs.append((outs, Bout))
 
+    def submit(self, tile_cols=0, staging=None):
+        """One bto_batch_submit call (plan, copy and launch), through `staging`
+        (pinned host memory) when given."""
+        nb = bto.bto_batch_workspace_bytes(self.descs, tile_cols)
+        ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+        ws.fill_(0xA5)
+        self.ws = ws
+        sb = 0 if staging is None else staging.numel()
+        bto.bto_batch_submit(len(self.specs), self.descs, tile_cols, ws, nb, staging, sb, None)
+        torch.cuda.synchronize()
+        return bto.bto_device_status(ws)
+
     def run(self, tile_cols=0, graph=False, reps=1):
         nb = bto.bto_batch_workspace_bytes(self.descs, tile_cols)
         ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")

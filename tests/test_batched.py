@@ -91,3 +91,27 @@ def test_batch_logu_alone_vs_mix_and_graph():
     for i in range(len(specs)):
         for k, (g1, g2) in enumerate(zip(b.result(i), mixed[i])):
             assert np.array_equal(g1, g2, equal_nan=True), (specs[i], k)
+
+
+@pytest.mark.parametrize("pinned", [False, True], ids=["pageable", "pinned"])
+def test_batch_submit_equals_prepare_run(pinned):
+    """bto_batch_submit (counters zeroed in the uploaded plan, only non-empty
+    queues launched, grids sized to their items) gives the bits of
+    bto_batch_prepare + bto_batch_run, through pageable or pinned staging;
+    a tiny staging buffer falls back to the pageable copy."""
+    specs = [(op, m, n, m) for (op, m, n) in logu_sizes(5, 40, 32, 700, ops=("bicgk", "gemver", "atax", "gesummv"))]
+    specs += [("bicgk", 300, 200, 300, "bf16"), ("atax", 257, 129, 257, "bf16")]
+    b = Batch(specs, seed=11)
+    assert b.run(64) == 0
+    ref = [b.result(i) for i in range(len(specs))]
+    for staging in ([torch.empty(1 << 20, dtype=torch.uint8, pin_memory=True),
+                     torch.empty(64, dtype=torch.uint8, pin_memory=True)] if pinned else [None]):
+        for out, Bout in b.outs:
+            for to, _ in out:
+                to.fill_(float("nan"))
+            if Bout is not None:
+                Bout.fill_(0)
+        assert b.submit(64, staging) == 0
+        for i in range(len(specs)):
+            for k, (g1, g2) in enumerate(zip(b.result(i), ref[i])):
+                assert np.array_equal(g1, g2, equal_nan=True), (specs[i], k)

@@ -575,9 +575,10 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3):
         m, n = int(sizes[2 * i]), int(sizes[2 * i + 1])
         op = int(ops[i])
         d = descs[i]
-        d.op, d.a_type, d.m, d.n, d.lda, d.ldb, d.alpha, d.beta = op, 1, m, n, m, m, 1.5, 1.25
-        A = torch.empty(m * n, **f32)
-        bto.bto_fill_f32(seed, 1000 * i, 0, m, n, 0, A, m, None)
+        lda = (m + 3) // 4 * 4      # columns start on 16 bytes (padded leading dimension)
+        d.op, d.a_type, d.m, d.n, d.lda, d.ldb, d.alpha, d.beta = op, 1, m, n, lda, lda, 1.5, 1.25
+        A = torch.empty(lda * n, **f32)
+        bto.bto_fill_f32(seed, 1000 * i, 0, m, n, 0, A, lda, None)
         keep.append(A)
         d.A = A.data_ptr()
         lens = [n, m] if op == 0 else [m, n, m, n, m, n]
@@ -591,7 +592,7 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3):
             keep.append(t)
             d.out[k] = t.data_ptr()
         if op == 2:
-            B = torch.empty(m * n, **f32)
+            B = torch.empty(lda * n, **f32)
             keep.append(B)
             d.B = B.data_ptr()
             nbytes += 3 * 4 * m * n + 4 * (4 * m + 4 * n)
@@ -626,7 +627,8 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3):
     return {"instances": count, "ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
             "hbm_frac": round(nbytes / ms / 1e6 / hbm, 3), "compulsory_bytes": nbytes,
             "tile_cols": best, "tuner_ms": {str(k): round(v, 4) for k, v in cand_ms.items()},
-            "status": status, "launch": "CUDA graph of bto_batch_run (reset + persistent kernel)"}
+            "status": status, "launch": "CUDA graph of bto_batch_run (TMA-path sweeps and combines; fallback kernel idle)",
+            "layout": "column-major, leading dimension rounded up to a multiple of 4 floats"}
 
 
 def serving_form(torch, duration=5.0, rate=20000.0, seed=4):

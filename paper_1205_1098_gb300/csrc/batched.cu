@@ -645,6 +645,11 @@ struct Plan {
     std::vector<bto_batch_desc> descs;
     std::vector<InstInfo> info;
     std::vector<Item> items;
+    BtPlan* bt;                 // instances on the TMA path
+    Plan() : bt(bt_plan_create()) {}
+    ~Plan() { bt_plan_destroy(bt); }
+    Plan(const Plan&) = delete;
+    Plan& operator=(const Plan&) = delete;
 };
 
 int64_t esize(int a_type) { return a_type == BTO_BF16 ? 2 : 4; }
@@ -677,6 +682,7 @@ bool make_plan(int count, const bto_batch_desc* descs, int tile_cols, Plan* P, i
     P->descs.assign(descs, descs + count);
     P->info.resize(count);
     P->items.clear();
+    bt_plan_reset(P->bt, tile_cols);
     std::vector<std::pair<double, Item>> first, second;
     int64_t qsize = 0, tsize = 0;
     for (int i = 0; i < count; i++) {
@@ -689,6 +695,9 @@ bool make_plan(int count, const bto_batch_desc* descs, int tile_cols, Plan* P, i
                   ((op != BTO_OP_GEMVER && op != BTO_OP_GESUMMV) || (aligned16(d.B) && d.ldb % V == 0));
         inf.qoff = -1;
         inf.toff = -1;
+        inf.stage1 = 0;
+        // Instances whose matrices suit the TMA go through the sweep path.
+        if (bt_plan_add(P->bt, d)) continue;
         const int64_t panels = n > 0 ? ceil_div(n, tile_cols) : 0;
         const int64_t rblocks = m > 0 ? ceil_div(m, kRows) : 0;
         auto push = [&](std::vector<std::pair<double, Item>>& v, int kind, int64_t lo, int64_t hi, double cost) {
@@ -749,10 +758,12 @@ bool make_plan(int count, const bto_batch_desc* descs, int tile_cols, Plan* P, i
     H.off_desc = region((size_t)count * sizeof(bto_batch_desc));
     H.off_info = region((size_t)count * sizeof(InstInfo));
     H.off_items = region(P->items.size() * sizeof(Item));
+    if (!bt_plan_empty(P->bt)) cur = (size_t)bt_plan_layout_records(P->bt, (int64_t)cur);
     H.counters_bytes = (int64_t)(count + kQueues) * sizeof(unsigned);
     H.off_counters = region((size_t)H.counters_bytes);
     H.off_qpart = region((size_t)std::max<int64_t>(qsize, 1) * sizeof(float2));
     H.off_t = region((size_t)std::max<int64_t>(tsize, 1) * sizeof(float));
+    if (!bt_plan_empty(P->bt)) cur = (size_t)bt_plan_layout_partials(P->bt, (int64_t)cur);
     H.total = cur;
     return true;
 }
@@ -784,8 +795,9 @@ size_t image_bytes(const Plan& P, bool counters) {
     return (size_t)P.h.off_counters + (counters ? (size_t)P.h.counters_bytes : 0);
 }
 
-void write_image(const Plan& P, char* img, bool counters) {
+void write_image(const Plan& P, char* img, bool counters, char* ws) {
     std::memset(img, 0, image_bytes(P, counters));
+    bt_plan_write(P.bt, img, ws);
     std::memcpy(img + kHeaderOff, &P.h, sizeof(Header));
     const size_t count = P.descs.size();
     if (count) std::memcpy(img + P.h.off_desc, P.descs.data(), count * sizeof(bto_batch_desc));
@@ -804,11 +816,11 @@ bto_status submit_plan(const Plan& P, void* ws, size_t ws_bytes, void* staging, 
     if (staging && staging_bytes >= nb) {
         // Pinned staging that the caller keeps until the stream has passed
         // this copy: no host wait.
-        write_image(P, static_cast<char*>(staging), true);
+        write_image(P, static_cast<char*>(staging), true, static_cast<char*>(ws));
         if (cudaMemcpyAsync(ws, staging, nb, cudaMemcpyHostToDevice, st) != cudaSuccess) return BTO_ERR_CUDA;
     } else {
         std::vector<char> img(nb);
-        write_image(P, img.data(), true);
+        write_image(P, img.data(), true, static_cast<char*>(ws));
         if (cudaMemcpyAsync(ws, img.data(), nb, cudaMemcpyHostToDevice, st) != cudaSuccess) return BTO_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return BTO_ERR_CUDA;
     }
@@ -827,7 +839,9 @@ bto_status submit_plan(const Plan& P, void* ws, size_t ws_bytes, void* staging, 
             default: batch_kernel<__nv_bfloat16, 1><<<grid, kThreads, kSmemBytes, st>>>(w); break;
         }
     }
-    return launch_status();
+    const bto_status e = launch_status();
+    if (e != BTO_OK || bt_plan_empty(P.bt)) return e;
+    return bt_launch(w, P.bt, st);
 }
 
 }  // namespace
@@ -888,7 +902,7 @@ extern "C" bto_status bto_batch_prepare(int count, const bto_batch_desc* descs, 
     // Stage the plan in one host image and copy it with one transfer; the
     // counters are reset by bto_batch_run's first kernel.
     std::vector<char> img(image_bytes(P, false));
-    write_image(P, img.data(), false);
+    write_image(P, img.data(), false, static_cast<char*>(ws));
     if (cudaMemcpyAsync(ws, img.data(), img.size(), cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess)
         return BTO_ERR_CUDA;
     // The host image is released on return: wait for the copy to leave it.
@@ -914,7 +928,10 @@ extern "C" bto_status bto_batch_run(void* ws, size_t ws_bytes, bto_stream_t stre
     batch_kernel<float, 1><<<grid, kThreads, kSmemBytes, st>>>(w);
     batch_kernel<__nv_bfloat16, 0><<<grid, kThreads, kSmemBytes, st>>>(w);
     batch_kernel<__nv_bfloat16, 1><<<grid, kThreads, kSmemBytes, st>>>(w);
-    return launch_status();
+    const bto_status e = launch_status();
+    if (e != BTO_OK) return e;
+    // The TMA path's kernels read their counts from the workspace (none: they return at once).
+    return bt_launch(w, nullptr, st);
 }
 
 extern "C" bto_status bto_batch_submit(int count, const bto_batch_desc* descs, int tile_cols, void* ws,

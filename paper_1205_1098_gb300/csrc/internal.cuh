@@ -101,6 +101,20 @@ __host__ __device__ inline int64_t lp_row_at(int64_t m, int64_t NR, int64_t rb) 
 inline int64_t lp_col_unit(int a_type) { return a_type == BTO_BF16 ? 32 : 16; }
 PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type);
 
+// TMA path of the batched form (batched_tma.cu): instances whose matrices
+// suit the tensor memory accelerator, as tiles through the reduced-precision
+// sweep.  bt_plan_add returns false for an instance the path cannot take.
+struct BtPlan;
+BtPlan* bt_plan_create();
+void bt_plan_destroy(BtPlan* p);
+void bt_plan_reset(BtPlan* p, int tile_cols);
+bool bt_plan_empty(const BtPlan* p);
+bool bt_plan_add(BtPlan* p, const bto_batch_desc& d);
+int64_t bt_plan_layout_records(BtPlan* p, int64_t cur);
+int64_t bt_plan_layout_partials(BtPlan* p, int64_t cur);
+void bt_plan_write(const BtPlan* p, char* img, char* ws);
+bto_status bt_launch(char* ws, const BtPlan* p, cudaStream_t st);
+
 // Batched form, planned once and submitted (the serving runtime's path).
 struct BatchPlan;
 BatchPlan* batch_plan_create();

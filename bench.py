@@ -558,7 +558,7 @@ def mrhs_form(torch, bto, hbm, steps, n=8192, k=64, seed=6):
                             "s": float(np.linalg.norm(Sh - sref) / np.linalg.norm(sref))}}
 
 
-def batched_form(torch, bto, hbm, steps, count=4096, seed=3):
+def batched_form(torch, bto, hbm, steps, count=4096, seed=3, tile=0):
     """Config 4: `count` BICGK/GEMVER instances (50/50 by a draw), m, n
     log-uniform in [32, 2048], FP32, one persistent launch, replayed from a
     CUDA graph; the panel width is chosen by the measured-cost tuner."""
@@ -599,7 +599,10 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3):
         else:
             nbytes += 4 * m * n + 4 * (2 * m + 2 * n)
     torch.cuda.synchronize()
-    best, cand_ms = autotune.tune(descs, use_cache=False)
+    if tile:
+        best, cand_ms = tile, {}           # profiling runs: a fixed panel width, no tuner
+    else:
+        best, cand_ms = autotune.tune(descs, use_cache=False)
     nb = bto.bto_batch_workspace_bytes(descs, best)
     ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
     bto.bto_batch_prepare(count, descs, best, ws, nb, None)
@@ -660,6 +663,7 @@ def main():
     ap.add_argument("--serving-only", type=float, default=0.0, help="profiling runs: only serving, for this many s")
     ap.add_argument("--batched-only", action="store_true", help="profiling runs: only the batched form")
     ap.add_argument("--batched-count", type=int, default=4096, help="instances in the batched form")
+    ap.add_argument("--batched-tile", type=int, default=0, help="profiling runs: fixed panel width (no tuner)")
     ap.add_argument("--mrhs-only", type=int, default=0, help="profiling runs: only multi-RHS BICGK with this k")
     ap.add_argument("--no-mrhs", action="store_true")
     ap.add_argument("--precision-only", type=int, default=0,
@@ -685,7 +689,8 @@ def main():
         build.build()
         import paper_1205_1098_gb300 as bto
         hbm, _, _ = load_peaks()
-        print(json.dumps({"batched_form": batched_form(torch, bto, hbm, args.steps, count=args.batched_count)}))
+        print(json.dumps({"batched_form": batched_form(torch, bto, hbm, args.steps, count=args.batched_count,
+                                                       tile=args.batched_tile)}))
         return
     if args.mrhs_only:
         import torch

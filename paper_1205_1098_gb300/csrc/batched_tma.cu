@@ -56,7 +56,7 @@ constexpr size_t stage_bytes() { return (size_t)kBoxR * Cfg<TA>::BoxC * sizeof(T
 template <typename TA>
 constexpr size_t bt_smem() {
     return 1024 + kStagesT * stage_bytes<TA>() + 2 * kStagesT * sizeof(uint64_t) +
-           2 * kCW * kBoxR * sizeof(float) + 5 * kMaxTw * sizeof(float);
+           2 * kCW * kBoxR * sizeof(float) + 8 * kMaxTw * sizeof(float);
 }
 
 }  // namespace
@@ -91,13 +91,17 @@ struct BtComb {
     double a1, a2, b;
 };
 
+struct BtChunk { int32_t job, start; };   // 256 consecutive outputs of one combine job
+
 struct BtHeader {
     int32_t ninst, pad;
     int32_t nitems[2][2];      // [stage][FP32, BF16]
     int32_t ncomb[2];
+    int32_t nchunk[2];
     int64_t off_inst;
     int64_t off_items[2][2];
     int64_t off_comb[2];
+    int64_t off_chunk[2];
 };
 
 namespace {
@@ -138,8 +142,24 @@ struct Smem {
     uint64_t* empty;
     float* qred;               // [2][8][256]
     float* shi; float* slo;    // [kMaxTw]
-    float* sp; float* sv1; float* sv2;
+    float* sp; float* sv1; float* sv2;   // the current item's column vectors (one of two buffers)
 };
+
+__device__ __forceinline__ void cp4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// Issues (cp.async, 4 bytes each) the copies of an item's column vectors into
+// the buffer at vb ([3][kMaxTw]: p, v1, v2) and commits them as one group.
+__device__ __forceinline__ void fetch_vectors(const BtItem& it, const BtInst& in, float* vb) {
+    const int ncols = it.c1 - it.c0;
+    const bool q = it.mode == LP_QS || it.mode == LP_Q, g1 = it.mode == LP_G1;
+    for (int k = threadIdx.x; k < ncols; k += kConsumers) {
+        if (q) cp4(vb + k, it.p + it.c0 + k);
+        if (g1) { cp4(vb + kMaxTw + k, in.v1 + it.c0 + k); cp4(vb + 2 * kMaxTw + k, in.v2 + it.c0 + k); }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
 
 // One item on the consumer warps: the tile's stages in ring order, the
 // arithmetic of the reduced-precision sweep, and the tile's partials.
@@ -156,11 +176,9 @@ __device__ __forceinline__ void consume(const BtItem& it, const BtInst& in, cons
     const int64_t c0 = it.c0, c1 = it.c1, r0 = it.r0, r1 = it.r1;
     const int ncols = (int)(c1 - c0);
     TA* ring = reinterpret_cast<TA*>(sm.ring);
-    for (int k = threadIdx.x; k < ncols; k += kConsumers) {
-        sm.shi[k] = 0.0f; sm.slo[k] = 0.0f;
-        if (HAS_Q) sm.sp[k] = __ldg(it.p + c0 + k);
-        if (MODE == LP_G1) { sm.sv1[k] = __ldg(in.v1 + c0 + k); sm.sv2[k] = __ldg(in.v2 + c0 + k); }
-    }
+    // The column vectors were copied during the previous item (fetch_vectors);
+    // the barrier makes every thread's copies visible.
+    for (int k = threadIdx.x; k < ncols; k += kConsumers) { sm.shi[k] = 0.0f; sm.slo[k] = 0.0f; }
     named_bar(1, kConsumers);
     TA* Bout = static_cast<TA*>(in.Bout);
     for (int64_t R0 = r0; R0 < r1; R0 += kBoxR) {
@@ -322,9 +340,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) bt_sweep(char* ws, int stage) {
     sm.qred = reinterpret_cast<float*>(sm.empty + S);
     sm.shi = sm.qred + 2 * kCW * kBoxR;
     sm.slo = sm.shi + kMaxTw;
-    sm.sp = sm.slo + kMaxTw;
-    sm.sv1 = sm.sp + kMaxTw;
-    sm.sv2 = sm.sv1 + kMaxTw;
+    float* vbuf = sm.slo + kMaxTw;      // [2][3][kMaxTw]
     __shared__ int s_abort_;
     volatile int* abortp = &s_abort_;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -372,11 +388,30 @@ __global__ void __launch_bounds__(kThreadsT, 1) bt_sweep(char* ws, int stage) {
     }
 
     // ---------------- consumers
+    // Column vectors go through two buffers: the next item's are copied
+    // (cp.async) while this item runs.
     int slot = 0;
     uint32_t ph = 0;
-    for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+    int buf = 0;
+    {
+        const BtItem first = items[blockIdx.x];
+        fetch_vectors(first, insts[first.inst], vbuf);
+    }
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x, buf ^= 1) {
         const BtItem it = items[t];
         const BtInst& in = insts[it.inst];
+        const int tn = t + gridDim.x;
+        float* nb = vbuf + (buf ^ 1) * 3 * kMaxTw;
+        if (tn < nitems) {
+            const BtItem nx = items[tn];
+            fetch_vectors(nx, insts[nx.inst], nb);
+        } else {
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // this item's copies are in
+        sm.sp = vbuf + buf * 3 * kMaxTw;
+        sm.sv1 = sm.sp + kMaxTw;
+        sm.sv2 = sm.sv1 + kMaxTw;
         switch (it.mode) {
             case LP_QS: consume<TA, LP_QS>(it, in, sm, slot, ph, abortp, status); break;
             case LP_Q: consume<TA, LP_Q>(it, in, sm, slot, ph, abortp, status); break;
@@ -388,25 +423,41 @@ __global__ void __launch_bounds__(kThreadsT, 1) bt_sweep(char* ws, int stage) {
 
 // out[i] = a1 sum_k P[k][i] + a2 sum_k P2[k][i] + b v[i], each partial a
 // (hi, lo) pair converted to FP64, partials added in k order, one rounding.
+// A block takes one chunk of 256 outputs of one job (a flat list built by the
+// host), one output per thread, and loads an output's partials four at a
+// time before adding them, so the loads overlap instead of forming a chain
+// of round trips.
+__device__ __forceinline__ double sum_partials(const float2* P, int64_t ld, int K, int64_t i) {
+    double s = 0.0;
+    int k = 0;
+    for (; k + 4 <= K; k += 4) {
+        float2 h[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) h[u] = __ldcg(P + (int64_t)(k + u) * ld + i);
+#pragma unroll
+        for (int u = 0; u < 4; u++) s += (double)h[u].x + (double)h[u].y;
+    }
+    for (; k < K; k++) {
+        const float2 h = __ldcg(P + (int64_t)k * ld + i);
+        s += (double)h.x + (double)h.y;
+    }
+    return s;
+}
+
 __global__ void __launch_bounds__(256) bt_combine(const char* ws, int stage) {
     const BtHeader* bh = bt_header(ws);
     if (!bh) return;
-    const int nj = bh->ncomb[stage];
+    const int nch = bh->nchunk[stage];
     const BtComb* jobs = reinterpret_cast<const BtComb*>(ws + bh->off_comb[stage]);
-    for (int j = blockIdx.x; j < nj; j += gridDim.x) {
-        const BtComb c = jobs[j];
-        for (int64_t i = threadIdx.x; i < c.len; i += blockDim.x) {
-            double s = 0.0, s2 = 0.0;
-            for (int k = 0; k < c.K; k++) {
-                const float2 h = __ldcg(c.P + (int64_t)k * c.ld + i);
-                s += (double)h.x + (double)h.y;
-            }
-            for (int k = 0; k < c.K2; k++) {
-                const float2 h = __ldcg(c.P2 + (int64_t)k * c.ld + i);
-                s2 += (double)h.x + (double)h.y;
-            }
+    const BtChunk* chunks = reinterpret_cast<const BtChunk*>(ws + bh->off_chunk[stage]);
+    for (int ci = blockIdx.x; ci < nch; ci += gridDim.x) {
+        const BtChunk ch = chunks[ci];
+        const BtComb& c = jobs[ch.job];
+        const int64_t i = (int64_t)ch.start + threadIdx.x;
+        if (i < c.len) {
+            const double s = sum_partials(c.P, c.ld, c.K, i);
             double o = c.a1 * s;
-            if (c.K2 > 0) o = fma(c.a2, s2, o);
+            if (c.K2 > 0) o = fma(c.a2, sum_partials(c.P2, c.ld, c.K2, i), o);
             if (c.v) o = fma(c.b, (double)__ldcg(c.v + i), o);
             c.out[i] = (float)o;
         }
@@ -428,9 +479,10 @@ struct BtPlan {
     std::vector<CombRec> combs;
     int64_t q_elems = 0, s_elems = 0, t_elems = 0;   // float2, float2, float
     // Layout (set by bt_plan_layout).
-    int64_t off_hdr = 0, off_inst = 0, off_items[2][2] = {{0, 0}, {0, 0}}, off_comb[2] = {0, 0};
+    int64_t off_hdr = 0, off_inst = 0, off_items[2][2] = {{0, 0}, {0, 0}}, off_comb[2] = {0, 0}, off_chunk[2] = {0, 0};
+    std::vector<BtChunk> chunks[2];
     int64_t off_q = 0, off_s = 0, off_t = 0;
-    int32_t nitems[2][2] = {{0, 0}, {0, 0}}, ncomb[2] = {0, 0};
+    int32_t nitems[2][2] = {{0, 0}, {0, 0}}, ncomb[2] = {0, 0}, nchunk[2] = {0, 0};
 };
 
 BtPlan* bt_plan_create() { return new BtPlan(); }
@@ -561,12 +613,18 @@ int64_t bt_plan_layout_records(BtPlan* P, int64_t cur) {
     for (const auto& r : P->items) P->nitems[r.stage][r.type]++;
     std::stable_sort(P->combs.begin(), P->combs.end(),
                      [](const BtPlan::CombRec& a, const BtPlan::CombRec& b) { return a.stage < b.stage; });
-    for (const auto& c : P->combs) P->ncomb[c.stage]++;
+    for (int s = 0; s < 2; s++) P->chunks[s].clear();
+    for (const auto& c : P->combs) {
+        const int32_t j = P->ncomb[c.stage]++;
+        for (int64_t st = 0; st < c.c.len; st += 256) P->chunks[c.stage].push_back(BtChunk{j, (int32_t)st});
+    }
+    for (int s = 0; s < 2; s++) P->nchunk[s] = (int32_t)P->chunks[s].size();
     P->off_hdr = region(sizeof(BtHeader));
     P->off_inst = region((int64_t)(P->inst.size() * sizeof(BtInst)));
     for (int s = 0; s < 2; s++)
         for (int t = 0; t < 2; t++) P->off_items[s][t] = region((int64_t)P->nitems[s][t] * (int64_t)sizeof(BtItem));
     for (int s = 0; s < 2; s++) P->off_comb[s] = region((int64_t)P->ncomb[s] * (int64_t)sizeof(BtComb));
+    for (int s = 0; s < 2; s++) P->off_chunk[s] = region((int64_t)P->nchunk[s] * (int64_t)sizeof(BtChunk));
     return cur;
 }
 
@@ -592,6 +650,10 @@ void bt_plan_write(const BtPlan* P, char* img, char* ws) {
         for (int t = 0; t < 2; t++) { h.nitems[s][t] = P->nitems[s][t]; h.off_items[s][t] = P->off_items[s][t]; }
         h.ncomb[s] = P->ncomb[s];
         h.off_comb[s] = P->off_comb[s];
+        h.nchunk[s] = P->nchunk[s];
+        h.off_chunk[s] = P->off_chunk[s];
+        if (!P->chunks[s].empty())
+            std::memcpy(img + P->off_chunk[s], P->chunks[s].data(), P->chunks[s].size() * sizeof(BtChunk));
     }
     std::memcpy(img + P->off_hdr, &h, sizeof(h));
     if (!P->inst.empty()) std::memcpy(img + P->off_inst, P->inst.data(), P->inst.size() * sizeof(BtInst));
@@ -655,7 +717,7 @@ bto_status bt_launch(char* ws, const BtPlan* P, cudaStream_t st) {
             if (t == 0) bt_sweep<float><<<grid, kThreadsT, bt_smem<float>(), st>>>(ws, stage);
             else bt_sweep<__nv_bfloat16><<<grid, kThreadsT, bt_smem<__nv_bfloat16>(), st>>>(ws, stage);
         }
-        const int nc = P ? P->ncomb[stage] : dinf.sms * 8;
+        const int nc = P ? P->nchunk[stage] : dinf.sms * 8;
         if (nc > 0) bt_combine<<<std::min(nc, dinf.sms * 8), 256, 0, st>>>(ws, stage);
     }
     return launch_status();

@@ -245,6 +245,34 @@ __global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kern
                     fetch(j + 4, xa, pa);
                     use(j + 2, xb, pb);
                 }
+            } else if (MODE == PM_Q2) {
+                // GESUMMV: one column of each matrix per step, two buffers taking
+                // turns as in the q-only mode; columns in the same order.
+                double ax[kRPT], bx[kRPT], ay[kRPT], by[kRPT], px = 0.0, py = 0.0;
+                auto fetch2 = [&](int64_t j, double (&x)[kRPT], double (&y)[kRPT], double& pv) {
+                    if (j < c1) {
+                        load_col<VEC>(a.A + j * a.lda, R0, r1, warp, lane, x);
+                        load_col<VEC>(a.B + j * a.ldb, R0, r1, warp, lane, y);
+                        pv = __ldg(a.p + j);
+                    }
+                };
+                auto use2 = [&](int64_t j, const double (&x)[kRPT], const double (&y)[kRPT], double pv) {
+                    if (j < c1) {
+#pragma unroll
+                        for (int k = 0; k < kRPT; k++) {
+                            qacc[k] = fma(x[k], pv, qacc[k]);
+                            qacc2[k] = fma(y[k], pv, qacc2[k]);
+                        }
+                    }
+                };
+                fetch2(c0, ax, bx, px);
+#pragma unroll 1
+                for (int64_t j = c0; j < c1; j += 2) {
+                    fetch2(j + 1, ay, by, py);
+                    use2(j, ax, bx, px);
+                    fetch2(j + 2, ax, bx, px);
+                    use2(j + 1, ay, by, py);
+                }
             } else
             for (int64_t g0 = c0; g0 < c1; g0 += kGroup) {
                 const int nc = (int)((c1 - g0) < kGroup ? (c1 - g0) : kGroup);

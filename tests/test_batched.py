@@ -115,3 +115,24 @@ def test_batch_submit_equals_prepare_run(pinned):
         for i in range(len(specs)):
             for k, (g1, g2) in enumerate(zip(b.result(i), ref[i])):
                 assert np.array_equal(g1, g2, equal_nan=True), (specs[i], k)
+
+
+TALL = [("bicgk", 5000, 700, 5000), ("gemver", 4500, 1300, 4500), ("atax", 4400, 520, 4400),
+        ("gesummv", 4100, 600, 4104), ("bicgk", 4400, 1100, 4400, "bf16"), ("gemver", 4200, 700, 4208, "bf16"),
+        ("atax", 6000, 333, 6000, "bf16"), ("gesummv", 4097, 515, 4104, "bf16"), ("bicgk", 4099, 9, 4100)]
+
+
+@pytest.mark.parametrize("tile_cols", [64, 512])
+def test_batch_tall_and_wide_tma(tile_cols):
+    """Instances taller than one 2048-row tile and wider than one panel (several
+    row-tile partials per column, several panel partials per row) on the TMA
+    path, in FP32 and BF16, with ragged last tiles; equal alone and in the mix."""
+    b = Batch(TALL, seed=13)
+    assert b.run(tile_cols) == 0
+    check_batch(b)
+    mixed = [b.result(i) for i in range(len(TALL))]
+    one = Batch([TALL[5]], seed=13)
+    _copy_instance(one, b, 5)
+    assert one.run(tile_cols) == 0
+    for k, (g1, g2) in enumerate(zip(one.result(0), mixed[5])):
+        assert np.array_equal(g1, g2, equal_nan=True), k

@@ -58,6 +58,7 @@ struct PanelPlan {
     int64_t ntiles = 0;
     int grid = 0;
     int64_t ldq = 0, lds = 0;  // leading dims of the partial arrays
+    int bps = 1;               // blocks per SM the tiles are planned for (reduced-precision sweeps)
 };
 PanelPlan panel_plan(int64_t m, int64_t n, int sms);
 size_t panel_smem_bytes(int mode, const PanelPlan& pl);
@@ -99,7 +100,13 @@ __host__ __device__ inline int64_t lp_row_at(int64_t m, int64_t NR, int64_t rb) 
     return r < m ? r : m;
 }
 inline int64_t lp_col_unit(int a_type) { return a_type == BTO_BF16 ? 32 : 16; }
-PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type);
+// Blocks per SM of an op's reduced-precision sweeps (the plan makes tiles for
+// that many blocks): two for BF16 BICGK, ATAX and GESUMMV, whose sweeps fit two
+// blocks' registers; one otherwise (GEMVER's first pass needs more).
+inline int lp_blocks_per_sm(int op, int a_type) {
+    return (a_type == BTO_BF16 && (op == BTO_OP_BICGK || op == BTO_OP_ATAX || op == BTO_OP_GESUMMV)) ? 2 : 1;
+}
+PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type, int bps = 1);
 
 // TMA path of the batched form (batched_tma.cu): instances whose matrices
 // suit the tensor memory accelerator, as tiles through the reduced-precision
@@ -149,7 +156,7 @@ struct LpArgs {
 // Launches the TMA-fed sweep; returns false (launching nothing) when the
 // layout does not meet the tensor-map rules, so the caller uses the
 // load-instruction sweep instead.
-bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, cudaStream_t st, bto_status* out);
+bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, int bps, cudaStream_t st, bto_status* out);
 
 // ------------------------------------------------------------ ATAX group bands
 // A cooperative grid of G blocks is cut into NG groups of S; group g takes

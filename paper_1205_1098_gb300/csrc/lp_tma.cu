@@ -53,10 +53,19 @@ template <typename TA> struct Cfg {
 template <typename TA>
 constexpr size_t stage_bytes() { return (size_t)kBoxR * Cfg<TA>::BoxC * sizeof(TA); }
 
-template <typename TA>
+// Ring depth for BPS blocks per SM: twelve stages at one block, five each at
+// two (the plan decides; see lp_blocks_per_sm).  With BF16 the consumers have
+// twice the elements per byte of FP32 and wait on shuffle and FMA chains; a
+// second block per SM covers those waits (BF16 BICGK 0.568 -> 0.514 ms at
+// n = 32768).
+template <typename TA, int BPS> struct LpStages {
+    static constexpr int value = BPS == 2 ? 5 : Cfg<TA>::S;
+};
+
+template <typename TA, int BPS>
 size_t tma_smem(int64_t tcmax) {
-    return Cfg<TA>::S * stage_bytes<TA>()                   // ring
-           + 2 * Cfg<TA>::S * sizeof(uint64_t)               // full, empty
+    return LpStages<TA, BPS>::value * stage_bytes<TA>()     // ring
+           + 2 * LpStages<TA, BPS>::value * sizeof(uint64_t)   // full, empty
            + 2 * kConsumerWarps * kBoxR * sizeof(float)      // q reduction (hi, lo)
            + 5 * (size_t)tcmax * sizeof(float) + 128;        // s (hi, lo), p, v1, v2 of the tile
 }
@@ -95,11 +104,11 @@ __device__ __forceinline__ void unpack16(const uint4& raw, float* out) {
     }
 }
 
-template <typename TA, int MODE>
-__global__ void __launch_bounds__(kThreadsT, 1) lp_tma_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                              const LpArgs a) {
+template <typename TA, int MODE, int BPS>
+__global__ void __launch_bounds__(kThreadsT, BPS) lp_tma_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                const LpArgs a) {
     constexpr int V = 16 / sizeof(TA);
-    constexpr int S = Cfg<TA>::S;
+    constexpr int S = LpStages<TA, BPS>::value;
     constexpr int kBoxC = Cfg<TA>::BoxC;
     constexpr int CPW = Cfg<TA>::CPW;
     constexpr bool HAS_Q = (MODE == LP_QS || MODE == LP_Q);
@@ -357,10 +366,10 @@ EncodeFn encode_fn() {
     return fn;
 }
 
-template <typename TA, int MODE>
+template <typename TA, int MODE, int BPS>
 bto_status launch_t(const CUtensorMap& map, const LpArgs& a, int grid, cudaStream_t st) {
-    auto k = lp_tma_kernel<TA, MODE>;
-    const size_t smem = tma_smem<TA>(a.tcmax);
+    auto k = lp_tma_kernel<TA, MODE, BPS>;
+    const size_t smem = tma_smem<TA, BPS>(a.tcmax);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return BTO_ERR_CUDA;
     k<<<grid, kThreadsT, smem, st>>>(map, a);
@@ -384,12 +393,13 @@ bool encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, size_t esize, c
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type) {
+PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type, int bps) {
     PanelPlan pl;
+    pl.bps = bps;
     pl.ldq = round_up(m > 0 ? m : 1, 32);
     pl.lds = round_up(n > 0 ? n : 1, 32);
     if (m <= 0 || n <= 0) return pl;
-    const int64_t G = sms, cu = lp_col_unit(a_type);
+    const int64_t G = (int64_t)sms * bps, cu = lp_col_unit(a_type);
     const int64_t cunits = ceil_div(n, cu), runits = ceil_div(m, kBoxR);
     const int64_t NC = std::min<int64_t>(G, cunits);
     const int64_t NR = std::max<int64_t>(1, std::min<int64_t>(G / NC, runits));
@@ -401,7 +411,7 @@ PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type) {
     return pl;
 }
 
-bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, cudaStream_t st, bto_status* out) {
+bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, int bps, cudaStream_t st, bto_status* out) {
     const size_t es = a_type == BTO_F32 ? 4 : 2;
     const void* base = a.A;
     CUtensorMap map;
@@ -417,17 +427,23 @@ bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, cudaStream_t
     if (!encode_tmap_2d(&map, dt, es, base, a.m, a.n, a.lda, kBoxR, bc)) return false;
     if (a_type == BTO_F32) {
         switch (mode) {
-            case LP_QS: *out = launch_t<float, LP_QS>(map, a, grid, st); return true;
-            case LP_Q: *out = launch_t<float, LP_Q>(map, a, grid, st); return true;
-            case LP_G1: *out = launch_t<float, LP_G1>(map, a, grid, st); return true;
-            case LP_S: *out = launch_t<float, LP_S>(map, a, grid, st); return true;
+            case LP_QS: *out = launch_t<float, LP_QS, 1>(map, a, grid, st); return true;
+            case LP_Q: *out = launch_t<float, LP_Q, 1>(map, a, grid, st); return true;
+            case LP_G1: *out = launch_t<float, LP_G1, 1>(map, a, grid, st); return true;
+            case LP_S: *out = launch_t<float, LP_S, 1>(map, a, grid, st); return true;
+        }
+    } else if (bps == 2) {
+        switch (mode) {   // GEMVER's first pass (LP_G1) is planned for one block per SM
+            case LP_QS: *out = launch_t<__nv_bfloat16, LP_QS, 2>(map, a, grid, st); return true;
+            case LP_Q: *out = launch_t<__nv_bfloat16, LP_Q, 2>(map, a, grid, st); return true;
+            case LP_S: *out = launch_t<__nv_bfloat16, LP_S, 2>(map, a, grid, st); return true;
         }
     } else {
         switch (mode) {
-            case LP_QS: *out = launch_t<__nv_bfloat16, LP_QS>(map, a, grid, st); return true;
-            case LP_Q: *out = launch_t<__nv_bfloat16, LP_Q>(map, a, grid, st); return true;
-            case LP_G1: *out = launch_t<__nv_bfloat16, LP_G1>(map, a, grid, st); return true;
-            case LP_S: *out = launch_t<__nv_bfloat16, LP_S>(map, a, grid, st); return true;
+            case LP_QS: *out = launch_t<__nv_bfloat16, LP_QS, 1>(map, a, grid, st); return true;
+            case LP_Q: *out = launch_t<__nv_bfloat16, LP_Q, 1>(map, a, grid, st); return true;
+            case LP_G1: *out = launch_t<__nv_bfloat16, LP_G1, 1>(map, a, grid, st); return true;
+            case LP_S: *out = launch_t<__nv_bfloat16, LP_S, 1>(map, a, grid, st); return true;
         }
     }
     return false;

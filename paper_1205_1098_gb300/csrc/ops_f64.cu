@@ -24,7 +24,8 @@ bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type, const D
         return BTO_ERR_UNSUPPORTED;
     WsLayout L;
     size_t cur = WS_HEADER;
-    const PanelPlan pl = a_type == BTO_F64 ? panel_plan(m, n, d.sms) : lp_plan(m, n, d.sms, a_type);
+    const PanelPlan pl = a_type == BTO_F64 ? panel_plan(m, n, d.sms)
+                                           : lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(op, a_type));
     const size_t qp = (size_t)pl.NC * pl.ldq * sizeof(double);
     const size_t sp = (size_t)pl.NR * pl.lds * sizeof(double);
     switch (op) {

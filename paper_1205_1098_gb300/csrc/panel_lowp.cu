@@ -295,7 +295,7 @@ bto_status lp_launch_t(const LpArgs& a, const PanelPlan& pl, bool vec, cudaStrea
 bto_status lp_launch(int a_type, int mode, const LpArgs& a, const PanelPlan& pl, cudaStream_t st) {
     if (pl.ntiles == 0) return BTO_OK;
     bto_status tst;
-    if (lp_tma_launch(a_type, mode, a, (int)std::min<int64_t>(pl.ntiles, pl.grid), st, &tst)) return tst;
+    if (lp_tma_launch(a_type, mode, a, (int)std::min<int64_t>(pl.ntiles, pl.grid), pl.bps, st, &tst)) return tst;
     const size_t es = a_type == BTO_F32 ? 4 : 2;
     const int64_t V = 16 / (int64_t)es;
     bool vec = aligned16(a.A) && (a.lda % V == 0);
@@ -349,7 +349,7 @@ extern "C" bto_status bto_bicgk_ex(int64_t m, int64_t n, int a_type, const void*
     }
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = lp_plan(m, n, d.sms, a_type);
+    const PanelPlan pl = lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(BTO_OP_BICGK, a_type));
     char* w = static_cast<char*>(ws);
     if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
     LpArgs a{};
@@ -445,7 +445,7 @@ extern "C" bto_status bto_atax_ex(int64_t m, int64_t n, float beta, int a_type, 
     }
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = lp_plan(m, n, d.sms, a_type);
+    const PanelPlan pl = lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(BTO_OP_ATAX, a_type));
     char* w = static_cast<char*>(ws);
     if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
     if (n == 0) return BTO_OK;
@@ -489,7 +489,7 @@ extern "C" bto_status bto_gesummv_ex(int64_t m, int64_t n, float alpha, float be
     }
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = lp_plan(m, n, d.sms, a_type);
+    const PanelPlan pl = lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(BTO_OP_GESUMMV, a_type));
     char* w = static_cast<char*>(ws);
     if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
     LpArgs a{};

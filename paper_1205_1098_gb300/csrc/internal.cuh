@@ -101,10 +101,11 @@ __host__ __device__ inline int64_t lp_row_at(int64_t m, int64_t NR, int64_t rb) 
 }
 inline int64_t lp_col_unit(int a_type) { return a_type == BTO_BF16 ? 32 : 16; }
 // Blocks per SM of an op's reduced-precision sweeps (the plan makes tiles for
-// that many blocks): two for BF16 BICGK, ATAX and GESUMMV, whose sweeps fit two
-// blocks' registers; one otherwise (GEMVER's first pass needs more).
+// that many blocks): two for BICGK and for BF16 ATAX and GESUMMV, whose sweeps
+// fit two blocks' registers; one otherwise (GEMVER's first pass needs more).
 inline int lp_blocks_per_sm(int op, int a_type) {
-    return (a_type == BTO_BF16 && (op == BTO_OP_BICGK || op == BTO_OP_ATAX || op == BTO_OP_GESUMMV)) ? 2 : 1;
+    return ((a_type == BTO_BF16 && (op == BTO_OP_BICGK || op == BTO_OP_ATAX || op == BTO_OP_GESUMMV)) ||
+            (a_type == BTO_F32 && op == BTO_OP_BICGK)) ? 2 : 1;
 }
 PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type, int bps = 1);
 

@@ -425,7 +425,10 @@ bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, int bps, cud
     if (mode == LP_G1 && !(aligned16(a.Bout) && ((size_t)a.ldb * es) % 16 == 0)) return false;
     const uint32_t bc = a_type == BTO_F32 ? box_cols<float>() : box_cols<__nv_bfloat16>();
     if (!encode_tmap_2d(&map, dt, es, base, a.m, a.n, a.lda, kBoxR, bc)) return false;
-    if (a_type == BTO_F32) {
+    if (a_type == BTO_F32 && bps == 2 && mode == LP_QS) {
+        *out = launch_t<float, LP_QS, 2>(map, a, grid, st);
+        return true;
+    } else if (a_type == BTO_F32) {
         switch (mode) {
             case LP_QS: *out = launch_t<float, LP_QS, 1>(map, a, grid, st); return true;
             case LP_Q: *out = launch_t<float, LP_Q, 1>(map, a, grid, st); return true;

@@ -221,16 +221,26 @@ __device__ __forceinline__ void consume(const BtItem& it, const BtInst& in, cons
                                 const float v1j = sm.sv1[lc], v2j = sm.sv2[lc];
                                 TA bq[kRPT];
                                 float bf[kRPT];
+                                unsigned bw[kRPT / 2];     // BF16: the rounded pairs as stored
 #pragma unroll
                                 for (int k = 0; k < kRPT; k += 2) {
                                     const float2 t = __ffma2_rn(make_float2(u2r[k], u2r[k + 1]), make_float2(v2j, v2j),
                                                                 __ffma2_rn(make_float2(u1r[k], u1r[k + 1]),
                                                                            make_float2(v1j, v1j),
                                                                            make_float2(av[k], av[k + 1])));
-                                    bq[k] = from_f<TA>(t.x);
-                                    bq[k + 1] = from_f<TA>(t.y);
-                                    bf[k] = to_f<TA>(bq[k]);
-                                    bf[k + 1] = to_f<TA>(bq[k + 1]);
+                                    if constexpr (sizeof(TA) == 2) {
+                                        // One conversion rounds both rows (nearest even).
+                                        const __nv_bfloat162 b2 = __float22bfloat162_rn(t);
+                                        const unsigned w = *reinterpret_cast<const unsigned*>(&b2);
+                                        bw[k / 2] = w;
+                                        bf[k] = __uint_as_float(w << 16);
+                                        bf[k + 1] = __uint_as_float(w & 0xFFFF0000u);
+                                    } else {
+                                        bq[k] = from_f<TA>(t.x);
+                                        bq[k + 1] = from_f<TA>(t.y);
+                                        bf[k] = to_f<TA>(bq[k]);
+                                        bf[k + 1] = to_f<TA>(bq[k + 1]);
+                                    }
                                 }
                                 TA* bcol = Bout + col * in.ldb;
 #pragma unroll
@@ -238,14 +248,27 @@ __device__ __forceinline__ void consume(const BtItem& it, const BtInst& in, cons
                                     const int64_t i = R0 + h * 32 * V + lane * V;
                                     if (i + V <= r1) {   // B and ldb are 16-byte aligned on this path
                                         uint4 raw;
-                                        TA* e = reinterpret_cast<TA*>(&raw);
+                                        if constexpr (sizeof(TA) == 2) {
+                                            raw = make_uint4(bw[4 * h], bw[4 * h + 1], bw[4 * h + 2], bw[4 * h + 3]);
+                                        } else {
+                                            TA* e = reinterpret_cast<TA*>(&raw);
 #pragma unroll
-                                        for (int q = 0; q < V; q++) e[q] = bq[h * V + q];
+                                            for (int q = 0; q < V; q++) e[q] = bq[h * V + q];
+                                        }
                                         *reinterpret_cast<uint4*>(bcol + i) = raw;
                                     } else {
 #pragma unroll
-                                        for (int q = 0; q < V; q++)
-                                            if (i + q < r1) bcol[i + q] = bq[h * V + q];
+                                        for (int q = 0; q < V; q++) {
+                                            if (i + q < r1) {
+                                                if constexpr (sizeof(TA) == 2) {
+                                                    const unsigned w = bw[(h * V + q) / 2];
+                                                    bcol[i + q] = __ushort_as_bfloat16(
+                                                        (unsigned short)(((h * V + q) & 1) ? (w >> 16) : (w & 0xFFFFu)));
+                                                } else {
+                                                    bcol[i + q] = bq[h * V + q];
+                                                }
+                                            }
+                                        }
                                     }
                                 }
                                 sl[CPW * gs + cc] = dot8(bf, rv);

@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(kThreadsT, BPS) lp_tma_kernel(const __grid_con
                             const float v1j = sv1[lc], v2j = sv2[lc];
                             TA bq[kRPT];
                             float bf[kRPT];
+                            unsigned bw[kRPT / 2];     // BF16: the rounded pairs as stored
 #pragma unroll
                             for (int k = 0; k < kRPT; k += 2) {
                                 // Two rows per packed FMA; per element the same two FMAs as before.
@@ -249,10 +250,21 @@ __global__ void __launch_bounds__(kThreadsT, BPS) lp_tma_kernel(const __grid_con
                                                             __ffma2_rn(make_float2(u1r[k], u1r[k + 1]),
                                                                        make_float2(v1j, v1j),
                                                                        make_float2(av[k], av[k + 1])));
-                                bq[k] = from_f<TA>(t.x);
-                                bq[k + 1] = from_f<TA>(t.y);
-                                bf[k] = to_f<TA>(bq[k]);
-                                bf[k + 1] = to_f<TA>(bq[k + 1]);
+                                if constexpr (sizeof(TA) == 2) {
+                                    // One conversion rounds both rows (nearest even, as the
+                                    // single-value form); the word is what is stored, and its
+                                    // halves widen back with one bit operation each.
+                                    const __nv_bfloat162 b2 = __float22bfloat162_rn(t);
+                                    const unsigned w = *reinterpret_cast<const unsigned*>(&b2);
+                                    bw[k / 2] = w;
+                                    bf[k] = __uint_as_float(w << 16);
+                                    bf[k + 1] = __uint_as_float(w & 0xFFFF0000u);
+                                } else {
+                                    bq[k] = from_f<TA>(t.x);
+                                    bq[k + 1] = from_f<TA>(t.y);
+                                    bf[k] = to_f<TA>(bq[k]);
+                                    bf[k + 1] = to_f<TA>(bq[k + 1]);
+                                }
                             }
                             TA* bcol = Bout + col * a.ldb;
 #pragma unroll
@@ -260,14 +272,27 @@ __global__ void __launch_bounds__(kThreadsT, BPS) lp_tma_kernel(const __grid_con
                                 const int64_t i = R0 + h * 32 * V + lane * V;
                                 if (i + V <= r1) {   // B and ldb are 16-byte aligned on this path
                                     uint4 raw;
-                                    TA* e = reinterpret_cast<TA*>(&raw);
+                                    if constexpr (sizeof(TA) == 2) {
+                                        raw = make_uint4(bw[4 * h], bw[4 * h + 1], bw[4 * h + 2], bw[4 * h + 3]);
+                                    } else {
+                                        TA* e = reinterpret_cast<TA*>(&raw);
 #pragma unroll
-                                    for (int q = 0; q < V; q++) e[q] = bq[h * V + q];
+                                        for (int q = 0; q < V; q++) e[q] = bq[h * V + q];
+                                    }
                                     *reinterpret_cast<uint4*>(bcol + i) = raw;
                                 } else {
 #pragma unroll
-                                    for (int q = 0; q < V; q++)
-                                        if (i + q < r1) bcol[i + q] = bq[h * V + q];
+                                    for (int q = 0; q < V; q++) {
+                                        if (i + q < r1) {
+                                            if constexpr (sizeof(TA) == 2) {
+                                                const unsigned w = bw[(h * V + q) / 2];
+                                                const unsigned short bits = (unsigned short)(((h * V + q) & 1) ? (w >> 16) : (w & 0xFFFFu));
+                                                bcol[i + q] = __ushort_as_bfloat16(bits);
+                                            } else {
+                                                bcol[i + q] = bq[h * V + q];
+                                            }
+                                        }
+                                    }
                                 }
                             }
                             sl[CPW * gs + cc] = dot8(bf, rv);

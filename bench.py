@@ -82,6 +82,10 @@ def flops(k, m, n, N):
 # DRAM bytes (read + write) per call, from one ncu capture (--set full) of the
 # same kernels at n = 8192 on a GB300; traffic grows with m n, so the bench
 # scales it to its own size.  Set to None for a kernel changed since then.
+# The headline metric and workload, shared by this arm and the reference arm.
+METRIC = ("fused FP64 kernel-suite effective HBM bandwidth (GEMVER/BiCGK/ATAX/GESUMMV/DGEMV/DGEMVT at "
+          "n=16384, AXPYDOT/WAXPBY/VADD at 2^26) vs unfused")
+WORKLOAD = "FP64 kernel suite: 16384x16384 column-major matrices, 2^26-element vectors"
 NCU_TRAFFIC_N = 8192
 NCU_TRAFFIC = {
     "gemver": (537.443328 + 493.722880) * 1e6 + (537.009664 + 8.566784) * 1e6,
@@ -401,12 +405,12 @@ def run_reference(args):
     sample = ("per step: the oracle (plain C, FP64, 1 thread) on the suite at n=%d matrices and "
               "%d-element vectors, a bounded sample of the n=16384 / 2^26 workload" % (ns, nv))
     print(json.dumps({
-        "impl": "reference", "metric": "fused FP64 kernel-suite effective HBM bandwidth",
+        "impl": "reference", "metric": METRIC,
         "value": round(value, 4), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * secs / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (SplitMix64 uniform[-1,1), seed 1)",
-        "config": {"workload": "FP64 suite n=16384, vectors 2^26 (bounded host sample)"},
+        "config": {"workload": WORKLOAD, "parallelism": "single"},
         "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -819,14 +823,12 @@ def main():
     launches = args.steps * sum(LAUNCHES[k] for k in KERNELS)
     if rank == 0:
         print(json.dumps({
-            "metric": "fused FP64 kernel-suite effective HBM bandwidth (GEMVER/BiCGK/ATAX/GESUMMV/"
-                      "DGEMV/DGEMVT at n=16384, AXPYDOT/WAXPBY/VADD at 2^26) vs unfused",
+            "metric": METRIC,
             "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (SplitMix64 uniform[-1,1), seed 1), generated on the device",
-            "config": {"workload": "FP64 kernel suite: 16384x16384 column-major matrices, 2^26-element "
-                                   "vectors", "parallelism": "replicas" if world > 1 else "single",
+            "config": {"workload": WORKLOAD, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "every input is larger than L2 (2 GiB matrices, 512 MiB vectors); no flush"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "kernels": per, "unfused": unfused,

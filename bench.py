@@ -245,6 +245,10 @@ def timed_steps(torch, suite, steps, warmup, form, dist, per_kernel=True):
         dist.barrier()
     total = t0.elapsed_time(t1)
     kern = {k: (sum(a.elapsed_time(e) for a, e in ev[k]) / len(ev[k]) if ev[k] else None) for k in KERNELS}
+    # Per-kernel spread over the steps (median, p10, p90 in ms).
+    spread = {k: tuple(float(v) for v in np.percentile([a.elapsed_time(e) for a, e in ev[k]], [50, 10, 90]))
+              for k in KERNELS if ev[k]}
+    timed_steps.spread = spread
     return total / steps, kern
 
 
@@ -502,6 +506,49 @@ def precision_form(torch, bto, hbm, steps, n=32768):
     return out
 
 
+def gemver_small(torch, bto, hbm, reps=30, n=2048):
+    """GEMVER at n = 2048, FP64 (seed 0, alpha 1.5, beta 1.2): its 32 MiB matrix
+    fits in L2, so it is timed warm (back-to-back calls) and cold (a 512 MiB
+    write between calls evicts L2).  Median of `reps` calls each."""
+    f64 = dict(dtype=torch.float64, device="cuda")
+    A, B = torch.empty(n * n, **f64), torch.empty(n * n, **f64)
+    bto.bto_fill_f64(0, 0, 0, n, n, 0, A, n, None)
+    vec = []
+    for aid in range(1, 7):
+        v = torch.empty(n, **f64)
+        bto.bto_fill_f64(0, aid, 0, n, 1, 0, v, n, None)
+        vec.append(v)
+    x, w = torch.empty(n, **f64), torch.empty(n, **f64)
+    nb = bto.bto_workspace_bytes("gemver", 0, n, n)
+    wsb = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(128 << 20, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def call():
+        bto.bto_gemver(n, n, 1.5, 1.2, A, n, *vec, B, n, x, w, wsb, nb, None)
+
+    out = {}
+    for mode in ("warm", "cold"):
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(reps):   # all queued, one wait: host launch gaps stay out of the events
+            if mode == "cold":
+                flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            call()
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
+        byts = compulsory_bytes("gemver", n, n, 0)
+        out[mode] = {"ms": round(ms, 4), "gbs": round(byts / ms / 1e6, 1), "hbm_frac": round(byts / ms / 1e6 / hbm, 3)}
+    out["note"] = "A, B 32 MiB each: warm runs from L2; cold evicts L2 with a 512 MiB write before every call"
+    return out
+
+
 def mrhs_form(torch, bto, hbm, steps, n=8192, k=64, seed=6):
     """Multi-right-hand-side BICGK: Q = A P, S = A^T R with A n x n BF16 and
     k BF16 right-hand sides, FP32 Q and S, on the tensor cores.  Each timed
@@ -638,7 +685,7 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3, tile=0):
             "layout": "column-major, leading dimension rounded up to a multiple of 4 floats"}
 
 
-def serving_form(torch, duration=5.0, rate=20000.0, seed=4):
+def serving_form(torch, duration=10.0, rate=20000.0, seed=4):
     """Config 5: Poisson arrivals at `rate` of mixed GEMVER/BiCGK/ATAX/GESUMMV
     requests, n log-uniform in [64, 8192], FP32 or BF16 matrices by a seeded
     flag, resident operands, admission under a 40 GB budget."""
@@ -748,7 +795,9 @@ def main():
         t = kern[k] * 1e-3
         gbs = compulsory_bytes(k, m, n, N) / t / 1e9
         tf = flops(k, m, n, N) / t / 1e12
-        per[k] = {"ms": round(kern[k], 4), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3),
+        med, p10, p90 = timed_steps.spread[k]
+        per[k] = {"ms": round(kern[k], 4), "ms_median": round(med, 4), "ms_p10": round(p10, 4),
+                  "ms_p90": round(p90, 4), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3),
                   "fp64_tflops": round(tf, 4), "fp64_frac": round(tf / fp64_peak, 3),
                   "bound": "alu" if tf / fp64_peak > gbs / hbm else "hbm"}
 
@@ -811,6 +860,10 @@ def main():
     if not args.no_serving and not args.only:
         torch.cuda.empty_cache()
         serving = serving_form(torch)
+    small = None
+    if not args.only:
+        torch.cuda.empty_cache()
+        small = gemver_small(torch, bto, hbm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -836,6 +889,7 @@ def main():
             "batched_4096": batched,
             "mrhs_8192_k64": mrhs,
             "serving": serving,
+            "gemver_n2048": small,
             "peaks": {"hbm_gbs": hbm, "hbm_source": peak_src, "fp64_tflops": round(fp64_peak, 4)},
         }))
     if dist:

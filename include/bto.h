@@ -378,7 +378,7 @@ bto_status bto_bicgk_mrhs(int64_t m, int64_t n, int64_t k, const uint16_t *A, in
  *  - Size limit: the call is accepted when
  *    bto_workspace_bytes(BTO_OP_BICGK, BTO_FORM_FUSED, m, n, BTO_F64) is at
  *    most BTO_NOALLOC_SCRATCH_BYTES (for square FP64 problems on a 152-SM
- *    GB300, up to about n = 3400); larger problems return BTO_ERR_WORKSPACE
+ *    GB300, every n up to 3427); larger workspaces return BTO_ERR_WORKSPACE
  *    with bto_last_invalid_arg() naming m (1) or n (2), and nothing runs.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call

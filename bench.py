@@ -35,7 +35,7 @@ FP64_FLOP_PER_CLK_PER_SM = 4.0   # 2 FP64 FMA per clock per SM (measured: 2.05)
 
 KERNELS = ["bicgk", "atax", "gesummv", "gemver", "dgemv", "dgemvt", "axpydot", "waxpby", "vadd"]
 MATRIX_KERNELS = KERNELS[:6]
-# Launches of our kernels per call (panel pass(es) + combine(s); ATAX is one cooperative kernel).
+# Launches of our kernels per call (panel pass(es) + combine(s); ATAX: its cooperative kernel + combine).
 LAUNCHES = {"bicgk": 2, "atax": 2, "gesummv": 2, "gemver": 4, "dgemv": 2, "dgemvt": 4,
             "axpydot": 2, "waxpby": 1, "vadd": 1}
 UNFUSED_LAUNCHES = {"bicgk": 4, "atax": 5, "gesummv": 4, "gemver": 8, "dgemv": 3, "dgemvt": 5,

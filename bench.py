@@ -549,6 +549,29 @@ def gemver_small(torch, bto, hbm, reps=30, n=2048):
     return out
 
 
+def schedule_search_form(torch, n=N_MAT, pop=8, gens=5, seed=0):
+    """The measured-cost schedule search (f2) on each FP64 matrix kernel at
+    n x n: genetic search (seeded with the fused automatic schedule) and
+    exhaustive search over the same space, each with its number of distinct
+    schedules measured; fitness = median of 5 calls (CUDA events)."""
+    from paper_1205_1098_gb300 import schedule_search as S
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = {}
+    for op in S.OPS:
+        prob = S.Problem(op, n, n)
+        auto = prob.fitness((True, 0, 0))
+        ga = S.mfga(op, prob.fitness, sms, pop=pop, gens=gens, seed=seed)
+        ex = S.exhaustive(op, prob.fitness, sms)
+        name = lambda o: "%s, panels %s, row blocks %s" % ("fused" if o[0] else "unfused", o[1] or "auto", o[2] or "auto")
+        out[op] = {"fused_auto_ms": round(auto, 4),
+                   "ga": {"best": name(ga["best"]), "ms": round(ga["best_ms"], 4), "evaluations": ga["evaluations"]},
+                   "exhaustive": {"best": name(ex["best"]), "ms": round(ex["best_ms"], 4),
+                                  "evaluations": ex["evaluations"]}}
+        del prob
+        torch.cuda.empty_cache()
+    return out
+
+
 def mrhs_form(torch, bto, hbm, steps, n=8192, k=64, seed=6):
     """Multi-right-hand-side BICGK: Q = A P, S = A^T R with A n x n BF16 and
     k BF16 right-hand sides, FP32 Q and S, on the tensor cores.  Each timed
@@ -715,6 +738,8 @@ def main():
     ap.add_argument("--batched-only", action="store_true", help="profiling runs: only the batched form")
     ap.add_argument("--batched-count", type=int, default=4096, help="instances in the batched form")
     ap.add_argument("--batched-tile", type=int, default=0, help="profiling runs: fixed panel width (no tuner)")
+    ap.add_argument("--no-search", action="store_true", help="skip the schedule search")
+    ap.add_argument("--search-only", type=int, default=0, help="only the schedule search, at this n")
     ap.add_argument("--mrhs-only", type=int, default=0, help="profiling runs: only multi-RHS BICGK with this k")
     ap.add_argument("--no-mrhs", action="store_true")
     ap.add_argument("--precision-only", type=int, default=0,
@@ -751,6 +776,12 @@ def main():
         hbm, _, _ = load_peaks()
         print(json.dumps({"mrhs": mrhs_form(torch, bto, hbm, args.steps, n=args.n if args.n != N_MAT else 8192,
                                             k=args.mrhs_only)}))
+        return
+    if args.search_only:
+        import torch
+        from paper_1205_1098_gb300 import build
+        build.build()
+        print(json.dumps({"schedule_search": schedule_search_form(torch, n=args.search_only)}))
         return
     if args.precision_only:
         import torch
@@ -864,6 +895,10 @@ def main():
     if not args.only:
         torch.cuda.empty_cache()
         small = gemver_small(torch, bto, hbm)
+    search = None
+    if not args.no_search and not args.only:
+        torch.cuda.empty_cache()
+        search = schedule_search_form(torch, n=m)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -890,6 +925,7 @@ def main():
             "mrhs_8192_k64": mrhs,
             "serving": serving,
             "gemver_n2048": small,
+            "schedule_search": search,
             "peaks": {"hbm_gbs": hbm, "hbm_source": peak_src, "fp64_tflops": round(fp64_peak, 4)},
         }))
     if dist:

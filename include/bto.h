@@ -168,6 +168,21 @@ bto_status bto_waxpby(int64_t n, double alpha, const double *x, double beta,
 bto_status bto_vadd(int64_t n, const double *w, const double *y, const double *z,
                     double *x, bto_stream_t stream);
 
+/* --------------------------------------------------------- schedule overrides
+ * The FP64 matrix kernels (BICGK, ATAX's two-pass forms, GEMVER, GESUMMV,
+ * DGEMV, DGEMVT; op < BTO_OP_AXPYDOT) split A into row blocks x column panels
+ * whose partial sums a fixed-order combine adds.  These calls replace the
+ * automatic numbers of panels and row blocks for one (op, form), process-wide,
+ * so that a measured-cost search (the paper's empirical search, Section IV)
+ * can explore the schedules; 0 restores the automatic choice.  Set them before
+ * the calls and the bto_workspace_bytes queries they should affect.  Panels are
+ * clamped to [ceil(n / 512), n] and row blocks to [1, ceil(m / 64)].  Results
+ * stay within the usual tolerance under any schedule (the split changes the
+ * summation order).  ATAX's fused group-band kernel has its own plan; its
+ * schedule applies to its two-pass form (and to bto_unfused_atax). */
+bto_status bto_schedule_set(int op, int form, int panels, int row_blocks);
+bto_status bto_schedule_get(int op, int form, int *panels, int *row_blocks);
+
 /* ------------------------------------------- reduced-precision storage form
  * BICGK, GEMVER, ATAX and GESUMMV (Table I) with the matrices stored in FP32
  * or BF16 to cut the bytes of this bandwidth-bound path (the paper's kernels

@@ -47,6 +47,7 @@ SIGNATURES = {
     "bto_batch_prepare": "kpkpzs",
     "bto_batch_run": "pzs",
     "bto_batch_submit": "kpkpzpzs",
+    "bto_schedule_set": "kkkk",
     "bto_bicgk_mrhs": "iiipipipipipipzs",
 }
 _KIND = {"i": _c_i64, "u": _c_u64, "d": _c_f64, "f": ctypes.c_float, "p": _c_ptr, "z": _c_size,
@@ -189,6 +190,20 @@ def bto_bicgk_mrhs_workspace_bytes(m, n, k):
     return out.value
 
 
+def bto_schedule_get(op, form):
+    """(panels, row_blocks) set for (op, form); 0 means automatic."""
+    if isinstance(op, str):
+        op = OPS[op]
+    a, b = _c_int(0), _c_int(0)
+    L = lib()
+    L.bto_schedule_get.argtypes = [_c_int, _c_int, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]
+    L.bto_schedule_get.restype = _c_int
+    st = L.bto_schedule_get(int(op), int(form), ctypes.byref(a), ctypes.byref(b))
+    if st != BTO_OK:
+        raise BtoError("bto_schedule_get", st, L.bto_last_invalid_arg())
+    return a.value, b.value
+
+
 def bto_device_status(ws, stream=None):
     out = _c_int(0)
     L = lib()
@@ -265,4 +280,4 @@ def exported_symbols():
     return sorted(list(SIGNATURES) + ["bto_version", "bto_status_string", "bto_last_invalid_arg",
                                       "bto_workspace_bytes", "bto_device_status",
                                       "bto_bicgk_mrhs_workspace_bytes", "bto_batch_workspace_bytes",
-                                      "bto_serve_run"])
+                                      "bto_serve_run", "bto_schedule_get"])

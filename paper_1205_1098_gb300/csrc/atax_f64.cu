@@ -326,7 +326,7 @@ bto_status atax_impl(int64_t m, int64_t n, double beta, const double* A, int64_t
     if (!ap.fused) {
         // Slices too wide for shared memory: t = A x into the workspace, then
         // y = beta A^T t (A is read twice).
-        const PanelPlan pl = panel_plan(m, n, d.sms);
+        const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_ATAX, BTO_FORM_FUSED);
         double* t = reinterpret_cast<double*>(w + L.off[0]);
         PanelArgs a{};
         a.m = m; a.n = n; a.A = A; a.lda = lda; a.p = x;

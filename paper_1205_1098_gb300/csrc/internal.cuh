@@ -60,7 +60,8 @@ struct PanelPlan {
     int64_t ldq = 0, lds = 0;  // leading dims of the partial arrays
     int bps = 1;               // blocks per SM the tiles are planned for (reduced-precision sweeps)
 };
-PanelPlan panel_plan(int64_t m, int64_t n, int sms);
+// op and form select a schedule override (bto_schedule_set); op < 0: none.
+PanelPlan panel_plan(int64_t m, int64_t n, int sms, int op = -1, int form = BTO_FORM_FUSED);
 size_t panel_smem_bytes(int mode, const PanelPlan& pl);
 
 struct PanelArgs {

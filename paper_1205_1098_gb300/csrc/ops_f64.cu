@@ -24,7 +24,7 @@ bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type, const D
         return BTO_ERR_UNSUPPORTED;
     WsLayout L;
     size_t cur = WS_HEADER;
-    const PanelPlan pl = a_type == BTO_F64 ? panel_plan(m, n, d.sms)
+    const PanelPlan pl = a_type == BTO_F64 ? panel_plan(m, n, d.sms, op, form)
                                            : lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(op, a_type));
     const size_t qp = (size_t)pl.NC * pl.ldq * sizeof(double);
     const size_t sp = (size_t)pl.NR * pl.lds * sizeof(double);
@@ -107,7 +107,7 @@ extern "C" bto_status bto_bicgk(int64_t m, int64_t n, const double* A, int64_t l
     if (!c.ok()) return c.finish();
 
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = panel_plan(m, n, d.sms);
+    const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_BICGK, BTO_FORM_FUSED);
     PanelArgs a{};
     a.m = m; a.n = n; a.A = A; a.lda = lda; a.p = p; a.r = r;
     a.qpart = wsd(ws, L.off[0]); a.spart = wsd(ws, L.off[1]);
@@ -138,7 +138,7 @@ extern "C" bto_status bto_dgemv(int64_t m, int64_t n, double alpha, const double
     if (!c.ok()) return c.finish();
 
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = panel_plan(m, n, d.sms);
+    const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_DGEMV, BTO_FORM_FUSED);
     PanelArgs a{};
     a.m = m; a.n = n; a.A = A; a.lda = lda; a.p = x;
     a.qpart = wsd(ws, L.off[0]);
@@ -169,7 +169,7 @@ extern "C" bto_status bto_gesummv(int64_t m, int64_t n, double alpha, const doub
     if (!c.ok()) return c.finish();
 
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = panel_plan(m, n, d.sms);
+    const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_GESUMMV, BTO_FORM_FUSED);
     PanelArgs a{};
     a.m = m; a.n = n; a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.p = x;
     a.qpart = wsd(ws, L.off[0]); a.qpart2 = wsd(ws, L.off[1]);
@@ -201,7 +201,7 @@ extern "C" bto_status bto_dgemvt(int64_t m, int64_t n, double alpha, double beta
     if (!c.ok()) return c.finish();
 
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = panel_plan(m, n, d.sms);
+    const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_DGEMVT, BTO_FORM_FUSED);
     PanelArgs a{};
     a.m = m; a.n = n; a.A = A; a.lda = lda; a.r = y;
     a.qpart = wsd(ws, L.off[0]); a.spart = wsd(ws, L.off[1]);
@@ -250,7 +250,7 @@ extern "C" bto_status bto_gemver(int64_t m, int64_t n, double alpha, double beta
     if (!c.ok()) return c.finish();
 
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = panel_plan(m, n, d.sms);
+    const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_GEMVER, BTO_FORM_FUSED);
     PanelArgs a{};
     a.m = m; a.n = n; a.A = A; a.lda = lda; a.Bout = B; a.ldb = ldb;
     a.u1 = u1; a.v1 = v1; a.u2 = u2; a.v2 = v2; a.r = y;

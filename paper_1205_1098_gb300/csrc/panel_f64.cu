@@ -25,6 +25,7 @@
 // per-panel partial vector that a second kernel adds up in panel order.
 // All sums run in a fixed order, so results are bitwise reproducible.
 #include "internal.cuh"
+#include <atomic>
 #include <algorithm>
 
 namespace bto {
@@ -431,7 +432,16 @@ bto_status launch_mode(const PanelArgs& a, const PanelPlan& pl, bool vec2, cudaS
 
 }  // namespace
 
-PanelPlan panel_plan(int64_t m, int64_t n, int sms) {
+namespace {
+
+// Schedule overrides, per (op, form): column panels and row blocks (0: the
+// automatic choice).  Set from the host before the calls they affect.
+constexpr int kSchedOps = BTO_OP_DGEMVT + 1;
+std::atomic<int> g_sched[kSchedOps][2][2];
+
+}  // namespace
+
+PanelPlan panel_plan(int64_t m, int64_t n, int sms, int op, int form) {
     PanelPlan pl;
     pl.ldq = round_up(m > 0 ? m : 1, 32);
     pl.lds = round_up(n > 0 ? n : 1, 32);
@@ -452,6 +462,21 @@ PanelPlan panel_plan(int64_t m, int64_t n, int sms) {
         int64_t want = std::min<int64_t>(n, ceil_div(2 * G, NR));
         want = std::min<int64_t>(want, std::max<int64_t>(1, ((int64_t)3 << 20) / (8 * round_up(m, 32))));
         NC = std::max(NC, ceil_div(n, ceil_div(n, want)));
+    }
+    // Fused GEMVER: one chunk per row block (at n = 16384, 8 row blocks of
+    // 2048 rows instead of 2), as the measured schedule search found best for
+    // it (1.96 -> 1.92 ms); the other kernels' optima were within 1% of the
+    // plan above.
+    if (op == BTO_OP_GEMVER && form == BTO_FORM_FUSED) NR = std::max<int64_t>(NR, ceil_div(m, kChunk));
+    // A schedule set with bto_schedule_set replaces the choices above.
+    if (op >= 0 && op < kSchedOps && (form == BTO_FORM_FUSED || form == BTO_FORM_UNFUSED)) {
+        const int hp = g_sched[op][form][0].load(std::memory_order_relaxed);
+        const int hr = g_sched[op][form][1].load(std::memory_order_relaxed);
+        if (hp > 0) {
+            NC = std::min<int64_t>(hp, n);
+            if (ceil_div(n, NC) > kMaxPanel) NC = ceil_div(n, kMaxPanel);
+        }
+        if (hr > 0) NR = std::min<int64_t>(hr, ceil_div(m, 64));
     }
     // Row blocks start on multiples of 64: drop blocks that would be empty.
     while (NR > 1 && row_split_at(m, NR, 1) == 0) NR--;
@@ -498,3 +523,27 @@ bto_status launch_combine(const CombineJob* jobs, int njobs, cudaStream_t st) {
 }
 
 }  // namespace bto
+
+using namespace bto;
+
+extern "C" bto_status bto_schedule_set(int op, int form, int panels, int row_blocks) {
+    clear_invalid_arg();
+    if (op < BTO_OP_BICGK || op > BTO_OP_DGEMVT) { set_invalid_arg(1); return BTO_ERR_INVALID_VALUE; }
+    if (form != BTO_FORM_FUSED && form != BTO_FORM_UNFUSED) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
+    if (panels < 0 || panels > (1 << 20)) { set_invalid_arg(3); return BTO_ERR_INVALID_VALUE; }
+    if (row_blocks < 0 || row_blocks > (1 << 20)) { set_invalid_arg(4); return BTO_ERR_INVALID_VALUE; }
+    g_sched[op][form][0].store(panels, std::memory_order_relaxed);
+    g_sched[op][form][1].store(row_blocks, std::memory_order_relaxed);
+    return BTO_OK;
+}
+
+extern "C" bto_status bto_schedule_get(int op, int form, int* panels, int* row_blocks) {
+    clear_invalid_arg();
+    if (op < BTO_OP_BICGK || op > BTO_OP_DGEMVT) { set_invalid_arg(1); return BTO_ERR_INVALID_VALUE; }
+    if (form != BTO_FORM_FUSED && form != BTO_FORM_UNFUSED) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
+    if (!panels) { set_invalid_arg(3); return BTO_ERR_INVALID_VALUE; }
+    if (!row_blocks) { set_invalid_arg(4); return BTO_ERR_INVALID_VALUE; }
+    *panels = g_sched[op][form][0].load(std::memory_order_relaxed);
+    *row_blocks = g_sched[op][form][1].load(std::memory_order_relaxed);
+    return BTO_OK;
+}

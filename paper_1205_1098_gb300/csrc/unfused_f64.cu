@@ -118,7 +118,7 @@ struct Ctx {
 bool make_ctx(int op, int64_t m, int64_t n, void* ws, Ctx* c) {
     if (!device_info(&c->d)) return false;
     if (ws_layout(op, BTO_FORM_UNFUSED, m, n, BTO_F64, c->d, &c->L) != BTO_OK) return false;
-    c->pl = panel_plan(m, n, c->d.sms);
+    c->pl = panel_plan(m, n, c->d.sms, op, BTO_FORM_UNFUSED);
     c->w = static_cast<char*>(ws);
     return true;
 }

@@ -180,3 +180,21 @@ def test_serve_validation_without_gpu(L):
     assert run() == (bto.BTO_ERR_INVALID_VALUE, 3)           # no resident BF16 matrix
     reqs[1].a_type, reqs[0].t = bto.BTO_F32, 1.0
     assert run() == (bto.BTO_ERR_INVALID_VALUE, 3)           # arrivals out of order
+
+
+def test_schedule_overrides_without_gpu(L):
+    """bto_schedule_set/get: per (op, form), validated, 0 = automatic, no GPU."""
+    try:
+        for form in (0, 1):
+            assert bto.bto_schedule_get("gemver", form) == (0, 0)
+        bto.bto_schedule_set(bto.OPS["gemver"], 1, 96, 3)
+        assert bto.bto_schedule_get("gemver", 1) == (96, 3)
+        assert bto.bto_schedule_get("gemver", 0) == (0, 0)
+        for bad, arg in (((9, 0, 1, 1), 1), ((8, 0, 1, 1), 1), ((0, 2, 1, 1), 2), ((0, 0, -1, 1), 3),
+                         ((0, 0, 1, (1 << 20) + 1), 4)):
+            with pytest.raises(bto.BtoError) as e:
+                bto.bto_schedule_set(*bad)
+            assert e.value.status == bto.BTO_ERR_INVALID_VALUE and e.value.arg == arg, bad
+    finally:
+        bto.bto_schedule_set(bto.OPS["gemver"], 1, 0, 0)
+    assert bto.bto_schedule_get("gemver", 1) == (0, 0)

@@ -88,8 +88,8 @@ METRIC = ("fused FP64 kernel-suite effective HBM bandwidth (GEMVER/BiCGK/ATAX/GE
 WORKLOAD = "FP64 kernel suite: 16384x16384 column-major matrices, 2^26-element vectors"
 NCU_TRAFFIC_N = 8192
 NCU_TRAFFIC = {
-    "gemver": (537.443328 + 493.722880) * 1e6 + (537.009664 + 8.566784) * 1e6,
-    "atax": (545.658368 + 3.995136) * 1e6,
+    "gemver": (537.580544 + 492.955392) * 1e6 + (537.008128 + 8.569088) * 1e6,
+    "atax": (545.888768 + 3.536128) * 1e6,
 }
 
 
@@ -572,6 +572,70 @@ def schedule_search_form(torch, n=N_MAT, pop=8, gens=5, seed=0):
     return out
 
 
+def layout_form(torch, bto, fp64_peak, n=N_MAT, reps=7, seed=1):
+    """Storage order and transposition (f1) at n x n: each FP64 matrix kernel on
+    column-major storage (the ordinary entry point) and on row-major storage
+    (bto_*_layout), and DGEMV with and without transposition in both orders.
+    Median of `reps` calls after 2 warm-ups (CUDA events); both matrices are
+    2 GiB, larger than L2."""
+    f64 = dict(dtype=torch.float64, device="cuda")
+    A, B, Bo = (torch.empty(n * n, **f64) for _ in range(3))
+    bto.bto_fill_f64(seed, 0, 0, n, n, 0, A, n, None)
+    bto.bto_fill_f64(seed, 1, 0, n, n, 0, B, n, None)
+    v = []
+    for aid in range(10, 18):
+        t = torch.empty(n, **f64)
+        bto.bto_fill_f64(seed, aid, 0, n, 1, 0, t, n, None)
+        v.append(t)
+    o1, o2 = torch.empty(n, **f64), torch.empty(n, **f64)
+    st = torch.cuda.current_stream()
+    COL, ROW = bto.BTO_COL_MAJOR, bto.BTO_ROW_MAJOR
+
+    def time(call):
+        for _ in range(2):
+            call()
+        evs = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            call()
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in evs]))
+
+    def calls(op, lay, trans, ws, nb):
+        if op == "bicgk":
+            return lambda: bto.bto_bicgk_layout(lay, n, n, A, n, v[0], v[1], o1, o2, ws, nb)
+        if op == "atax":
+            return lambda: bto.bto_atax_layout(lay, n, n, 1.25, A, n, v[0], o1, ws, nb)
+        if op == "gemver":
+            return lambda: bto.bto_gemver_layout(lay, n, n, 1.5, 1.2, A, n, *v[2:8], Bo, n, o1, o2, ws, nb)
+        if op == "gesummv":
+            return lambda: bto.bto_gesummv_layout(lay, n, n, 1.5, A, n, -0.75, B, n, v[0], o1, ws, nb)
+        if op == "dgemv":
+            return lambda: bto.bto_dgemv_layout(lay, trans, n, n, 1.5, A, n, v[0], -0.5, v[1], o1, ws, nb)
+        return lambda: bto.bto_dgemvt_layout(lay, n, n, 1.5, 1.2, A, n, v[1], v[0], o1, o2, ws, nb)
+
+    out = {}
+    cases = [(op, 0) for op in ("bicgk", "atax", "gemver", "gesummv", "dgemvt")] + [("dgemv", 0), ("dgemv", 1)]
+    for op, trans in cases:
+        row = {}
+        for lay, name in ((COL, "col_major"), (ROW, "row_major")):
+            nb = bto.bto_layout_workspace_bytes(op, lay, trans, n, n)
+            ws = torch.empty(max(nb, 1), dtype=torch.uint8, device="cuda")
+            ms = time(calls(op, lay, trans, ws, nb))
+            tf = flops(op, n, n, 0) / ms / 1e9
+            row[name] = {"ms": round(ms, 4), "fp64_tflops": round(tf, 4), "fp64_frac": round(tf / fp64_peak, 3)}
+            del ws
+        out[op + ("_trans" if trans else "")] = row
+    out["note"] = ("row-major A is the column-major A^T: BICGK one pass, GEMVER/DGEMVT two, GESUMMV one pass "
+                   "per matrix, BATAX two passes (A read twice)")
+    del A, B, Bo
+    torch.cuda.empty_cache()
+    return out
+
+
 def mrhs_form(torch, bto, hbm, steps, n=8192, k=64, seed=6):
     """Multi-right-hand-side BICGK: Q = A P, S = A^T R with A n x n BF16 and
     k BF16 right-hand sides, FP32 Q and S, on the tensor cores.  Each timed
@@ -742,6 +806,8 @@ def main():
     ap.add_argument("--search-only", type=int, default=0, help="only the schedule search, at this n")
     ap.add_argument("--mrhs-only", type=int, default=0, help="profiling runs: only multi-RHS BICGK with this k")
     ap.add_argument("--no-mrhs", action="store_true")
+    ap.add_argument("--no-layout", action="store_true", help="skip the row-major / transposed forms")
+    ap.add_argument("--layout-only", action="store_true", help="only the row-major / transposed forms")
     ap.add_argument("--precision-only", type=int, default=0,
                     help="profiling runs: only the reduced-precision form at this n")
     ap.add_argument("--n", type=int, default=N_MAT, help="matrix size (profiling runs)")
@@ -776,6 +842,16 @@ def main():
         hbm, _, _ = load_peaks()
         print(json.dumps({"mrhs": mrhs_form(torch, bto, hbm, args.steps, n=args.n if args.n != N_MAT else 8192,
                                             k=args.mrhs_only)}))
+        return
+    if args.layout_only:
+        import torch
+        from paper_1205_1098_gb300 import build
+        build.build()
+        import paper_1205_1098_gb300 as bto
+        _, sm_max, _ = load_peaks()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak = FP64_FLOP_PER_CLK_PER_SM * sms * sm_max * 1e6 / 1e12
+        print(json.dumps({"layout": layout_form(torch, bto, peak, n=args.n)}))
         return
     if args.search_only:
         import torch
@@ -895,6 +971,10 @@ def main():
     if not args.only:
         torch.cuda.empty_cache()
         small = gemver_small(torch, bto, hbm)
+    layout = None
+    if not args.no_layout and not args.only:
+        torch.cuda.empty_cache()
+        layout = layout_form(torch, bto, fp64_peak, n=m)
     search = None
     if not args.no_search and not args.only:
         torch.cuda.empty_cache()
@@ -926,6 +1006,7 @@ def main():
             "serving": serving,
             "gemver_n2048": small,
             "schedule_search": search,
+            "layout_n16384": layout,
             "peaks": {"hbm_gbs": hbm, "hbm_source": peak_src, "fp64_tflops": round(fp64_peak, 4)},
         }))
     if dist:

@@ -168,6 +168,73 @@ bto_status bto_waxpby(int64_t n, double alpha, const double *x, double beta,
 bto_status bto_vadd(int64_t n, const double *w, const double *y, const double *z,
                     double *x, bto_stream_t stream);
 
+/* ------------------------------------------ storage order and transposition
+ * The FP64 matrix sequences on row-major as well as column-major storage, and
+ * DGEMV with a BLAS-style transposition flag.  The paper's type system treats
+ * a matrix as a container of row or column containers and generates code for
+ * either order (Section II; BATAX's A in Fig. 1 is declared row-major).
+ * layout: BTO_COL_MAJOR (element (i, j) at A[i + j*lda], lda >= max(1, m)) or
+ * BTO_ROW_MAJOR (element (i, j) at A[i*lda + j], lda >= max(1, n)); B (GEMVER,
+ * GESUMMV) has the same layout with its own ldb.  The statements, vector
+ * lengths, aliasing rules and errors are those of the column-major entry point
+ * of the same name; argument positions (bto_last_invalid_arg) count the
+ * leading layout (and trans) arguments.  A column-major call is the ordinary
+ * entry point.  On row-major storage the stored matrix is A^T in column-major
+ * order, so the two products of each statement exchange roles in the same
+ * fused passes (BICGK: one pass; GEMVER: two, B written once and read back
+ * once; DGEMVT: two; DGEMV: one).  GESUMMV on row-major storage runs one pass
+ * per matrix (each read once) and BATAX two passes (A read twice: t = A x is
+ * formed in the workspace, then y = beta A^T t).
+ * The workspace is bto_layout_workspace_bytes(op, layout, trans, m, n); it is
+ * the same as bto_workspace_bytes(op, BTO_FORM_FUSED, m, n, BTO_F64) for
+ * column-major calls without transposition.  trans must be BTO_NO_TRANS except
+ * for op = BTO_OP_DGEMV. */
+#define BTO_COL_MAJOR 0
+#define BTO_ROW_MAJOR 1
+#define BTO_NO_TRANS 0
+#define BTO_TRANS 1
+
+bto_status bto_layout_workspace_bytes(int op, int layout, int trans, int64_t m, int64_t n,
+                                      size_t *bytes);
+
+/* BICGK: q <- A p ; s <- A^T r (A m x n in `layout`). */
+bto_status bto_bicgk_layout(int layout, int64_t m, int64_t n, const double *A, int64_t lda,
+                            const double *p, const double *r, double *q, double *s,
+                            void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* BATAX: y <- beta A^T (A x) (A m x n in `layout`; x, y: n). */
+bto_status bto_atax_layout(int layout, int64_t m, int64_t n, double beta, const double *A,
+                           int64_t lda, const double *x, double *y, void *ws, size_t ws_bytes,
+                           bto_stream_t stream);
+
+/* GEMVER: B <- A + u1 v1^T + u2 v2^T ; x <- beta B^T y + z ; w <- alpha B x
+ * (A and B m x n in `layout`; B == A with ldb == lda and x == z allowed). */
+bto_status bto_gemver_layout(int layout, int64_t m, int64_t n, double alpha, double beta,
+                             const double *A, int64_t lda, const double *u1, const double *v1,
+                             const double *u2, const double *v2, const double *y, const double *z,
+                             double *B, int64_t ldb, double *x, double *w,
+                             void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* GESUMMV: y <- alpha A x + beta B x (A, B m x n in `layout`). */
+bto_status bto_gesummv_layout(int layout, int64_t m, int64_t n, double alpha, const double *A,
+                              int64_t lda, double beta, const double *B, int64_t ldb,
+                              const double *x, double *y, void *ws, size_t ws_bytes,
+                              bto_stream_t stream);
+
+/* DGEMV with transposition: z <- alpha op(A) x + beta y, A m x n in `layout`,
+ * op(A) = A (trans = BTO_NO_TRANS; x: n, y and z: m) or A^T (BTO_TRANS; x: m,
+ * y and z: n).  z == y allowed.  An empty product gives z = beta y. */
+bto_status bto_dgemv_layout(int layout, int trans, int64_t m, int64_t n, double alpha,
+                            const double *A, int64_t lda, const double *x, double beta,
+                            const double *y, double *z, void *ws, size_t ws_bytes,
+                            bto_stream_t stream);
+
+/* DGEMVT: x <- beta A^T y + z ; w <- alpha A x (A m x n in `layout`). */
+bto_status bto_dgemvt_layout(int layout, int64_t m, int64_t n, double alpha, double beta,
+                             const double *A, int64_t lda, const double *y, const double *z,
+                             double *x, double *w, void *ws, size_t ws_bytes,
+                             bto_stream_t stream);
+
 /* --------------------------------------------------------- schedule overrides
  * The FP64 matrix kernels (BICGK, ATAX's two-pass forms, GEMVER, GESUMMV,
  * DGEMV, DGEMVT; op < BTO_OP_AXPYDOT) split A into row blocks x column panels

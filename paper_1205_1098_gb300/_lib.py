@@ -49,6 +49,12 @@ SIGNATURES = {
     "bto_batch_submit": "kpkpzpzs",
     "bto_schedule_set": "kkkk",
     "bto_bicgk_mrhs": "iiipipipipipipzs",
+    "bto_bicgk_layout": "kiipipppppzs",
+    "bto_atax_layout": "kiidpipppzs",
+    "bto_gemver_layout": "kiiddpipppppppipppzs",
+    "bto_gesummv_layout": "kiidpidpipppzs",
+    "bto_dgemv_layout": "kkiidpipdpppzs",
+    "bto_dgemvt_layout": "kiiddpipppppzs",
 }
 _KIND = {"i": _c_i64, "u": _c_u64, "d": _c_f64, "f": ctypes.c_float, "p": _c_ptr, "z": _c_size,
          "s": _c_ptr, "k": _c_int}
@@ -57,6 +63,8 @@ BTO_OK, BTO_ERR_INVALID_VALUE, BTO_ERR_UNSUPPORTED, BTO_ERR_WORKSPACE = 0, 1, 2,
 BTO_ERR_CUDA, BTO_ERR_TIMEOUT, BTO_ERR_BUDGET = 4, 5, 6
 BTO_F64, BTO_F32, BTO_BF16 = 0, 1, 2
 BTO_FORM_FUSED, BTO_FORM_UNFUSED = 0, 1
+BTO_COL_MAJOR, BTO_ROW_MAJOR = 0, 1
+BTO_NO_TRANS, BTO_TRANS = 0, 1
 OPS = {"bicgk": 0, "atax": 1, "gemver": 2, "gesummv": 3, "dgemv": 4, "dgemvt": 5,
        "axpydot": 6, "waxpby": 7, "vadd": 8}
 
@@ -180,6 +188,20 @@ def bto_workspace_bytes(op, form, m, n, a_type=BTO_F64):
     return out.value
 
 
+def bto_layout_workspace_bytes(op, layout, trans, m, n):
+    """Workspace bytes of the bto_*_layout entry points (op: a bto_op value or a name)."""
+    if isinstance(op, str):
+        op = OPS[op]
+    out = _c_size(0)
+    L = lib()
+    L.bto_layout_workspace_bytes.argtypes = [_c_int, _c_int, _c_int, _c_i64, _c_i64, ctypes.POINTER(_c_size)]
+    L.bto_layout_workspace_bytes.restype = _c_int
+    st = L.bto_layout_workspace_bytes(int(op), int(layout), int(trans), int(m), int(n), ctypes.byref(out))
+    if st != BTO_OK:
+        raise BtoError("bto_layout_workspace_bytes", st, L.bto_last_invalid_arg())
+    return out.value
+
+
 def bto_bicgk_mrhs_workspace_bytes(m, n, k):
     """Workspace bytes of bto_bicgk_mrhs for an m x n A and k right-hand sides."""
     out = _c_size(0)
@@ -280,4 +302,4 @@ def exported_symbols():
     return sorted(list(SIGNATURES) + ["bto_version", "bto_status_string", "bto_last_invalid_arg",
                                       "bto_workspace_bytes", "bto_device_status",
                                       "bto_bicgk_mrhs_workspace_bytes", "bto_batch_workspace_bytes",
-                                      "bto_serve_run", "bto_schedule_get"])
+                                      "bto_serve_run", "bto_schedule_get", "bto_layout_workspace_bytes"])

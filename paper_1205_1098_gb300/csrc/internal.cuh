@@ -50,7 +50,11 @@ inline bto_status launch_status() {
 // The matrix is cut into NR row blocks x NC column panels; tile (rb, cb)
 // leaves row-vector partials in qpart[cb][.] and column-vector partials in
 // spart[rb][.]; a combine kernel adds them in a fixed order.
-enum PanelMode { PM_QS = 0, PM_Q = 1, PM_S = 2, PM_G1 = 3, PM_Q2 = 4 };
+// PM_G1 forms B = A + u1 v1^T + u2 v2^T with s = B^T r (GEMVER's first pass
+// on column-major storage); PM_G1Q forms the same B with q = B p instead (the
+// first pass on row-major storage, where the transposed product of the
+// statement becomes the non-transposed product of the stored matrix).
+enum PanelMode { PM_QS = 0, PM_Q = 1, PM_S = 2, PM_G1 = 3, PM_Q2 = 4, PM_G1Q = 5 };
 
 struct PanelPlan {
     int NR = 0, NC = 0;
@@ -68,10 +72,11 @@ struct PanelArgs {
     int64_t m, n;
     const double* A; int64_t lda;
     const double* B; int64_t ldb;    // second input matrix (PM_Q2)
-    double* Bout;                    // output matrix (PM_G1), may equal A
-    const double* p;                 // column-indexed vector (PM_QS, PM_Q, PM_Q2)
+    double* Bout;                    // output matrix (PM_G1, PM_G1Q), may equal A
+    const double* p;                 // column-indexed vector (PM_QS, PM_Q, PM_Q2, PM_G1Q)
     const double* r;                 // row-indexed vector (PM_QS, PM_S, PM_G1: y)
-    const double* u1; const double* v1; const double* u2; const double* v2;   // PM_G1
+    // PM_G1, PM_G1Q: u1, u2 row-indexed, v1, v2 column-indexed.
+    const double* u1; const double* v1; const double* u2; const double* v2;
     double* qpart; double* qpart2; double* spart;
     int64_t ldq, lds;
     int NR, NC; int64_t ntiles; int reverse;

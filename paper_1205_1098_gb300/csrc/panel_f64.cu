@@ -187,8 +187,9 @@ struct ColsAhead { static constexpr int value = (MODE == PM_Q || MODE == PM_S) ?
 
 template <int MODE, int VEC>
 __global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kernel(const PanelArgs a) {
-    constexpr bool HAS_Q = (MODE == PM_QS || MODE == PM_Q || MODE == PM_Q2);
+    constexpr bool HAS_Q = (MODE == PM_QS || MODE == PM_Q || MODE == PM_Q2 || MODE == PM_G1Q);
     constexpr bool HAS_S = (MODE == PM_QS || MODE == PM_S || MODE == PM_G1);
+    constexpr bool GEN = (MODE == PM_G1 || MODE == PM_G1Q);   // forms and stores B
     extern __shared__ double sw[];   // [kWarps][TCmax] per-warp column sums
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t tcmax = (a.n + a.NC - 1) / a.NC;
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kern
         for (int64_t R0 = r0; R0 < r1; R0 += kChunk) {
             double rv[kRPT], qacc[kRPT], qacc2[kRPT], u1r[kRPT], u2r[kRPT];
             if (HAS_S) load_vec_rows<VEC>(a.r, R0, r1, warp, lane, rv);
-            if (MODE == PM_G1) {
+            if (GEN) {
                 load_vec_rows<VEC>(a.u1, R0, r1, warp, lane, u1r);
                 load_vec_rows<VEC>(a.u2, R0, r1, warp, lane, u2r);
             }
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kern
                         const int jj = jb + u;
                         if (jj < nc) {
                             const int64_t j = g0 + jj;
-                            if (MODE == PM_G1) {
+                            if (GEN) {
                                 load_col_rw<VEC>(a.A + j * a.lda, R0, r1, warp, lane, av[u]);
                                 v1j[u] = __ldg(a.v1 + j);
                                 v2j[u] = __ldg(a.v2 + j);
@@ -304,16 +305,21 @@ __global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kern
                         const int jj = jb + u;
                         if (jj < nc) {
                             const int64_t j = g0 + jj;
-                            if (MODE == PM_G1) {
+                            if (GEN) {
                                 double b[kRPT];
 #pragma unroll
                                 for (int k = 0; k < kRPT; k++)
                                     b[k] = fma(u2r[k], v2j[u], fma(u1r[k], v1j[u], av[u][k]));
                                 store_col<VEC>(a.Bout + j * a.ldb, R0, r1, warp, lane, b);
-                                double acc = b[0] * rv[0];
+                                if (MODE == PM_G1) {
+                                    double acc = b[0] * rv[0];
 #pragma unroll
-                                for (int k = 1; k < kRPT; k++) acc = fma(b[k], rv[k], acc);
-                                sl[jj] = acc;
+                                    for (int k = 1; k < kRPT; k++) acc = fma(b[k], rv[k], acc);
+                                    sl[jj] = acc;
+                                } else {
+#pragma unroll
+                                    for (int k = 0; k < kRPT; k++) qacc[k] = fma(b[k], pj[u], qacc[k]);
+                                }
                             } else {
                                 if (HAS_Q) {
 #pragma unroll
@@ -499,13 +505,14 @@ bto_status launch_panel(int mode, const PanelArgs& a, const PanelPlan& pl, cudaS
     // even leading dimension (rows pair up from even offsets).
     bool vec2 = aligned16(a.A) && (a.lda % 2 == 0);
     if (mode == PM_Q2) vec2 = vec2 && aligned16(a.B) && (a.ldb % 2 == 0);
-    if (mode == PM_G1) vec2 = vec2 && aligned16(a.Bout) && (a.ldb % 2 == 0);
+    if (mode == PM_G1 || mode == PM_G1Q) vec2 = vec2 && aligned16(a.Bout) && (a.ldb % 2 == 0);
     switch (mode) {
         case PM_QS: return launch_mode<PM_QS>(a, pl, vec2, st);
         case PM_Q: return launch_mode<PM_Q>(a, pl, vec2, st);
         case PM_S: return launch_mode<PM_S>(a, pl, vec2, st);
         case PM_G1: return launch_mode<PM_G1>(a, pl, vec2, st);
         case PM_Q2: return launch_mode<PM_Q2>(a, pl, vec2, st);
+        case PM_G1Q: return launch_mode<PM_G1Q>(a, pl, vec2, st);
     }
     return BTO_ERR_INVALID_VALUE;
 }

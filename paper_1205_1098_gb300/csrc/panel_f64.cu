@@ -179,7 +179,8 @@ __device__ __host__ __forceinline__ int64_t row_split_at(int64_t m, int64_t part
 // latency than loads issued early.  The q-only mode has its own loop (two
 // buffers of two columns taking turns); three or four blocks per SM were
 // slower for it.  The same loop for the s-only mode measured no faster than
-// its four-column bursts.
+// its four-column bursts; what raised that mode (77% -> 88% of the FP64
+// peak) was walking column groups outside the row chunks (below).
 template <int MODE>
 struct BlocksPerSM { static constexpr int value = 2; };
 template <int MODE>
@@ -190,6 +191,7 @@ __global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kern
     constexpr bool HAS_Q = (MODE == PM_QS || MODE == PM_Q || MODE == PM_Q2 || MODE == PM_G1Q);
     constexpr bool HAS_S = (MODE == PM_QS || MODE == PM_S || MODE == PM_G1);
     constexpr bool GEN = (MODE == PM_G1 || MODE == PM_G1Q);   // forms and stores B
+    constexpr bool COLS_OUTER = (MODE == PM_S);   // column sums alone (see below)
     extern __shared__ double sw[];   // [kWarps][TCmax] per-warp column sums
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t tcmax = (a.n + a.NC - 1) / a.NC;
@@ -206,6 +208,42 @@ __global__ void __launch_bounds__(kThreads, BlocksPerSM<MODE>::value) panel_kern
             __syncthreads();
         }
 
+        if (COLS_OUTER) {
+            // Column groups outside the row chunks: each column's sum runs on
+            // through every chunk of the row block, so the transposing
+            // butterfly (one FP64 add per column and lane) runs once per group
+            // and row block instead of once per chunk.  (GEMVER's first pass,
+            // also column sums only, keeps the chunk-outer order: this one
+            // would spill there.)
+            for (int64_t g0 = c0; g0 < c1; g0 += kGroup) {
+                const int nc = (int)((c1 - g0) < kGroup ? (c1 - g0) : kGroup);
+                double sl[kGroup];
+#pragma unroll
+                for (int jj = 0; jj < kGroup; jj++) sl[jj] = 0.0;
+#pragma unroll 1
+                for (int64_t R0 = r0; R0 < r1; R0 += kChunk) {
+                    double rv[kRPT];
+                    load_vec_rows<VEC>(a.r, R0, r1, warp, lane, rv);
+                    constexpr int KU = ColsAhead<MODE>::value;
+#pragma unroll
+                    for (int jb = 0; jb < kGroup; jb += KU) {
+                        // Issue the loads of KU columns before consuming any of them.
+                        double av[KU][kRPT];
+#pragma unroll
+                        for (int u = 0; u < KU; u++)
+                            if (jb + u < nc) load_col<VEC>(a.A + (g0 + jb + u) * a.lda, R0, r1, warp, lane, av[u]);
+#pragma unroll
+                        for (int u = 0; u < KU; u++)
+                            if (jb + u < nc) {
+#pragma unroll
+                                for (int k = 0; k < kRPT; k++) sl[jb + u] = fma(av[u][k], rv[k], sl[jb + u]);
+                            }
+                    }
+                }
+                const double cs = transpose_reduce16(sl, lane);
+                if (lane < nc) sw[warp * tcmax + (g0 - c0) + lane] += cs;
+            }
+        } else
         for (int64_t R0 = r0; R0 < r1; R0 += kChunk) {
             double rv[kRPT], qacc[kRPT], qacc2[kRPT], u1r[kRPT], u2r[kRPT];
             if (HAS_S) load_vec_rows<VEC>(a.r, R0, r1, warp, lane, rv);

@@ -636,6 +636,78 @@ def layout_form(torch, bto, fp64_peak, n=N_MAT, reps=7, seed=1):
     return out
 
 
+GEN_SPECS = {
+    "bicgk": ("in: A : matrix, p r : vector\nout: q s : vector\nq = A * p\ns = A' * r", 4),
+    "gemver": ("in: A : matrix, u1 v1 u2 v2 y z : vector, alpha beta : scalar\nout: B : matrix, x w : vector\n"
+               "B = A + u1 * v1' + u2 * v2'\nx = beta * B' * y + z\nw = alpha * B * x", 8),
+    "batax_row": ("in: x : vector, beta : scalar, A : matrix(row)\nout: y : vector\n"
+                  "y = beta * A' * (A * x)", 4),
+    "chain": ("in: A C : matrix, p r : vector\nout: q s v : vector\nq = A * p\ns = A' * r\nv = C * q + 2 * s", 6),
+}
+
+
+def generator_form(torch, bto, fp64_peak, n=N_MAT, reps=7, seed=1):
+    """Sequences planned by the generator (f3) from their statement form, timed
+    as one native program call each at n x n (median of `reps` after 2
+    warm-ups), beside the hand-written entry point where there is one.  FLOPs:
+    2 per matrix element per product, 4 for GEMVER's update."""
+    from paper_1205_1098_gb300 import generator as G
+    f64 = dict(dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def time(call):
+        for _ in range(2):
+            call()
+        evs = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            call()
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in evs]))
+
+    out = {}
+    for name, (text, fl) in GEN_SPECS.items():
+        P = G.compile(text)
+        shapes = {k: (n, n) for k, d in P.decls.items() if d[0] == "matrix" and d[2] == "in"}
+        bind, aid = {}, 0
+        for k, d in sorted(P.decls.items()):
+            aid += 1
+            if d[0] == "scalar":
+                bind[k] = 1.25
+            elif d[0] == "matrix":
+                bind[k] = torch.empty(n * n, **f64)
+                if d[2] == "in":
+                    bto.bto_fill_f64(seed, aid, 0, n, n, 0, bind[k], n, None)
+            else:
+                bind[k] = torch.empty(n, **f64)
+                bto.bto_fill_f64(seed, aid, 0, n, 1, 0, bind[k], n, None)
+        prog, keep = P.program(bind, shapes)
+        nb = bto.bto_program_workspace_bytes(prog)
+        ws = torch.empty(max(nb, 1), dtype=torch.uint8, device="cuda")
+        ms = time(lambda: bto.bto_program_run(prog, ws, nb, None))
+        tf = fl * n * n / ms / 1e9
+        row = {"passes": [s["mode"] for s in P.passes], "ms": round(ms, 4), "fp64_tflops": round(tf, 4),
+               "fp64_frac": round(tf / fp64_peak, 3)}
+        if name in ("bicgk", "gemver"):
+            hnb = bto.bto_workspace_bytes(name, 0, n, n)
+            hws = torch.empty(hnb, dtype=torch.uint8, device="cuda")
+            b = bind
+            if name == "bicgk":
+                call = lambda: bto.bto_bicgk(n, n, b["A"], n, b["p"], b["r"], b["q"], b["s"], hws, hnb)
+            else:
+                call = lambda: bto.bto_gemver(n, n, 1.25, 1.25, b["A"], n, b["u1"], b["v1"], b["u2"], b["v2"],
+                                              b["y"], b["z"], b["B"], n, b["x"], b["w"], hws, hnb)
+            row["hand_written_ms"] = round(time(call), 4)
+            del hws
+        out[name] = row
+        del bind, keep, ws, prog
+        torch.cuda.empty_cache()
+    return out
+
+
 def mrhs_form(torch, bto, hbm, steps, n=8192, k=64, seed=6):
     """Multi-right-hand-side BICGK: Q = A P, S = A^T R with A n x n BF16 and
     k BF16 right-hand sides, FP32 Q and S, on the tensor cores.  Each timed
@@ -808,6 +880,8 @@ def main():
     ap.add_argument("--no-mrhs", action="store_true")
     ap.add_argument("--no-layout", action="store_true", help="skip the row-major / transposed forms")
     ap.add_argument("--layout-only", action="store_true", help="only the row-major / transposed forms")
+    ap.add_argument("--no-generator", action="store_true", help="skip the generated sequences")
+    ap.add_argument("--generator-only", action="store_true", help="only the generated sequences")
     ap.add_argument("--precision-only", type=int, default=0,
                     help="profiling runs: only the reduced-precision form at this n")
     ap.add_argument("--n", type=int, default=N_MAT, help="matrix size (profiling runs)")
@@ -842,6 +916,16 @@ def main():
         hbm, _, _ = load_peaks()
         print(json.dumps({"mrhs": mrhs_form(torch, bto, hbm, args.steps, n=args.n if args.n != N_MAT else 8192,
                                             k=args.mrhs_only)}))
+        return
+    if args.generator_only:
+        import torch
+        from paper_1205_1098_gb300 import build
+        build.build()
+        import paper_1205_1098_gb300 as bto
+        _, sm_max, _ = load_peaks()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak = FP64_FLOP_PER_CLK_PER_SM * sms * sm_max * 1e6 / 1e12
+        print(json.dumps({"generator": generator_form(torch, bto, peak, n=args.n)}))
         return
     if args.layout_only:
         import torch
@@ -975,6 +1059,10 @@ def main():
     if not args.no_layout and not args.only:
         torch.cuda.empty_cache()
         layout = layout_form(torch, bto, fp64_peak, n=m)
+    gen = None
+    if not args.no_generator and not args.only:
+        torch.cuda.empty_cache()
+        gen = generator_form(torch, bto, fp64_peak, n=m)
     search = None
     if not args.no_search and not args.only:
         torch.cuda.empty_cache()
@@ -1007,6 +1095,7 @@ def main():
             "gemver_n2048": small,
             "schedule_search": search,
             "layout_n16384": layout,
+            "generator_n16384": gen,
             "peaks": {"hbm_gbs": hbm, "hbm_source": peak_src, "fp64_tflops": round(fp64_peak, 4)},
         }))
     if dist:

@@ -235,6 +235,106 @@ bto_status bto_dgemvt_layout(int layout, int64_t m, int64_t n, double alpha, dou
                              double *x, double *w, void *ws, size_t ws_bytes,
                              bto_stream_t stream);
 
+/* ------------------------------------------------------------ pass programs
+ * A program is a list of instructions over the FP64 panel engine, which a
+ * generator (paper_1205_1098_gb300.generator) produces from a short
+ * description of a BLAS-1/2 sequence, the way the paper's compiler turns its
+ * input (Section II, Fig. 1) into fused loop nests: each PASS instruction
+ * reads one column-major matrix (two for BTO_PASS_Q2) once and forms up to
+ * two products of it, leaving per-tile partial sums in numbered slots; each
+ * COMBINE adds the partial sums of one or two slots in a fixed order and
+ * scales them (plus a scaled vector); WAXPBY forms a x + b y.
+ *
+ * PASS over the stored m x n matrix A (lda >= max(1, m)), tiles in reverse
+ * order if `reverse`:
+ *   BTO_PASS_QS   slot_q <- A p (length m), slot_s <- A^T r (length n)
+ *   BTO_PASS_Q    slot_q <- A p
+ *   BTO_PASS_S    slot_s <- A^T r
+ *   BTO_PASS_G1   Bout <- A + u1 v1^T + u2 v2^T (u length m, v length n;
+ *                 ldbo; Bout == A with ldbo == lda allowed),
+ *                 slot_s <- Bout^T r
+ *   BTO_PASS_Q2   slot_q <- A p, slot_q2 <- B p (B m x n, ldb)
+ *   BTO_PASS_G1Q  Bout as for G1, slot_q <- Bout p
+ * COMBINE: out[0..n) <- a1 * (sum of slot src1) + a2 * (sum of slot src2)
+ *   + b * x, where src2 = -1 and x = NULL drop their terms, src1 = -1 gives
+ *   0 for its term; a slot's length must equal n; x may equal out.
+ * WAXPBY: out[0..n) <- a1 * x + b * y; out must not overlap x or y.
+ * Slots are numbered 0..BTO_PROGRAM_MAX_SLOTS-1; each is written by one PASS
+ * and read only by later COMBINEs.  Vectors must not overlap the matrix a
+ * PASS writes.  Sums run in a fixed order, so a program gives the same bits
+ * on every run. */
+#define BTO_INSTR_PASS 0
+#define BTO_INSTR_COMBINE 1
+#define BTO_INSTR_WAXPBY 2
+#define BTO_PASS_QS 0
+#define BTO_PASS_Q 1
+#define BTO_PASS_S 2
+#define BTO_PASS_G1 3
+#define BTO_PASS_Q2 4
+#define BTO_PASS_G1Q 5
+#define BTO_PROGRAM_MAX_SLOTS 64
+#define BTO_PROGRAM_MAX_INSTRS 4096
+
+typedef struct bto_instr {
+    int32_t op;            /* BTO_INSTR_*                                        */
+    int32_t mode;          /* PASS: BTO_PASS_*                                   */
+    int32_t reverse;       /* PASS: nonzero = tiles in reverse order             */
+    int32_t slot_q;        /* PASS: slot of A p (or Bout p), -1 if none          */
+    int32_t slot_q2;       /* PASS: slot of B p (BTO_PASS_Q2), -1 if none        */
+    int32_t slot_s;        /* PASS: slot of A^T r (or Bout^T r), -1 if none      */
+    int32_t src1, src2;    /* COMBINE: slots read, -1 if none                    */
+    int64_t m, n;          /* PASS: matrix rows, columns; COMBINE/WAXPBY: n = length */
+    const double *A; int64_t lda;
+    const double *B; int64_t ldb;
+    double *Bout; int64_t ldbo;
+    const double *p, *r;   /* PASS: length n (column-indexed), length m (row-indexed) */
+    const double *u1, *v1, *u2, *v2;
+    double *out;           /* COMBINE, WAXPBY                                    */
+    const double *x, *y;   /* COMBINE: x; WAXPBY: x and y                        */
+    double a1, a2, b;
+} bto_instr;
+
+/* Structural check of a program (no device access): on an invalid
+ * instruction returns BTO_ERR_INVALID_VALUE and writes its index to
+ * *bad_index (-1 when the count itself is invalid). */
+bto_status bto_program_check(const bto_instr *prog, int count, int *bad_index);
+
+/* Workspace bytes for the slots of a program on the current device. */
+bto_status bto_program_workspace_bytes(const bto_instr *prog, int count, size_t *bytes);
+
+/* Checks the program, then enqueues its kernels on `stream` in order (no
+ * host synchronisation; a program may be recorded into a CUDA graph). */
+bto_status bto_program_run(const bto_instr *prog, int count, void *ws, size_t ws_bytes,
+                           bto_stream_t stream);
+
+/* ------------------------------------------------------------ sparse (CSR)
+ * BICGK and BATAX on a sparse matrix in compressed sparse row form, one of
+ * the matrix formats the paper plans as future work (Section VII).  A is
+ * m x n with nnz stored entries: row_ptr has m + 1 int64 entries
+ * (nondecreasing, row_ptr[0] = 0, row_ptr[m] = nnz), col and val nnz entries
+ * (int32 column indices in [0, n), FP64 values; duplicates are summed, order
+ * within a row is free).  One sweep over the stored entries: each row's
+ * products are summed in a fixed order by a group of lanes (bitwise
+ * reproducible), the transposed product is scattered with FP64 atomic adds
+ * (reproducible to rounding only).  BATAX forms t_i = A(i,:) x inside the
+ * group and scatters beta A(i,:)^T t_i from the same entries, so A is read
+ * once and t is never stored.  n <= 2^31 - 1.
+ * ws: at least 256 bytes, 256-byte aligned; its first word is the device
+ * status (bto_device_status): BTO_ERR_INVALID_VALUE if a row pointer lay
+ * outside [0, nnz] or decreased, or a column index outside [0, n) (those
+ * entries are skipped, never dereferenced). */
+#define BTO_CSR_WORKSPACE_BYTES 256
+
+/* q <- A p (q: m) ; s <- A^T r (s: n); p: n, r: m. */
+bto_status bto_csr_bicgk(int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                         const double *val, const double *p, const double *r, double *q, double *s,
+                         void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* y <- beta A^T (A x); x: n, y: n. */
+bto_status bto_csr_atax(int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                        const double *val, double beta, const double *x, double *y, void *ws,
+                        size_t ws_bytes, bto_stream_t stream);
+
 /* --------------------------------------------------------- schedule overrides
  * The FP64 matrix kernels (BICGK, ATAX's two-pass forms, GEMVER, GESUMMV,
  * DGEMV, DGEMVT; op < BTO_OP_AXPYDOT) split A into row blocks x column panels

@@ -45,13 +45,15 @@ def _bind(L):
         "oracle_dot2": [i, _D, _D],
         "oracle_bicgk_mrhs": [i, i, i, _D, i, _D, i, _D, i, _D, i, _D, i],
         "oracle_row_dot": [i, _D, _D],
+        "oracle_csr_bicgk": [i, i, ctypes.c_void_p, ctypes.c_void_p, _D, _D, _D, _D, _D],
+        "oracle_csr_atax": [i, i, d, ctypes.c_void_p, ctypes.c_void_p, _D, _D, _D],
     }
     for name, args in sig.items():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = ctypes.c_int if name in (
             "oracle_atax", "oracle_gemver", "oracle_gesummv", "oracle_dgemv",
-            "oracle_dgemvt") else (ctypes.c_double if name in ("oracle_dot2", "oracle_row_dot") else None)
+            "oracle_dgemvt", "oracle_csr_atax") else (ctypes.c_double if name in ("oracle_dot2", "oracle_row_dot") else None)
     return L
 
 
@@ -83,6 +85,35 @@ def _mat(A, m):
 def _chk(rc):
     if rc != 0:
         raise MemoryError("oracle allocation failed")
+
+
+def _csr(row_ptr, col, val):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    v = np.ascontiguousarray(val, dtype=np.float64)
+    return rp, ci, v
+
+
+def csr_bicgk(m, n, row_ptr, col, val, p, r, L=None):
+    """Sparse BICGK on CSR arrays (row_ptr int64, col int32, val FP64)."""
+    L = L or lib()
+    rp, ci, v = _csr(row_ptr, col, val)
+    p, r = _vec(p), _vec(r)
+    q, s = np.empty(m), np.empty(n)
+    L.oracle_csr_bicgk(m, n, rp.ctypes.data, ci.ctypes.data if ci.size else None, _p(v), _p(p), _p(r),
+                       _p(q), _p(s))
+    return q, s
+
+
+def csr_atax(m, n, beta, row_ptr, col, val, x, L=None):
+    """Sparse BATAX on CSR arrays."""
+    L = L or lib()
+    rp, ci, v = _csr(row_ptr, col, val)
+    x = _vec(x)
+    y = np.empty(n)
+    _chk(L.oracle_csr_atax(m, n, beta, rp.ctypes.data, ci.ctypes.data if ci.size else None, _p(v), _p(x),
+                           _p(y)))
+    return y
 
 
 def bicgk(m, n, A, p, r, L=None):

@@ -259,3 +259,42 @@ double oracle_row_dot(int64_t n, const double *row, const double *p)
         acc += row[j] * p[j];
     return acc;
 }
+
+/* Sparse BICGK on compressed sparse rows (the sparse format the paper plans
+ * in Section VII): q_i = sum over the stored entries k of row i of
+ * val[k] p[col[k]], taken in storage order; s_j = sum over every stored
+ * entry in column j of val[k] r_i, taken in row order then storage order.
+ * Duplicated (row, column) entries add. */
+void oracle_csr_bicgk(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                      const double *val, const double *p, const double *r, double *q, double *s)
+{
+    for (int64_t j = 0; j < n; j++) s[j] = 0.0;
+    for (int64_t i = 0; i < m; i++) {
+        double acc = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) {
+            acc += val[k] * p[col[k]];
+            s[col[k]] += val[k] * r[i];
+        }
+        q[i] = acc;
+    }
+}
+
+/* Sparse BATAX: t = A x (row by row), then y = beta A^T t, as the dense
+ * oracle_atax orders it. */
+int oracle_csr_atax(int64_t m, int64_t n, double beta, const int64_t *row_ptr, const int32_t *col,
+                    const double *val, const double *x, double *y)
+{
+    double *t = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+    if (!t) return 1;
+    for (int64_t i = 0; i < m; i++) {
+        double acc = 0.0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) acc += val[k] * x[col[k]];
+        t[i] = acc;
+    }
+    for (int64_t j = 0; j < n; j++) y[j] = 0.0;
+    for (int64_t i = 0; i < m; i++)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) y[col[k]] += val[k] * t[i];
+    for (int64_t j = 0; j < n; j++) y[j] *= beta;
+    free(t);
+    return 0;
+}

@@ -55,6 +55,8 @@ SIGNATURES = {
     "bto_gesummv_layout": "kiidpidpipppzs",
     "bto_dgemv_layout": "kkiidpipdpppzs",
     "bto_dgemvt_layout": "kiiddpipppppzs",
+    "bto_csr_bicgk": "iiippppppppzs",
+    "bto_csr_atax": "iiipppdpppzs",
 }
 _KIND = {"i": _c_i64, "u": _c_u64, "d": _c_f64, "f": ctypes.c_float, "p": _c_ptr, "z": _c_size,
          "s": _c_ptr, "k": _c_int}
@@ -202,6 +204,58 @@ def bto_layout_workspace_bytes(op, layout, trans, m, n):
     return out.value
 
 
+class Instr(ctypes.Structure):
+    """bto_instr of include/bto.h (one instruction of a pass program)."""
+    _fields_ = [("op", ctypes.c_int32), ("mode", ctypes.c_int32), ("reverse", ctypes.c_int32),
+                ("slot_q", ctypes.c_int32), ("slot_q2", ctypes.c_int32), ("slot_s", ctypes.c_int32),
+                ("src1", ctypes.c_int32), ("src2", ctypes.c_int32),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("Bout", ctypes.c_void_p), ("ldbo", ctypes.c_int64),
+                ("p", ctypes.c_void_p), ("r", ctypes.c_void_p),
+                ("u1", ctypes.c_void_p), ("v1", ctypes.c_void_p), ("u2", ctypes.c_void_p), ("v2", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("a1", ctypes.c_double), ("a2", ctypes.c_double), ("b", ctypes.c_double)]
+
+
+BTO_INSTR_PASS, BTO_INSTR_COMBINE, BTO_INSTR_WAXPBY = 0, 1, 2
+BTO_PASS_QS, BTO_PASS_Q, BTO_PASS_S, BTO_PASS_G1, BTO_PASS_Q2, BTO_PASS_G1Q = 0, 1, 2, 3, 4, 5
+BTO_PROGRAM_MAX_SLOTS, BTO_PROGRAM_MAX_INSTRS = 64, 4096
+
+
+def _program_fn(name, argtypes):
+    f = getattr(lib(), name)
+    f.argtypes = argtypes
+    f.restype = _c_int
+    return f
+
+
+def bto_program_check(prog):
+    """(status, bad_index) of the structural check of a ctypes Instr array."""
+    bad = _c_int(-1)
+    f = _program_fn("bto_program_check", [_c_ptr, _c_int, ctypes.POINTER(_c_int)])
+    st = f(ctypes.addressof(prog) if len(prog) else None, len(prog), ctypes.byref(bad))
+    return st, bad.value
+
+
+def bto_program_workspace_bytes(prog):
+    out = _c_size(0)
+    f = _program_fn("bto_program_workspace_bytes", [_c_ptr, _c_int, ctypes.POINTER(_c_size)])
+    st = f(ctypes.addressof(prog) if len(prog) else None, len(prog), ctypes.byref(out))
+    if st != BTO_OK:
+        raise BtoError("bto_program_workspace_bytes", st, lib().bto_last_invalid_arg())
+    return out.value
+
+
+def bto_program_run(prog, ws, ws_bytes, stream=None):
+    f = _program_fn("bto_program_run", [_c_ptr, _c_int, _c_ptr, _c_size, _c_ptr])
+    st = f(ctypes.addressof(prog) if len(prog) else None, len(prog), _ptr(ws), int(ws_bytes), _stream(stream))
+    if st != BTO_OK:
+        raise BtoError("bto_program_run", st, lib().bto_last_invalid_arg())
+    return st
+
+
 def bto_bicgk_mrhs_workspace_bytes(m, n, k):
     """Workspace bytes of bto_bicgk_mrhs for an m x n A and k right-hand sides."""
     out = _c_size(0)
@@ -302,4 +356,5 @@ def exported_symbols():
     return sorted(list(SIGNATURES) + ["bto_version", "bto_status_string", "bto_last_invalid_arg",
                                       "bto_workspace_bytes", "bto_device_status",
                                       "bto_bicgk_mrhs_workspace_bytes", "bto_batch_workspace_bytes",
-                                      "bto_serve_run", "bto_schedule_get", "bto_layout_workspace_bytes"])
+                                      "bto_serve_run", "bto_schedule_get", "bto_layout_workspace_bytes",
+                                      "bto_program_check", "bto_program_workspace_bytes", "bto_program_run"])

@@ -154,3 +154,25 @@ def to_bf16_bits(a):
 def bf16_bits_to_f64(bits):
     bits = np.asarray(bits, dtype=np.uint16).astype(np.uint32) << np.uint32(16)
     return bits.view(np.float32).astype(np.float64)
+
+
+def csr(seed, aid, m, n, avg_row):
+    """A seeded m-by-n sparse matrix in compressed sparse rows.
+
+    Row i holds u64(seed, aid, i) mod (2 avg_row + 1) entries (mean avg_row;
+    none when n = 0); the entry at storage index k has column
+    u64(seed, aid + 1, k) mod n and value U[-1, 1) from (seed, aid + 2, k).
+    Columns are unsorted and may repeat within a row.  Returns (row_ptr
+    int64[m + 1], col int32[nnz], val float64[nnz])."""
+    m, n = int(m), int(n)
+    if n == 0 or m == 0:
+        lens = np.zeros(m, dtype=np.int64)
+    else:
+        lens = (u64(seed, aid, np.arange(m, dtype=np.uint64)) % np.uint64(2 * int(avg_row) + 1)).astype(np.int64)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    nnz = int(row_ptr[-1])
+    k = np.arange(nnz, dtype=np.uint64)
+    col = (u64(seed, aid + 1, k) % np.uint64(max(n, 1))).astype(np.int32) if nnz else np.zeros(0, np.int32)
+    val = values(seed, aid + 2, k) if nnz else np.zeros(0)
+    return row_ptr, col, val

@@ -126,6 +126,7 @@ def test_struct_layouts_match_header(tmp_path):
         "bto_serve_res": (_lib.ServeRes, {}),
         "bto_serve_cfg": (_lib.ServeCfg, {}),
         "bto_serve_stats": (_lib.ServeStats, {}),
+        "bto_instr": (_lib.Instr, {}),
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bto.h"', "int main(void) {"]
     for cname, (cls, rename) in structs.items():

@@ -708,6 +708,51 @@ def generator_form(torch, bto, fp64_peak, n=N_MAT, reps=7, seed=1):
     return out
 
 
+def sparse_form(torch, bto, hbm, m=1 << 20, avg=32, reps=7, seed=11):
+    """CSR BICGK and BATAX (f4) on a seeded m x m matrix with `avg` entries per
+    row on average (synth.csr: uniform row lengths 0..2 avg, uniform random
+    columns), median of `reps` calls after 2 warm-ups.  Algorithmic bytes:
+    12 per stored entry (value + int32 column), the row pointers, and each
+    vector read or written once."""
+    import synth
+    rp, col, val = synth.csr(seed, 70, m, m, avg)
+    nnz = len(col)
+    d_rp, d_col, d_val = (torch.from_numpy(a).cuda() for a in (rp, col, val))
+    f64 = dict(dtype=torch.float64, device="cuda")
+    p, r, q, s = (torch.empty(m, **f64) for _ in range(4))
+    bto.bto_fill_f64(seed, 1, 0, m, 1, 0, p, m, None)
+    bto.bto_fill_f64(seed, 2, 0, m, 1, 0, r, m, None)
+    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def time(call):
+        for _ in range(2):
+            call()
+        evs = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            call()
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in evs]))
+
+    out = {"m": m, "nnz": nnz, "avg_row": avg}
+    base = 12 * nnz + 8 * (m + 1)
+    for name, call, vec in (
+            ("bicgk", lambda: bto.bto_csr_bicgk(m, m, nnz, d_rp, d_col, d_val, p, r, q, s, ws, 256), 8 * 4 * m),
+            ("batax", lambda: bto.bto_csr_atax(m, m, nnz, d_rp, d_col, d_val, 0.75, p, q, ws, 256), 8 * 2 * m)):
+        ms = time(call)
+        gbs = (base + vec) / ms / 1e6
+        out[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3)}
+    torch.cuda.synchronize()
+    out["status"] = int(ws[:4].view(torch.int32).cpu().numpy()[0])
+    del d_rp, d_col, d_val
+    torch.cuda.empty_cache()
+    return out
+
+
 def mrhs_form(torch, bto, hbm, steps, n=8192, k=64, seed=6):
     """Multi-right-hand-side BICGK: Q = A P, S = A^T R with A n x n BF16 and
     k BF16 right-hand sides, FP32 Q and S, on the tensor cores.  Each timed
@@ -881,6 +926,8 @@ def main():
     ap.add_argument("--no-layout", action="store_true", help="skip the row-major / transposed forms")
     ap.add_argument("--layout-only", action="store_true", help="only the row-major / transposed forms")
     ap.add_argument("--no-generator", action="store_true", help="skip the generated sequences")
+    ap.add_argument("--no-sparse", action="store_true", help="skip the CSR forms")
+    ap.add_argument("--sparse-only", action="store_true", help="only the CSR forms")
     ap.add_argument("--generator-only", action="store_true", help="only the generated sequences")
     ap.add_argument("--precision-only", type=int, default=0,
                     help="profiling runs: only the reduced-precision form at this n")
@@ -916,6 +963,14 @@ def main():
         hbm, _, _ = load_peaks()
         print(json.dumps({"mrhs": mrhs_form(torch, bto, hbm, args.steps, n=args.n if args.n != N_MAT else 8192,
                                             k=args.mrhs_only)}))
+        return
+    if args.sparse_only:
+        import torch
+        from paper_1205_1098_gb300 import build
+        build.build()
+        import paper_1205_1098_gb300 as bto
+        hbm, _, _ = load_peaks()
+        print(json.dumps({"sparse": sparse_form(torch, bto, hbm)}))
         return
     if args.generator_only:
         import torch
@@ -1063,6 +1118,10 @@ def main():
     if not args.no_generator and not args.only:
         torch.cuda.empty_cache()
         gen = generator_form(torch, bto, fp64_peak, n=m)
+    sparse = None
+    if not args.no_sparse and not args.only:
+        torch.cuda.empty_cache()
+        sparse = sparse_form(torch, bto, hbm)
     search = None
     if not args.no_search and not args.only:
         torch.cuda.empty_cache()
@@ -1096,6 +1155,7 @@ def main():
             "schedule_search": search,
             "layout_n16384": layout,
             "generator_n16384": gen,
+            "csr_2e20_avg32": sparse,
             "peaks": {"hbm_gbs": hbm, "hbm_source": peak_src, "fp64_tflops": round(fp64_peak, 4)},
         }))
     if dist:

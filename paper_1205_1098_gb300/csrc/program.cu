@@ -100,7 +100,10 @@ size_t layout_slots(const bto_instr* prog, int count, const Slot* slots, int sms
     for (int i = 0; i < count; i++) {
         const bto_instr& I = prog[i];
         if (I.op != BTO_INSTR_PASS) continue;
-        const PanelPlan pl = panel_plan(I.m, I.n, sms);
+        // A pass that forms a matrix takes GEMVER's measured plan (row blocks
+        // of one chunk); the others the engine's default.
+        const bool gen = I.mode == BTO_PASS_G1 || I.mode == BTO_PASS_G1Q;
+        const PanelPlan pl = panel_plan(I.m, I.n, sms, gen ? BTO_OP_GEMVER : -1, BTO_FORM_FUSED);
         if (plans) (*plans)[i] = pl;
         const int ss[3] = {I.slot_q, I.slot_q2, I.slot_s};
         for (int k = 0; k < 3; k++) {

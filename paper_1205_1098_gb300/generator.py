@@ -41,7 +41,6 @@ assigned once, inputs never.  Matrix statements have the form
 `M = N + u * v' [+ ...]` with one or two rank-one terms.  Dot products
 (`x' * y`) are outside this generator (AXPYDOT has its own kernel).
 """
-import ctypes
 import re
 
 from . import _lib as L
@@ -351,9 +350,9 @@ class Plan:
     """A planned program: `steps` (symbolic passes, combines and WAXPBY steps)
     and `passes` (short descriptions, for inspection and tests)."""
 
-    def __init__(self, spec, steps, temps, dims, orient, decls, matrix_outs, zero_temps):
+    def __init__(self, spec, steps, temps, dims, orient, decls, matrix_outs):
         self.spec, self.steps, self.temps, self.dims = spec, steps, temps, dims
-        self.orient, self.decls, self.matrix_outs, self.zero_temps = orient, decls, matrix_outs, zero_temps
+        self.orient, self.decls, self.matrix_outs = orient, decls, matrix_outs
 
     @property
     def passes(self):
@@ -405,7 +404,7 @@ class Plan:
         return out
 
     def program(self, bindings, shapes, lds=None, device="cuda"):
-        """(ctypes Instr array, buffers kept alive, workspace bytes hint) for
+        """(ctypes Instr array, temporaries kept alive) for
         the given device buffers (torch tensors), scalars (floats) and matrix
         shapes {name: (rows, cols)} (lds: leading dimensions, default the
         stored row count)."""
@@ -578,7 +577,6 @@ def _plan(spec, stmts, orient, matrix_outs):
     decls = spec.decls
     dims = _Dims()
     temps = [s[1] for s in stmts if s[1] not in decls]
-    zero_temps = []
 
     # Rank-one coefficients other than 1 become scaled temporaries; a single
     # rank-one term gets a zero second term.
@@ -586,12 +584,11 @@ def _plan(spec, stmts, orient, matrix_outs):
     nz = [0]
 
     def zero(kind_dim):
+        """A new temporary vector of the given dimension (the caller fills it with zeros)."""
         nz[0] += 1
         z = "_z%d" % nz[0]
         temps.append(z)
-        zero_temps.append(z)
         dims.union(("len", z), kind_dim)
-        expanded.append(("vec", z, _V([])))
         return z
 
     for st in stmts:
@@ -613,7 +610,10 @@ def _plan(spec, stmts, orient, matrix_outs):
                 dims.union(("len", u), ("rows", base))
                 dims.union(("len", v), ("cols", base))
             if len(new) == 1:
-                new.append((zero(("rows", base)), zero(("cols", base))))
+                zu, zv = zero(("rows", base)), zero(("cols", base))
+                expanded.append(("vec", zu, _V([])))      # a statement with no terms: zeros
+                expanded.append(("vec", zv, _V([])))
+                new.append((zu, zv))
             expanded.append(("mat", tgt, base, new))
         else:
             expanded.append(st)
@@ -809,4 +809,4 @@ def _plan(spec, stmts, orient, matrix_outs):
                     changed = progress = True
         if not progress:
             raise SpecError("cannot schedule the remaining statements (a value is used before it is formed)")
-    return Plan(spec, steps, [t for t in dict.fromkeys(temps)], dims, orient, decls, matrix_outs, zero_temps)
+    return Plan(spec, steps, list(dict.fromkeys(temps)), dims, orient, decls, matrix_outs)

@@ -516,8 +516,16 @@ class Plan:
         return keep
 
 
-def compile(text):
-    """Parses and plans a program (see the module docstring)."""
+MAX_FUSE = {"qs": True, "q2": True, "update": True}
+
+
+def compile(text, policy=None):
+    """Parses and plans a program (see the module docstring).  `policy`
+    chooses which fusions the planner may make (all of them by default, the
+    paper's Max-Fuse starting point): "qs" pairs a non-transposed and a
+    transposed product of one matrix in a pass, "q2" pairs products of two
+    matrices on one input, "update" lets a pass that forms a matrix also form
+    a product of it."""
     spec = parse(text)
     decls = spec.decls
     norm = _Normaliser(decls)
@@ -563,7 +571,52 @@ def compile(text):
     for n, d in decls.items():
         if d[2] == "out" and n not in assigned:
             raise SpecError("output %s is never assigned" % n)
-    return _plan(spec, stmts, orient, matrix_outs)
+    return _plan(spec, stmts, orient, matrix_outs, dict(MAX_FUSE, **(policy or {})))
+
+
+def fusion_choices(text):
+    """Every distinct plan the fusion policies give for a program, as
+    [(policy, Plan)], Max-Fuse first: the legal points among which a
+    measured search (`search`) chooses, as the paper's search does."""
+    out, seen = [], set()
+    for qs in (True, False):
+        for q2 in (True, False):
+            for update in (True, False):
+                pol = {"qs": qs, "q2": q2, "update": update}
+                P = compile(text, pol)
+                key = P.describe()
+                if key not in seen:
+                    seen.add(key)
+                    out.append((pol, P))
+    return out
+
+
+def search(text, bindings, shapes, lds=None, reps=5):
+    """Measures every distinct fusion choice of a program on the current
+    device (median of `reps` calls after 2 warm-ups, CUDA events) and returns
+    {"best": policy, "best_ms": ms, "table": [(policy, passes, ms)]}."""
+    import torch
+    table = []
+    st = torch.cuda.current_stream()
+    for pol, P in fusion_choices(text):
+        prog, keep = P.program(bindings, shapes, lds)
+        nb = L.bto_program_workspace_bytes(prog)
+        ws = torch.empty(max(nb, 1), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            L.bto_program_run(prog, ws, nb, None)
+        evs = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            L.bto_program_run(prog, ws, nb, None)
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in evs)[reps // 2]
+        table.append((pol, [x["mode"] for x in P.passes], ms))
+        del ws, keep
+    best = min(table, key=lambda t: t[2])
+    return {"best": best[0], "best_ms": best[2], "table": table}
 
 
 def _prod(f):
@@ -573,7 +626,7 @@ def _prod(f):
     return v
 
 
-def _plan(spec, stmts, orient, matrix_outs):
+def _plan(spec, stmts, orient, matrix_outs, policy):
     decls = spec.decls
     dims = _Dims()
     temps = [s[1] for s in stmts if s[1] not in decls]
@@ -734,7 +787,7 @@ def _plan(spec, stmts, orient, matrix_outs):
         ready = [nd for nd in pending_nodes if nd["x"] in avail and (nd["M"] in avail or nd["M"] in forming)]
         # Updates, each with one product of the matrix it forms.
         for u in ready_upd:
-            mine = [nd for nd in ready if nd["M"] == u["out"]]
+            mine = [nd for nd in ready if nd["M"] == u["out"]] if policy["update"] else []
             s_nodes = [nd for nd in mine if nd["kind"] == "s"]
             q_nodes = [nd for nd in mine if nd["kind"] == "q"]
             (a1, b1), (a2, b2) = u["pairs"]
@@ -766,7 +819,7 @@ def _plan(spec, stmts, orient, matrix_outs):
         for M, lst in by_m.items():
             qs = [nd for nd in lst if nd["kind"] == "q"]
             ss = [nd for nd in lst if nd["kind"] == "s"]
-            while qs and ss:
+            while qs and ss and policy["qs"]:
                 nq, ns = qs.pop(0), ss.pop(0)
                 add_pass("QS", M, [("q", label(nq)), ("s", label(ns))], p=nq["x"], r=ns["x"], nq=nq, ns=ns)
                 progress = True
@@ -778,7 +831,7 @@ def _plan(spec, stmts, orient, matrix_outs):
         while singles_q:
             nq = singles_q.pop(0)
             mate = None
-            for cand in singles_q:
+            for cand in (singles_q if policy["q2"] else []):
                 if cand["x"] == nq["x"] and cand["M"] != nq["M"] and orient[cand["M"]] == orient[nq["M"]] and \
                         dims.find(("rows", cand["M"])) == dims.find(("rows", nq["M"])) and \
                         dims.find(("cols", cand["M"])) == dims.find(("cols", nq["M"])):

@@ -187,3 +187,38 @@ def test_model_reproduces_the_table_i_plans():
         for k, d in P.decls.items():
             if d[2] == "out":
                 assert np.allclose(got[k], want[k], rtol=1e-12, atol=1e-12), (name, k)
+
+
+@pytest.mark.parametrize("seed", range(0, 60, 3))
+def test_every_fusion_choice_plans_to_the_definition(seed):
+    """Each distinct plan the fusion policies give (the legal points a
+    measured search chooses among) computes the program; Max-Fuse comes
+    first and makes the fewest passes."""
+    rng = random.Random(seed)
+    text = random_program(rng)
+    m, n = 8, 5
+    nrng = np.random.default_rng(seed)
+    inputs = {"A": nrng.uniform(-1, 1, (m, n)), "B": nrng.uniform(-1, 1, (m, n)),
+              "C": nrng.uniform(-1, 1, (n, m)), "ym1": nrng.uniform(-1, 1, m), "ym2": nrng.uniform(-1, 1, m),
+              "xn1": nrng.uniform(-1, 1, n), "xn2": nrng.uniform(-1, 1, n), "a": 1.5, "b": -0.75}
+    shapes = {"A": (m, n), "B": (m, n), "C": (n, m)}
+    want = E.evaluate(text, inputs)
+    choices = G.fusion_choices(text)
+    assert choices[0][0] == G.MAX_FUSE
+    npass = [len(P.passes) for _, P in choices]
+    assert npass[0] == min(npass)
+    for pol, P in choices:
+        check_reduction_rule(P, inputs)
+        got = execute(P, inputs, shapes)
+        for k, d in P.decls.items():
+            if d[2] == "out":
+                assert np.allclose(got[k], want[k], rtol=1e-12, atol=1e-12), (pol, k)
+
+
+def test_fusion_choices_of_table_i():
+    import test_generator as T
+    modes = lambda name: [[s["mode"] for s in P.passes] for _, P in G.fusion_choices(T.SPECS[name])]
+    assert modes("bicgk") == [["QS"], ["S", "Q"]]
+    assert modes("gesummv") == [["Q2"], ["Q", "Q"]]
+    assert modes("gemver") == [["G1", "Q"], ["G1", "S", "Q"]]
+    assert modes("dgemv") == [["Q"]]

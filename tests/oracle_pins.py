@@ -9,7 +9,9 @@ test).  The pins are:
   * closed forms (all-ones and rank-1 matrices), the adjoint identity of
     BICGK, a second formula for GEMVER that never forms B, and special cases
     that reduce to an exact zero or to the input;
-  * the Dot2 error bound of Ogita, Rump and Oishi against an exact rational sum.
+  * the Dot2 error bound of Ogita, Rump and Oishi against an exact rational sum;
+  * for the sparse (CSR) definitions: a hand-worked example, integer-valued
+    inputs against exact products of the densified matrix, the identity.
 """
 from fractions import Fraction
 
@@ -287,5 +289,47 @@ def pin_mrhs_and_row_dot(L):
         assert O.row_dot(A[i], P[:, 0], L=L) == float(Ai[i] @ P[:, 0].astype(np.int64))
 
 
+# ---------------------------------------------------------------- sparse (CSR)
+def _densify(m, n, rp, col, val):
+    A = np.zeros((max(m, 1), n))
+    for i in range(m):
+        for k in range(rp[i], rp[i + 1]):
+            A[i, col[k]] += val[k]
+    return A[:m]
+
+
+def pin_csr_golden(L):
+    g, e = load("csr_bicgk_3x4.txt")
+    rp, col = g["row_ptr"].astype(np.int64), g["col"].astype(np.int32)
+    q, s = O.csr_bicgk(g["m"], g["n"], rp, col, g["val"], g["p"], g["r"], L=L)
+    assert np.array_equal(q, e["q"]) and np.array_equal(s, e["s"])
+    y = O.csr_atax(g["m"], g["n"], float(g["beta"]), rp, col, g["val"], g["p"], L=L)
+    assert np.array_equal(y, e["y"])
+
+
+def pin_csr_integer_exact(L):
+    """Integer-valued entries and vectors: every partial sum is exact, so the
+    CSR results equal exact int64 products of the densified matrix."""
+    m, n = 23, 17
+    rp, col, _ = synth.csr(3, 80, m, n, 5)
+    val = _ints(3, 90, len(col))
+    p, r = _ints(3, 91, n), _ints(3, 92, m)
+    Ai = _densify(m, n, rp, col, val).astype(np.int64)
+    q, s = O.csr_bicgk(m, n, rp, col, val, p, r, L=L)
+    assert np.array_equal(q, (Ai @ p.astype(np.int64)).astype(float))
+    assert np.array_equal(s, (Ai.T @ r.astype(np.int64)).astype(float))
+    y = O.csr_atax(m, n, 2.0, rp, col, val, p, L=L)
+    assert np.array_equal(y, (2 * (Ai.T @ (Ai @ p.astype(np.int64)))).astype(float))
+
+
+def pin_csr_identity(L):
+    n = 6
+    rp, col = np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32)
+    p, r = np.arange(1.0, n + 1), np.arange(-3.0, n - 3)
+    q, s = O.csr_bicgk(n, n, rp, col, np.ones(n), p, r, L=L)
+    assert np.array_equal(q, p) and np.array_equal(s, r)
+
+
 PINS = [pin_golden, pin_integer_exact, pin_closed_forms, pin_identities,
-        pin_vector_special, pin_ieee_and_empty, pin_dot2_bound, pin_mrhs_and_row_dot]
+        pin_vector_special, pin_ieee_and_empty, pin_dot2_bound, pin_mrhs_and_row_dot,
+        pin_csr_golden, pin_csr_integer_exact, pin_csr_identity]

@@ -7,9 +7,8 @@ hand-worked fixtures) for the Table I kernels and for sequences beyond them."""
 import numpy as np
 import pytest
 
-import golden_io
-import oracle as O
 from oracle import spec_eval as E
+from spec_pins import PINS
 from paper_1205_1098_gb300 import _lib, generator as G
 
 SPECS = {
@@ -129,70 +128,11 @@ def test_rejected_programs(text, msg):
 # ------------------------------------------------------------------ oracle pins
 
 
-def test_spec_eval_matches_c_oracle():
-    """The plain evaluator and the C oracle are independent implementations of
-    the Table I definitions: they agree to rounding."""
-    rng = np.random.default_rng(3)
-    m, n = 7, 5
-    A, B = rng.uniform(-1, 1, (m, n)), rng.uniform(-1, 1, (m, n))
-    v = {k: rng.uniform(-1, 1, ln) for k, ln in (("u1", m), ("v1", n), ("u2", m), ("v2", n), ("ym", m),
-                                                 ("zn", n), ("xn", n), ("rm", m))}
-    close = lambda a, b: np.allclose(a, b, rtol=0, atol=1e-13)
-    r = E.evaluate(SPECS["bicgk"], {"A": A, "p": v["xn"], "r": v["rm"]})
-    q, s = O.bicgk(m, n, A, v["xn"], v["rm"])
-    assert close(r["q"], q) and close(r["s"], s)
-    r = E.evaluate(SPECS["batax"], {"A": A, "x": v["xn"], "beta": 0.75})
-    assert close(r["y"], O.atax(m, n, 0.75, A, v["xn"]))
-    r = E.evaluate(SPECS["gemver"], {"A": A, "u1": v["u1"], "v1": v["v1"], "u2": v["u2"], "v2": v["v2"],
-                                     "y": v["ym"], "z": v["zn"], "alpha": 1.5, "beta": 1.2})
-    Bo, x, w = O.gemver(m, n, 1.5, 1.2, A, v["u1"], v["v1"], v["u2"], v["v2"], v["ym"], v["zn"])
-    assert close(r["B"], Bo) and close(r["x"], x) and close(r["w"], w)
-    r = E.evaluate(SPECS["gesummv"], {"A": A, "B": B, "x": v["xn"], "alpha": 1.5, "beta": -0.75})
-    assert close(r["y"], O.gesummv(m, n, 1.5, A, -0.75, B, v["xn"]))
-    r = E.evaluate(SPECS["dgemv"], {"A": A, "x": v["xn"], "y": v["ym"], "alpha": 1.5, "beta": -0.5})
-    assert close(r["z"], O.dgemv(m, n, 1.5, A, v["xn"], -0.5, v["ym"]))
-    r = E.evaluate(SPECS["dgemvt"], {"A": A, "y": v["ym"], "z": v["zn"], "alpha": 1.5, "beta": 1.2})
-    x, w = O.dgemvt(m, n, 1.5, 1.2, A, v["ym"], v["zn"])
-    assert close(r["x"], x) and close(r["w"], w)
-
-
-@pytest.mark.parametrize("fixture,spec", [
-    ("bicgk_2x3.txt", "bicgk"), ("atax_2x3.txt", "batax"), ("gemver_2x2.txt", "gemver"),
-    ("gesummv_2x2.txt", "gesummv"), ("dgemv_2x3.txt", "dgemv"), ("dgemvt_2x3.txt", "dgemvt"),
-])
-def test_spec_eval_reproduces_hand_worked_fixtures(fixture, spec):
-    inp, exp = golden_io.load(fixture)
-    m, n = inp.pop("m"), inp.pop("n")
-    vals = {}
-    for k, v in inp.items():
-        if k in ("A", "B"):
-            vals[k] = golden_io.colmajor(v, m, n)
-        else:
-            vals[k] = v
-    got = E.evaluate(SPECS[spec], vals)
-    for k, e in exp.items():
-        g = got[k]
-        g = np.asarray(g).ravel(order="F") if np.ndim(g) == 2 else np.asarray(g)
-        assert np.array_equal(g, e), (fixture, k, g, e)
-
-
-def test_spec_eval_closed_forms():
-    """Special cases with closed forms: A = I gives y = beta x for BATAX;
-    u1 = v1 = 0, u2 = v2 = 0 leaves B = A; a rank-one A = a b' gives
-    A x = a (b . x)."""
-    n = 6
-    x = np.arange(1.0, n + 1)
-    r = E.evaluate(SPECS["batax"], {"A": np.eye(n), "x": x, "beta": 2.0})
-    assert np.array_equal(r["y"], 2 * x)
-    A = np.arange(12.0).reshape(3, 4)
-    r = E.evaluate(SPECS["gemver"], {"A": A, "u1": np.zeros(3), "v1": np.zeros(4), "u2": np.zeros(3),
-                                     "v2": np.zeros(4), "y": np.ones(3), "z": np.zeros(4), "alpha": 1.0,
-                                     "beta": 1.0})
-    assert np.array_equal(r["B"], A) and np.array_equal(r["x"], A.sum(axis=0))
-    a, b = np.array([1.0, -2.0, 3.0]), np.array([2.0, 0.5, -1.0, 4.0])
-    xx = np.array([1.0, 2.0, 3.0, 4.0])
-    r = E.evaluate(SPECS["dgemv"], {"A": np.outer(a, b), "x": xx, "y": np.zeros(3), "alpha": 1.0, "beta": 0.0})
-    assert np.array_equal(r["z"], a * (b @ xx))
+@pytest.mark.parametrize("pin", PINS, ids=lambda f: f.__name__)
+def test_spec_eval_pins(pin):
+    """The plain evaluator against the C oracle, the hand-worked fixtures and
+    closed forms (tests/spec_pins.py)."""
+    pin(E)
 
 
 # ------------------------------------------------------------------ native check (CPU)

@@ -40,6 +40,15 @@ MUTANTS = [
     ("mrhs_wrong_column", "oracle_bicgk(m, n, A, lda, P + (size_t)c * (size_t)ldp, R + (size_t)c * (size_t)ldr,",
      "oracle_bicgk(m, n, A, lda, P, R + (size_t)c * (size_t)ldr,"),
     ("row_dot_sign", "acc += row[j] * p[j];", "acc -= row[j] * p[j];"),
+    ("csr_q_sign", "acc += val[k] * p[col[k]];", "acc -= val[k] * p[col[k]];"),
+    ("csr_s_wrong_row", "s[col[k]] += val[k] * r[i];", "s[col[k]] += val[k] * r[0];"),
+    ("csr_atax_dropped_beta", "for (int64_t j = 0; j < n; j++) y[j] *= beta;", ""),
+    ("csr_atax_drops_last_entry",
+     "for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) acc += val[k] * x[col[k]];",
+     "for (int64_t k = row_ptr[i]; k + 1 < row_ptr[i + 1]; k++) acc += val[k] * x[col[k]];"),
+    ("csr_atax_t_transposed",
+     "for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) y[col[k]] += val[k] * t[i];",
+     "for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) y[col[k]] += val[k] * x[col[k]];"),
 ]
 
 

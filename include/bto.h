@@ -350,6 +350,12 @@ bto_status bto_csr_atax(int64_t m, int64_t n, int64_t nnz, const int64_t *row_pt
 bto_status bto_schedule_set(int op, int form, int panels, int row_blocks);
 bto_status bto_schedule_get(int op, int form, int *panels, int *row_blocks);
 
+/* The tile plan the FP64 matrix kernels use for `op` in `form` on an m x n
+ * matrix with `sms` multiprocessors (overrides included): writes the number
+ * of row blocks and column panels.  Host only; touches no device.  ATAX's
+ * fused group-band kernel has its own plan; this is its two-pass plan. */
+bto_status bto_panel_plan(int op, int form, int64_t m, int64_t n, int sms, int *row_blocks, int *panels);
+
 /* ------------------------------------------- reduced-precision storage form
  * BICGK, GEMVER, ATAX and GESUMMV (Table I) with the matrices stored in FP32
  * or BF16 to cut the bytes of this bandwidth-bound path (the paper's kernels

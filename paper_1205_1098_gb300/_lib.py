@@ -266,6 +266,21 @@ def bto_bicgk_mrhs_workspace_bytes(m, n, k):
     return out.value
 
 
+def bto_panel_plan(op, form, m, n, sms):
+    """(row_blocks, panels) of the FP64 tile plan (host only)."""
+    if isinstance(op, str):
+        op = OPS[op]
+    a, b = _c_int(0), _c_int(0)
+    L = lib()
+    L.bto_panel_plan.argtypes = [_c_int, _c_int, _c_i64, _c_i64, _c_int, ctypes.POINTER(_c_int),
+                                 ctypes.POINTER(_c_int)]
+    L.bto_panel_plan.restype = _c_int
+    st = L.bto_panel_plan(int(op), int(form), int(m), int(n), int(sms), ctypes.byref(a), ctypes.byref(b))
+    if st != BTO_OK:
+        raise BtoError("bto_panel_plan", st, L.bto_last_invalid_arg())
+    return a.value, b.value
+
+
 def bto_schedule_get(op, form):
     """(panels, row_blocks) set for (op, form); 0 means automatic."""
     if isinstance(op, str):
@@ -357,4 +372,5 @@ def exported_symbols():
                                       "bto_workspace_bytes", "bto_device_status",
                                       "bto_bicgk_mrhs_workspace_bytes", "bto_batch_workspace_bytes",
                                       "bto_serve_run", "bto_schedule_get", "bto_layout_workspace_bytes",
-                                      "bto_program_check", "bto_program_workspace_bytes", "bto_program_run"])
+                                      "bto_program_check", "bto_program_workspace_bytes", "bto_program_run",
+                                      "bto_panel_plan"])

@@ -20,6 +20,7 @@
 // caller's device arena (the HBM budget) through a first-fit allocator with
 // coalescing; nothing is allocated on the device by the runtime.
 #include "check.cuh"
+#include "arena.h"
 #include <algorithm>
 #include <chrono>
 #include <deque>
@@ -31,52 +32,7 @@
 namespace bto {
 namespace {
 
-constexpr size_t kGranule = 256;
-
-// First-fit allocator over [0, capacity) of a device arena; free blocks are
-// kept by offset and merged with their neighbours when released.
-class Arena {
- public:
-    explicit Arena(size_t bytes) : cap_(bytes / kGranule * kGranule) {
-        if (cap_) free_[0] = cap_;
-    }
-    bool alloc(size_t bytes, size_t* off) {
-        bytes = round_up((int64_t)std::max<size_t>(bytes, 1), kGranule);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < bytes) continue;
-            *off = it->first;
-            const size_t rest = it->second - bytes, start = it->first + bytes;
-            free_.erase(it);
-            if (rest) free_[start] = rest;
-            used_ += bytes;
-            peak_ = std::max(peak_, used_);
-            return true;
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        bytes = round_up((int64_t)std::max<size_t>(bytes, 1), kGranule);
-        used_ -= bytes;
-        auto next = free_.lower_bound(off);
-        if (next != free_.end() && off + bytes == next->first) {
-            bytes += next->second;
-            next = free_.erase(next);
-        }
-        if (next != free_.begin()) {
-            auto prev = std::prev(next);
-            if (prev->first + prev->second == off) {
-                prev->second += bytes;
-                return;
-            }
-        }
-        free_[off] = bytes;
-    }
-    size_t peak() const { return peak_; }
-
- private:
-    size_t cap_, used_ = 0, peak_ = 0;
-    std::map<size_t, size_t> free_;
-};
+constexpr size_t kGranule = kArenaGranule;
 
 struct Block {
     size_t off = 0, bytes = 0;

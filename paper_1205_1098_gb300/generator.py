@@ -429,6 +429,14 @@ class Plan:
         for n, d in self.decls.items():
             if d[2] in ("in", "out") and d[0] != "scalar" and n not in buf:
                 raise SpecError("no buffer bound to %s" % n)
+            if d[0] == "scalar" and not isinstance(bindings.get(n), (int, float)):
+                raise SpecError("scalar %s needs a number" % n)
+        for n, t in bindings.items():
+            if n in self.decls and self.decls[n][0] != "scalar":
+                if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous():
+                    raise SpecError("%s must be a contiguous float64 tensor" % n)
+                if t.device.type != torch.device(device).type:
+                    raise SpecError("%s is on %s, the program runs on %s" % (n, t.device, device))
         for t in self.temps:
             buf[t] = keep[t] = torch.empty(max(vlen(t), 1), dtype=torch.float64, device=device)
         for n, d in self.decls.items():

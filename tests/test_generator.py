@@ -172,6 +172,21 @@ def test_generated_programs_pass_the_native_check(tmp_path):
         assert st == _lib.BTO_OK and bad == -1, (name, bad)
 
 
+def test_bound_buffers_are_checked():
+    import torch
+    P = G.compile(SPECS["dgemv"])
+    b = _bind(P, 40, 30, {"A": (40, 30)})
+    for name, bad in (("x", b["x"].float()), ("A", b["A"].view(40, 30).t()), ("alpha", "1.5")):
+        bb = dict(b)
+        bb[name] = bad
+        with pytest.raises(G.SpecError):
+            P.program(bb, {"A": (40, 30)}, device="cpu")
+    with pytest.raises(G.SpecError):          # a host tensor for a device program
+        P.program(b, {"A": (40, 30)}, device="cuda")
+    assert P.program(b, {"A": (40, 30)}, device="cpu")[0] is not None
+    assert torch.float64 == b["x"].dtype
+
+
 def test_inconsistent_shapes_are_rejected():
     P = G.compile(SPECS["four_products"])
     with pytest.raises(G.SpecError):

@@ -707,7 +707,7 @@ def _plan(spec, stmts, orient, matrix_outs, policy):
             terms = []
             for c, a in st[2].terms:
                 if a[0] == "mv":
-                    node = {"id": len(nodes), "M": a[1], "kind": stored_kind(a[1], a[2]), "x": a[3],
+                    node = {"id": len(nodes), "M": a[1], "tr": a[2], "kind": stored_kind(a[1], a[2]), "x": a[3],
                             "done": False, "slot": None}
                     nodes.append(node)
                     terms.append((c, ("node", node["id"])))
@@ -748,7 +748,11 @@ def _plan(spec, stmts, orient, matrix_outs, policy):
                 nd["done"] = True
 
     def label(nd):
-        return "%s%s %s" % (nd["M"], "" if nd["kind"] == "q" else "^T(stored)", nd["x"])
+        # The product as the program writes it; a pass that forms a matrix
+        # with no product of it ready sums a zero vector.
+        if nd["id"] < 0:
+            return "(no product)"
+        return "%s%s %s" % (nd["M"], "'" if nd["tr"] else "", nd["x"])
 
     def emit_combines(vs):
         out = vs["out"]

@@ -12,6 +12,10 @@
  * nest per statement of the table.  Compile with -ffp-contract=off so that
  * every multiply and add rounds on its own.
  *
+ * The CSR routines at the end define BICGK and BATAX on a matrix in
+ * compressed sparse rows (the sparse format of Section VII) as loops over the
+ * stored entries, in storage order.
+ *
  * Matrices are column-major: element (i, j) of A is A[i + j*lda].
  * Sizes m, n may be zero; empty sums are zero.  No BLAS-style shortcut is
  * taken for zero scalars: alpha*s is always evaluated, so NaN/Inf propagate.

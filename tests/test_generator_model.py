@@ -222,3 +222,24 @@ def test_fusion_choices_of_table_i():
     assert modes("gesummv") == [["Q2"], ["Q", "Q"]]
     assert modes("gemver") == [["G1", "Q"], ["G1", "S", "Q"]]
     assert modes("dgemv") == [["Q"]]
+
+
+@pytest.mark.parametrize("orient", ["matrix", "matrix(row)"])
+def test_chained_updates(orient):
+    """A formed matrix updated again: each update shares its pass with a
+    product of the matrix it forms (G1 or G1Q by storage order), and the
+    second pass reads the first one's output."""
+    text = ("chained updates\nin: A : %s, u w y : vector, v z : vector\nout: B : %s, C : %s, x s : vector\n"
+            "B = A + u * v'\nC = B + w * z' + 2 * u * z'\nx = C * z\ns = B' * y" % (orient, orient, orient))
+    P = G.compile(text)
+    modes = [p["mode"] for p in P.passes]
+    assert modes == (["G1", "G1Q"] if orient == "matrix" else ["G1Q", "G1"])
+    assert P.passes[1]["A"] == "B" and P.passes[1]["Bout"] == "C" and P.passes[1]["reverse"]
+    m, n = 6, 4
+    rng = np.random.default_rng(0)
+    inp = {"A": rng.uniform(-1, 1, (m, n)), "u": rng.uniform(-1, 1, m), "w": rng.uniform(-1, 1, m),
+           "y": rng.uniform(-1, 1, m), "v": rng.uniform(-1, 1, n), "z": rng.uniform(-1, 1, n)}
+    check_reduction_rule(P, inp)
+    got, want = execute(P, inp, {"A": (m, n)}), E.evaluate(text, inp)
+    for k in ("B", "C", "x", "s"):
+        assert np.allclose(got[k], want[k], rtol=1e-12, atol=1e-12), k

@@ -1,0 +1,113 @@
+// Double-float arithmetic: a value held as an unevaluated sum hi + lo of two
+// FP32 numbers (48 significant bits), for FP64 data on the FP32 pipe.
+//
+// Building blocks, each a published error-free transformation or a direct
+// consequence of the FP64 format:
+//   * split_f64: an FP64 number as hi + lo, from its bits with integer
+//     operations only (no FP64 instruction): hi takes the sign, the exponent
+//     and the top 23 fraction bits; lo the next 24 significant bits of the
+//     remainder, truncated.  |x - (hi + lo)| <= 2^-47 |x|.  Exact when the
+//     remainder has at most 24 significant bits (every FP32 value, every
+//     integer below 2^48).  Requires the exponent in FP32's normal range with
+//     room for a normal lo: 2^-74 <= |x| < 2^128, or x = 0 (`split_ok`).
+//   * two_sum (Knuth, TAOCP vol. 2, 4.2.2): s + e = a + b exactly.
+//   * two_prod (via FMA; Ogita, Rump and Oishi, SISC 2005): p + e = a * b
+//     exactly, unless underflow.
+//   * df_mac: acc + a * b in double-float, the product's cross terms folded
+//     into the low part and the sum renormalised with two_sum.
+// Host and device: compiled by nvcc for kernels and by a C++ compiler for the
+// CPU checks of these error bounds.
+#pragma once
+#include <cstdint>
+#include <cstring>
+#include <cmath>
+
+#if defined(__CUDACC__)
+#define DF_HD __host__ __device__ __forceinline__
+#else
+#define DF_HD inline
+#endif
+
+namespace bto {
+namespace df {
+
+struct f2 {
+    float hi, lo;
+};
+
+DF_HD uint64_t bits_of(double x) {
+    uint64_t u;
+    std::memcpy(&u, &x, sizeof u);
+    return u;
+}
+
+DF_HD float float_of(uint32_t u) {
+    float f;
+    std::memcpy(&f, &u, sizeof f);
+    return f;
+}
+
+DF_HD int clz64(uint64_t v) {
+#if defined(__CUDA_ARCH__)
+    return __clzll((long long)v);
+#else
+    return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
+// True when split_f64 represents x to 2^-47 relative (or exactly, x = 0).
+DF_HD bool split_ok(double x) {
+    const int e = (int)((bits_of(x) >> 52) & 0x7ff);     // biased FP64 exponent
+    return e == 0 ? (bits_of(x) << 1) == 0 : (e - 1023 >= -74 && e - 1023 <= 127);
+}
+
+// hi + lo from the bits of x (x finite, split_ok(x)).
+DF_HD f2 split_f64(double x) {
+    const uint64_t u = bits_of(x);
+    const uint32_t sign = (uint32_t)(u >> 63) << 31;
+    const int e = (int)((u >> 52) & 0x7ff);
+    if (e == 0) return {float_of(sign), 0.0f};
+    const int ue = e - 1023;                                  // unbiased exponent of x
+    const uint64_t frac = u & ((1ull << 52) - 1);
+    // hi: sign, exponent, top 23 fraction bits (truncated).
+    const float hi = float_of(sign | ((uint32_t)(ue + 127) << 23) | (uint32_t)(frac >> 29));
+    // Remainder: the low 29 fraction bits, worth rem * 2^(ue - 52).
+    const uint64_t rem = frac & ((1ull << 29) - 1);
+    if (rem == 0) return {hi, 0.0f};
+    const int lead = 63 - clz64(rem);                          // position of its leading one
+    const int le = ue - 52 + lead;                             // exponent of lo
+    // lo: the leading one and the next 23 bits of the remainder, truncated.
+    const uint32_t mant = lead >= 23 ? (uint32_t)(rem >> (lead - 23)) : (uint32_t)(rem << (23 - lead));
+    const float lo = float_of(sign | ((uint32_t)(le + 127) << 23) | (mant & ((1u << 23) - 1)));
+    return {hi, lo};
+}
+
+DF_HD f2 two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+DF_HD f2 fast_two_sum(float a, float b) {          // |a| >= |b|
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+DF_HD f2 two_prod(float a, float b) {
+    const float p = a * b;
+    return {p, std::fmaf(a, b, -p)};
+}
+
+// acc + a * b, with a and b double-floats.
+DF_HD f2 df_mac(f2 acc, f2 a, f2 b) {
+    const f2 p = two_prod(a.hi, b.hi);
+    const float cross = std::fmaf(a.hi, b.lo, std::fmaf(a.lo, b.hi, p.lo));
+    const f2 s = two_sum(acc.hi, p.hi);
+    return fast_two_sum(s.hi, s.lo + (acc.lo + cross));
+}
+
+DF_HD double to_f64(f2 v) { return (double)v.hi + (double)v.lo; }
+
+}  // namespace df
+}  // namespace bto

@@ -635,243 +635,281 @@ def _prod(f):
 
 
 def _plan(spec, stmts, orient, matrix_outs, policy):
-    decls = spec.decls
-    dims = _Dims()
-    temps = [s[1] for s in stmts if s[1] not in decls]
+    return _Planner(spec, stmts, orient, matrix_outs, policy).plan()
 
-    # Rank-one coefficients other than 1 become scaled temporaries; a single
-    # rank-one term gets a zero second term.
-    expanded = []
-    nz = [0]
 
-    def zero(kind_dim):
-        """A new temporary vector of the given dimension (the caller fills it with zeros)."""
-        nz[0] += 1
-        z = "_z%d" % nz[0]
-        temps.append(z)
-        dims.union(("len", z), kind_dim)
-        return z
+class _Planner:
+    """Schedules a normalised program into passes of the engine, level by
+    level: a level forms every product whose input vector is complete, then
+    emits the combines that complete vectors (the reduction rule)."""
 
-    for st in stmts:
-        if st[0] == "mat":
+    def __init__(self, spec, stmts, orient, matrix_outs, policy):
+        self.spec, self.decls, self.orient = spec, spec.decls, orient
+        self.matrix_outs, self.policy = matrix_outs, policy
+        self.dims = _Dims()
+        self.temps = [s[1] for s in stmts if s[1] not in self.decls]
+        self.nz = 0                  # numbering of the scaled and zero temporaries
+        self.nw = 0                  # numbering of the WAXPBY temporaries
+        self.steps = []
+        self.nslots = 0
+        self.last = (None, False)    # matrix of the previous pass, and whether it ran reversed
+        stmts = self._expand_updates(stmts)
+        self._tie_vector_lengths(stmts)
+        self._collect(stmts)
+
+    # ---------------------------------------------------------- preparation
+
+    def _temp(self, prefix, dim):
+        self.nz += 1
+        name = "%s%d" % (prefix, self.nz)
+        self.temps.append(name)
+        self.dims.union(("len", name), dim)
+        return name
+
+    def _expand_updates(self, stmts):
+        """Rank-one coefficients other than 1 become scaled temporaries; a
+        single rank-one term gets a zero second term (the engine's update
+        adds two)."""
+        out = []
+        for st in stmts:
+            if st[0] != "mat":
+                out.append(st)
+                continue
             _, tgt, base, outs = st
-            new = []
+            pairs = []
             for c, u, v in outs:
                 if any(isinstance(x, str) for x in c) or _prod(c) != 1.0:
-                    nz[0] += 1
-                    su = "_s%d" % nz[0]
-                    temps.append(su)
-                    expanded.append(("vec", su, _V([(c, ("v", u))])))
-                    dims.union(("len", su), ("len", u))
+                    su = self._temp("_s", ("len", u))
+                    out.append(("vec", su, _V([(c, ("v", u))])))
                     u = su
-                new.append((u, v))
-            dims.union(("rows", tgt), ("rows", base))
-            dims.union(("cols", tgt), ("cols", base))
-            for u, v in new:
-                dims.union(("len", u), ("rows", base))
-                dims.union(("len", v), ("cols", base))
-            if len(new) == 1:
-                zu, zv = zero(("rows", base)), zero(("cols", base))
-                expanded.append(("vec", zu, _V([])))      # a statement with no terms: zeros
-                expanded.append(("vec", zv, _V([])))
-                new.append((zu, zv))
-            expanded.append(("mat", tgt, base, new))
-        else:
-            expanded.append(st)
-    stmts = expanded
+                pairs.append((u, v))
+            self.dims.union(("rows", tgt), ("rows", base))
+            self.dims.union(("cols", tgt), ("cols", base))
+            for u, v in pairs:
+                self.dims.union(("len", u), ("rows", base))
+                self.dims.union(("len", v), ("cols", base))
+            if len(pairs) == 1:
+                zu, zv = self._temp("_z", ("rows", base)), self._temp("_z", ("cols", base))
+                out.append(("vec", zu, _V([])))          # a statement with no terms: zeros
+                out.append(("vec", zv, _V([])))
+                pairs.append((zu, zv))
+            out.append(("mat", tgt, base, pairs))
+        return out
 
-    # Vector lengths from the products.
-    for st in stmts:
-        if st[0] != "vec":
-            continue
-        tgt, v = st[1], st[2]
-        for c, a in v.terms:
-            if a[0] == "v":
-                dims.union(("len", tgt), ("len", a[1]))
-            else:
-                _, M, tr, x = a
-                dims.union(("len", x), ("rows" if tr else "cols", M))
-                dims.union(("len", tgt), ("cols" if tr else "rows", M))
+    def _tie_vector_lengths(self, stmts):
+        for st in stmts:
+            if st[0] != "vec":
+                continue
+            tgt = st[1]
+            for c, a in st[2].terms:
+                if a[0] == "v":
+                    self.dims.union(("len", tgt), ("len", a[1]))
+                else:
+                    _, M, tr, x = a
+                    self.dims.union(("len", x), ("rows" if tr else "cols", M))
+                    self.dims.union(("len", tgt), ("cols" if tr else "rows", M))
 
-    def stored_kind(M, tr):
+    def _stored_kind(self, M, tr):
         # Column-major: M x is the row accumulators (q), M' y the column sums (s).
         q = not tr
-        return "q" if (q if orient[M] == "col" else not q) else "s"
+        return "q" if (q if self.orient[M] == "col" else not q) else "s"
 
-    avail = {n for n, d in decls.items() if d[2] == "in"}
-    nodes = []          # product nodes
-    vec_stmts = []
-    upd = []
-    for st in stmts:
-        if st[0] == "vec":
-            terms = []
-            for c, a in st[2].terms:
-                if a[0] == "mv":
-                    node = {"id": len(nodes), "M": a[1], "tr": a[2], "kind": stored_kind(a[1], a[2]), "x": a[3],
-                            "done": False, "slot": None}
-                    nodes.append(node)
-                    terms.append((c, ("node", node["id"])))
-                else:
-                    terms.append((c, a))
-            vec_stmts.append({"out": st[1], "terms": terms, "done": False})
-        else:
-            upd.append({"out": st[1], "base": st[2], "pairs": st[3], "done": False})
+    def _collect(self, stmts):
+        """Product nodes, vector statements (as combines of nodes and
+        vectors) and rank updates."""
+        self.nodes, self.vec_stmts, self.upd = [], [], []
+        for st in stmts:
+            if st[0] == "vec":
+                terms = []
+                for c, a in st[2].terms:
+                    if a[0] == "mv":
+                        node = {"id": len(self.nodes), "M": a[1], "tr": a[2], "kind": self._stored_kind(a[1], a[2]),
+                                "x": a[3], "done": False, "slot": None}
+                        self.nodes.append(node)
+                        terms.append((c, ("node", node["id"])))
+                    else:
+                        terms.append((c, a))
+                self.vec_stmts.append({"out": st[1], "terms": terms, "done": False})
+            else:
+                self.upd.append({"out": st[1], "base": st[2], "pairs": st[3], "done": False})
 
-    steps = []
-    slot = [0]
-    last_matrix = [None, False]      # matrix of the previous pass, and whether it ran reversed
-    ntemp = [0]
+    # ---------------------------------------------------------- steps
 
-    def new_slot():
-        s = slot[0]
-        slot[0] += 1
+    def _new_slot(self):
+        s = self.nslots
+        self.nslots += 1
         if s >= L.BTO_PROGRAM_MAX_SLOTS:
             raise SpecError("program needs more than %d partial slots" % L.BTO_PROGRAM_MAX_SLOTS)
         return s
 
-    def add_pass(mode, A, forms, B=None, Bout=None, p=None, r=None, upd_vecs=None, nq=None, nq2=None, ns=None):
-        rev = (last_matrix[0] in (A, Bout) and last_matrix[0] is not None) and not last_matrix[1]
+    def _add_pass(self, mode, A, forms, B=None, Bout=None, p=None, r=None, upd_vecs=None, nq=None, nq2=None,
+                  ns=None):
+        # A pass over the matrix the previous pass read or wrote runs its
+        # tiles in reverse, so the tail still in L2 is read first.
+        rev = (self.last[0] is not None and self.last[0] in (A, Bout)) and not self.last[1]
         s = {"op": "pass", "mode": mode, "A": A, "B": B, "Bout": Bout, "p": p, "r": r, "reverse": rev,
              "forms": forms, "slot_q": None, "slot_q2": None, "slot_s": None}
         if upd_vecs:
             s.update(upd_vecs)
-        if nq is not None:
-            nq["slot"] = s["slot_q"] = new_slot()
-        if nq2 is not None:
-            nq2["slot"] = s["slot_q2"] = new_slot()
-        if ns is not None:
-            ns["slot"] = s["slot_s"] = new_slot()
-        steps.append(s)
-        last_matrix[0], last_matrix[1] = (Bout or A), rev
+        for key, nd in (("slot_q", nq), ("slot_q2", nq2), ("slot_s", ns)):
+            if nd is not None:
+                nd["slot"] = s[key] = self._new_slot()
+        self.steps.append(s)
+        self.last = (Bout or A, rev)
         for nd in (nq, nq2, ns):
             if nd is not None:
                 nd["done"] = True
 
-    def label(nd):
+    @staticmethod
+    def _label(nd):
         # The product as the program writes it; a pass that forms a matrix
         # with no product of it ready sums a zero vector.
         if nd["id"] < 0:
             return "(no product)"
         return "%s%s %s" % (nd["M"], "'" if nd["tr"] else "", nd["x"])
 
-    def emit_combines(vs):
+    def _emit_combines(self, vs):
+        """out = sum of scaled slot sums and scaled vectors: vector terms
+        beyond the first are folded with WAXPBY first, then combines add two
+        slots at a time (the later ones onto out itself)."""
         out = vs["out"]
-        parts = [(c, nodes[a[1]]["slot"]) for c, a in vs["terms"] if a[0] == "node"]
+        parts = [(c, self.nodes[a[1]]["slot"]) for c, a in vs["terms"] if a[0] == "node"]
         vecs = [(c, a[1]) for c, a in vs["terms"] if a[0] == "v"]
-        # Two or more vector terms: fold them with WAXPBY first.
         if len(vecs) >= 2:
             cur = vecs[0]
             for k, nxt in enumerate(vecs[1:]):
-                last = k == len(vecs) - 2
-                if last and not parts:
+                if k == len(vecs) - 2 and not parts:
                     dst = out
                 else:
-                    ntemp[0] += 1
-                    dst = "_w%d" % ntemp[0]
-                    temps.append(dst)
-                    dims.union(("len", dst), ("len", out))
-                steps.append({"op": "waxpby", "out": dst, "x": cur, "y": nxt})
+                    self.nw += 1
+                    dst = "_w%d" % self.nw
+                    self.temps.append(dst)
+                    self.dims.union(("len", dst), ("len", out))
+                self.steps.append({"op": "waxpby", "out": dst, "x": cur, "y": nxt})
                 cur = ([1.0], dst)
             if not parts:
                 return
             vecs = [cur]
         x = vecs[0] if vecs else None
         if not parts:
-            steps.append({"op": "combine", "out": out, "src1": None, "src2": None, "x": x})
+            self.steps.append({"op": "combine", "out": out, "src1": None, "src2": None, "x": x})
             return
         first = True
         while parts:
             p1 = parts.pop(0)
             p2 = parts.pop(0) if parts else None
-            steps.append({"op": "combine", "out": out, "src1": p1, "src2": p2,
-                          "x": x if first else ([1.0], out)})
+            self.steps.append({"op": "combine", "out": out, "src1": p1, "src2": p2,
+                               "x": x if first else ([1.0], out)})
             first = False
 
-    while True:
-        pending_nodes = [nd for nd in nodes if not nd["done"]]
-        pending_upd = [u for u in upd if not u["done"]]
-        if not pending_nodes and not pending_upd and all(v["done"] for v in vec_stmts):
-            break
-        progress = False
-        ready_upd = [u for u in pending_upd
-                     if u["base"] in avail and all(a in avail and b in avail for a, b in u["pairs"])]
-        forming = {u["out"]: u for u in ready_upd}
-        ready = [nd for nd in pending_nodes if nd["x"] in avail and (nd["M"] in avail or nd["M"] in forming)]
-        # Updates, each with one product of the matrix it forms.
+    # ---------------------------------------------------------- levels
+
+    def _update_passes(self, ready_upd, ready):
+        """Each ready update forms its matrix in a pass that also forms one
+        ready product of that matrix (G1 for a column sum, G1Q for a row
+        product), or a column sum of zeros when none is ready."""
         for u in ready_upd:
-            mine = [nd for nd in ready if nd["M"] == u["out"]] if policy["update"] else []
+            mine = [nd for nd in ready if nd["M"] == u["out"]] if self.policy["update"] else []
             s_nodes = [nd for nd in mine if nd["kind"] == "s"]
             q_nodes = [nd for nd in mine if nd["kind"] == "q"]
             (a1, b1), (a2, b2) = u["pairs"]
-            if orient[u["out"]] == "row":        # stored transpose: u and v exchange roles
+            if self.orient[u["out"]] == "row":        # stored transpose: u and v exchange roles
                 vecs = {"u1": b1, "v1": a1, "u2": b2, "v2": a2}
             else:
                 vecs = {"u1": a1, "v1": b1, "u2": a2, "v2": b2}
             if s_nodes or not q_nodes:
                 nd = s_nodes[0] if s_nodes else None
                 if nd is None:
-                    # No product is ready: the pass forms the matrix with a
-                    # column sum of a zero vector.
-                    nd = {"id": -1, "M": u["out"], "kind": "s", "x": zero(("rows" if orient[u["out"]] == "col"
-                                                                           else "cols", u["base"])),
-                          "done": False, "slot": None}
-                    steps.append({"op": "combine", "out": nd["x"], "src1": None, "src2": None, "x": None})
-                add_pass("G1", u["base"], [("s", label(nd))], Bout=u["out"], r=nd["x"], upd_vecs=vecs, ns=nd)
+                    z = self._temp("_z", ("rows" if self.orient[u["out"]] == "col" else "cols", u["base"]))
+                    nd = {"id": -1, "M": u["out"], "kind": "s", "x": z, "done": False, "slot": None}
+                    self.steps.append({"op": "combine", "out": z, "src1": None, "src2": None, "x": None})
+                self._add_pass("G1", u["base"], [("s", self._label(nd))], Bout=u["out"], r=nd["x"], upd_vecs=vecs,
+                               ns=nd)
             else:
                 nd = q_nodes[0]
-                add_pass("G1Q", u["base"], [("q", label(nd))], Bout=u["out"], p=nd["x"], upd_vecs=vecs, nq=nd)
+                self._add_pass("G1Q", u["base"], [("q", self._label(nd))], Bout=u["out"], p=nd["x"],
+                               upd_vecs=vecs, nq=nd)
             u["done"] = True
-            progress = True
-        # Plain passes over available matrices.
-        ready = [nd for nd in ready if not nd["done"] and nd["M"] in avail]
+        return bool(ready_upd)
+
+    def _q2_mate(self, nq, singles_q):
+        if not self.policy["q2"]:
+            return None
+        f = self.dims.find
+        for cand in singles_q:
+            if cand["x"] == nq["x"] and cand["M"] != nq["M"] and self.orient[cand["M"]] == self.orient[nq["M"]] and \
+                    f(("rows", cand["M"])) == f(("rows", nq["M"])) and f(("cols", cand["M"])) == f(("cols", nq["M"])):
+                return cand
+        return None
+
+    def _plain_passes(self, ready, avail):
+        """Products of available matrices: a row and a column product of one
+        matrix share a QS pass, row products of two equally shaped matrices
+        on one input a Q2 pass; the rest take a pass each."""
+        progress = False
         by_m = {}
         for nd in ready:
-            by_m.setdefault(nd["M"], []).append(nd)
+            if not nd["done"] and nd["M"] in avail:
+                by_m.setdefault(nd["M"], []).append(nd)
         singles_q = []
         for M, lst in by_m.items():
             qs = [nd for nd in lst if nd["kind"] == "q"]
             ss = [nd for nd in lst if nd["kind"] == "s"]
-            while qs and ss and policy["qs"]:
+            while qs and ss and self.policy["qs"]:
                 nq, ns = qs.pop(0), ss.pop(0)
-                add_pass("QS", M, [("q", label(nq)), ("s", label(ns))], p=nq["x"], r=ns["x"], nq=nq, ns=ns)
+                self._add_pass("QS", M, [("q", self._label(nq)), ("s", self._label(ns))], p=nq["x"], r=ns["x"],
+                               nq=nq, ns=ns)
                 progress = True
             for ns in ss:
-                add_pass("S", M, [("s", label(ns))], r=ns["x"], ns=ns)
+                self._add_pass("S", M, [("s", self._label(ns))], r=ns["x"], ns=ns)
                 progress = True
             singles_q.extend(qs)
-        # Products of two equally shaped matrices with the same input: one pass.
         while singles_q:
             nq = singles_q.pop(0)
-            mate = None
-            for cand in (singles_q if policy["q2"] else []):
-                if cand["x"] == nq["x"] and cand["M"] != nq["M"] and orient[cand["M"]] == orient[nq["M"]] and \
-                        dims.find(("rows", cand["M"])) == dims.find(("rows", nq["M"])) and \
-                        dims.find(("cols", cand["M"])) == dims.find(("cols", nq["M"])):
-                    mate = cand
-                    break
+            mate = self._q2_mate(nq, singles_q)
             if mate is not None:
                 singles_q.remove(mate)
-                add_pass("Q2", nq["M"], [("q", label(nq)), ("q2", label(mate))], B=mate["M"], p=nq["x"],
-                         nq=nq, nq2=mate)
+                self._add_pass("Q2", nq["M"], [("q", self._label(nq)), ("q2", self._label(mate))], B=mate["M"],
+                               p=nq["x"], nq=nq, nq2=mate)
             else:
-                add_pass("Q", nq["M"], [("q", label(nq))], p=nq["x"], nq=nq)
+                self._add_pass("Q", nq["M"], [("q", self._label(nq))], p=nq["x"], nq=nq)
             progress = True
-        for u in upd:
-            if u["done"]:
-                avail.add(u["out"])
-        # Combines of every statement whose products are complete, in order.
-        changed = True
+        return progress
+
+    def _complete_vectors(self, avail):
+        """Combines of every statement whose products are complete, in order;
+        a completed vector may complete a later statement at once."""
+        progress, changed = False, True
         while changed:
             changed = False
-            for vs in vec_stmts:
+            for vs in self.vec_stmts:
                 if vs["done"]:
                     continue
-                ok = all(nodes[a[1]]["done"] if a[0] == "node" else a[1] in avail for c, a in vs["terms"])
-                if ok:
-                    emit_combines(vs)
+                if all(self.nodes[a[1]]["done"] if a[0] == "node" else a[1] in avail for c, a in vs["terms"]):
+                    self._emit_combines(vs)
                     vs["done"] = True
                     avail.add(vs["out"])
                     changed = progress = True
-        if not progress:
-            raise SpecError("cannot schedule the remaining statements (a value is used before it is formed)")
-    return Plan(spec, steps, list(dict.fromkeys(temps)), dims, orient, decls, matrix_outs)
+        return progress
+
+    def plan(self):
+        avail = {n for n, d in self.decls.items() if d[2] == "in"}
+        while True:
+            pending_nodes = [nd for nd in self.nodes if not nd["done"]]
+            pending_upd = [u for u in self.upd if not u["done"]]
+            if not pending_nodes and not pending_upd and all(v["done"] for v in self.vec_stmts):
+                break
+            ready_upd = [u for u in pending_upd
+                         if u["base"] in avail and all(a in avail and b in avail for a, b in u["pairs"])]
+            forming = {u["out"] for u in ready_upd}
+            ready = [nd for nd in pending_nodes if nd["x"] in avail and (nd["M"] in avail or nd["M"] in forming)]
+            progress = self._update_passes(ready_upd, ready)
+            progress |= self._plain_passes(ready, avail)
+            for u in self.upd:
+                if u["done"]:
+                    avail.add(u["out"])
+            progress |= self._complete_vectors(avail)
+            if not progress:
+                raise SpecError("cannot schedule the remaining statements (a value is used before it is formed)")
+        return Plan(self.spec, self.steps, list(dict.fromkeys(self.temps)), self.dims, self.orient, self.decls,
+                    self.matrix_outs)

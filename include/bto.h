@@ -51,7 +51,7 @@ typedef struct CUstream_st *bto_stream_t;
 typedef enum {
     BTO_OK = 0,
     BTO_ERR_INVALID_VALUE = 1, /* bad size, pointer, alignment or aliasing      */
-    BTO_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement   */
+    BTO_ERR_UNSUPPORTED = 2,   /* valid request this library does not implement */
     BTO_ERR_WORKSPACE = 3,     /* ws NULL or smaller than bto_workspace_bytes() */
     BTO_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed          */
     BTO_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired            */

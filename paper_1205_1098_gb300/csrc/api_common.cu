@@ -46,7 +46,7 @@ extern "C" const char* bto_status_string(int s) {
     switch (s) {
         case BTO_OK: return "BTO_OK: success";
         case BTO_ERR_INVALID_VALUE: return "BTO_ERR_INVALID_VALUE: invalid size, pointer, alignment or aliasing";
-        case BTO_ERR_UNSUPPORTED: return "BTO_ERR_UNSUPPORTED: request not implemented by this build";
+        case BTO_ERR_UNSUPPORTED: return "BTO_ERR_UNSUPPORTED: request not implemented by this library version";
         case BTO_ERR_WORKSPACE: return "BTO_ERR_WORKSPACE: workspace missing or too small";
         case BTO_ERR_CUDA: return "BTO_ERR_CUDA: a CUDA runtime call or kernel launch failed";
         case BTO_ERR_TIMEOUT: return "BTO_ERR_TIMEOUT: a bounded device-side wait expired";

@@ -76,6 +76,10 @@ typedef enum {
  * one-kernel-per-BLAS-call sequences (bto_unfused_*). */
 #define BTO_FORM_FUSED 0
 #define BTO_FORM_UNFUSED 1
+/* The double-float forms of the FP64 matrix sequences (bto_*_df and
+ * bto_unfused_*_df, below): matrix ops BICGK .. DGEMVT, a_type BTO_F64. */
+#define BTO_FORM_DF 2
+#define BTO_FORM_DF_UNFUSED 3
 
 /* ---------------------------------------------------------------- utilities */
 
@@ -629,6 +633,86 @@ bto_status bto_unfused_waxpby(int64_t n, double alpha, const double *x, double b
                               const double *y, double *w, bto_stream_t stream);
 bto_status bto_unfused_vadd(int64_t n, const double *w, const double *y, const double *z,
                             double *x, bto_stream_t stream);
+
+/* --------------------------------- double-float form of the FP64 sequences
+ * The six FP64 matrix sequences of Table I (Section V-A) with the same
+ * arguments, outputs, aliasing rules and validation as bto_bicgk ..
+ * bto_dgemvt and bto_unfused_* above, computed in double-float arithmetic
+ * (each FP64 value carried as a sum of two FP32 numbers) on the FP32 units
+ * instead of the FP64 unit, which on this GPU issues two FMAs per clock per
+ * SM, too few to keep up with HBM.  Data in and out are FP64; only the
+ * arithmetic differs from the FP64 form:
+ *   - each matrix element keeps 47 of its 53 significant bits (the low 6
+ *     fraction bits are dropped); each product is exact up to the dropped
+ *     low-part product (below 2^-47 of it); sums are compensated (TwoSum);
+ *     the final reduction over tiles is FP64.  Normwise relative error
+ *     against exact FP64 arithmetic: about 1e-14 on ordinary data (the FP64
+ *     form's contract is 1e-12); integer-valued data below 2^24 in
+ *     magnitude give exact results, as in the FP64 form.
+ *   - GEMVER's B is hi + lo rounded once to FP64: within 2^-45 relative of
+ *     the exact A + u1 v1^T + u2 v2^T (the FP64 form rounds twice); x and w
+ *     are computed from that B.
+ *   - Operating range: matrix elements zero or of magnitude in [2^-70, 2^60),
+ *     vector elements zero or in [2^-30, 2^30).  A 256-row chunk of a tile
+ *     whose data fall outside it, or whose results are not finite, is
+ *     recomputed in FP64 (NaN and Inf propagate as in the FP64 form).
+ *   - Layout: the matrices are copied by the tensor memory accelerator, which
+ *     needs 16-byte aligned matrix pointers and even leading dimensions (and
+ *     m, n < 2^31).  Otherwise the call runs the FP64 form with the same
+ *     arguments (the workspace is large enough for either).
+ * Workspace: bto_workspace_bytes(op, BTO_FORM_DF, m, n, BTO_F64) for the
+ * fused calls, BTO_FORM_DF_UNFUSED for the unfused ones.  The status word at
+ * the start of ws is cleared by the call and reads BTO_ERR_TIMEOUT
+ * (bto_device_status) if a bounded wait of the sweep expired.
+ * ATAX in this form reads A twice (t = A x, then y = beta A^T t), as its
+ * unfused form; the other fused forms read each matrix as often as the FP64
+ * fused form.  The unfused forms follow the decompositions listed above,
+ * with every dgemv a double-float sweep (dcopy, dger, dscal stay FP64). */
+bto_status bto_bicgk_df(int64_t m, int64_t n, const double *A, int64_t lda,
+                        const double *p, const double *r, double *q, double *s,
+                        void *ws, size_t ws_bytes, bto_stream_t stream);
+bto_status bto_atax_df(int64_t m, int64_t n, double beta, const double *A, int64_t lda,
+                       const double *x, double *y, void *ws, size_t ws_bytes,
+                       bto_stream_t stream);
+bto_status bto_gemver_df(int64_t m, int64_t n, double alpha, double beta,
+                         const double *A, int64_t lda, const double *u1,
+                         const double *v1, const double *u2, const double *v2,
+                         const double *y, const double *z, double *B, int64_t ldb,
+                         double *x, double *w, void *ws, size_t ws_bytes,
+                         bto_stream_t stream);
+bto_status bto_gesummv_df(int64_t m, int64_t n, double alpha, const double *A, int64_t lda,
+                          double beta, const double *B, int64_t ldb, const double *x,
+                          double *y, void *ws, size_t ws_bytes, bto_stream_t stream);
+bto_status bto_dgemv_df(int64_t m, int64_t n, double alpha, const double *A, int64_t lda,
+                        const double *x, double beta, const double *y, double *z,
+                        void *ws, size_t ws_bytes, bto_stream_t stream);
+bto_status bto_dgemvt_df(int64_t m, int64_t n, double alpha, double beta,
+                         const double *A, int64_t lda, const double *y,
+                         const double *z, double *x, double *w,
+                         void *ws, size_t ws_bytes, bto_stream_t stream);
+bto_status bto_unfused_bicgk_df(int64_t m, int64_t n, const double *A, int64_t lda,
+                                const double *p, const double *r, double *q, double *s,
+                                void *ws, size_t ws_bytes, bto_stream_t stream);
+bto_status bto_unfused_atax_df(int64_t m, int64_t n, double beta, const double *A, int64_t lda,
+                               const double *x, double *y, void *ws, size_t ws_bytes,
+                               bto_stream_t stream);
+bto_status bto_unfused_gemver_df(int64_t m, int64_t n, double alpha, double beta,
+                                 const double *A, int64_t lda, const double *u1,
+                                 const double *v1, const double *u2, const double *v2,
+                                 const double *y, const double *z, double *B, int64_t ldb,
+                                 double *x, double *w, void *ws, size_t ws_bytes,
+                                 bto_stream_t stream);
+bto_status bto_unfused_gesummv_df(int64_t m, int64_t n, double alpha, const double *A,
+                                  int64_t lda, double beta, const double *B, int64_t ldb,
+                                  const double *x, double *y, void *ws, size_t ws_bytes,
+                                  bto_stream_t stream);
+bto_status bto_unfused_dgemv_df(int64_t m, int64_t n, double alpha, const double *A, int64_t lda,
+                                const double *x, double beta, const double *y, double *z,
+                                void *ws, size_t ws_bytes, bto_stream_t stream);
+bto_status bto_unfused_dgemvt_df(int64_t m, int64_t n, double alpha, double beta,
+                                 const double *A, int64_t lda, const double *y,
+                                 const double *z, double *x, double *w,
+                                 void *ws, size_t ws_bytes, bto_stream_t stream);
 
 /* ------------------------------------------------ synthetic input fills
  * Not part of any Table I operation: device-side generation of the seeded

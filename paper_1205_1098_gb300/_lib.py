@@ -58,13 +58,17 @@ SIGNATURES = {
     "bto_csr_bicgk": "iiippppppppzs",
     "bto_csr_atax": "iiipppdpppzs",
 }
+# The double-float forms take the FP64 forms' arguments.
+for _k in ("bicgk", "atax", "gemver", "gesummv", "dgemv", "dgemvt"):
+    SIGNATURES["bto_%s_df" % _k] = SIGNATURES["bto_" + _k]
+    SIGNATURES["bto_unfused_%s_df" % _k] = SIGNATURES["bto_unfused_" + _k]
 _KIND = {"i": _c_i64, "u": _c_u64, "d": _c_f64, "f": ctypes.c_float, "p": _c_ptr, "z": _c_size,
          "s": _c_ptr, "k": _c_int}
 
 BTO_OK, BTO_ERR_INVALID_VALUE, BTO_ERR_UNSUPPORTED, BTO_ERR_WORKSPACE = 0, 1, 2, 3
 BTO_ERR_CUDA, BTO_ERR_TIMEOUT, BTO_ERR_BUDGET = 4, 5, 6
 BTO_F64, BTO_F32, BTO_BF16 = 0, 1, 2
-BTO_FORM_FUSED, BTO_FORM_UNFUSED = 0, 1
+BTO_FORM_FUSED, BTO_FORM_UNFUSED, BTO_FORM_DF, BTO_FORM_DF_UNFUSED = 0, 1, 2, 3
 BTO_COL_MAJOR, BTO_ROW_MAJOR = 0, 1
 BTO_NO_TRANS, BTO_TRANS = 0, 1
 OPS = {"bicgk": 0, "atax": 1, "gemver": 2, "gesummv": 3, "dgemv": 4, "dgemvt": 5,

@@ -73,7 +73,7 @@ extern "C" bto_status bto_workspace_bytes(int op, int form, int64_t m, int64_t n
                                           size_t* bytes) {
     clear_invalid_arg();
     if (op < BTO_OP_BICGK || op > BTO_OP_VADD) { set_invalid_arg(1); return BTO_ERR_INVALID_VALUE; }
-    if (form != BTO_FORM_FUSED && form != BTO_FORM_UNFUSED) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
+    if (form < BTO_FORM_FUSED || form > BTO_FORM_DF_UNFUSED) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
     if (m < 0) { set_invalid_arg(3); return BTO_ERR_INVALID_VALUE; }
     if (n < 0) { set_invalid_arg(4); return BTO_ERR_INVALID_VALUE; }
     if (a_type < BTO_F64 || a_type > BTO_BF16) { set_invalid_arg(5); return BTO_ERR_INVALID_VALUE; }

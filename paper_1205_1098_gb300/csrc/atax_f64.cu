@@ -294,7 +294,7 @@ using namespace bto;
 
 namespace {
 
-bto_status atax_impl(int64_t m, int64_t n, double beta, const double* A, int64_t lda,
+bto_status atax_impl(int form, int64_t m, int64_t n, double beta, const double* A, int64_t lda,
                      const double* x, double* y, void* ws, size_t ws_bytes, int64_t stall_band,
                      unsigned long long timeout_ns, bto_stream_t stream) {
     clear_invalid_arg();
@@ -308,13 +308,29 @@ bto_status atax_impl(int64_t m, int64_t n, double beta, const double* A, int64_t
     DeviceInfo d; WsLayout L;
     if (c.ok()) {
         if (!device_info(&d)) return BTO_ERR_CUDA;
-        if (ws_layout(BTO_OP_ATAX, BTO_FORM_FUSED, m, n, BTO_F64, d, &L) != BTO_OK) return BTO_ERR_CUDA;
+        if (ws_layout(BTO_OP_ATAX, form, m, n, BTO_F64, d, &L) != BTO_OK) return BTO_ERR_CUDA;
         c.ws(8, ws, ws_bytes, L);
     }
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
     char* w = static_cast<char*>(ws);
     if (n == 0) return BTO_OK;
+    if (form == BTO_FORM_DF) {
+        // Double-float form: t = A x into the workspace, then y = beta A^T t
+        // with the tiles in reverse (the last ones are still in L2).
+        const PanelPlan dp = df_plan(m, n, d.sms);
+        const DfArgs probe = df_args(m, n, A, lda, dp, ws);
+        if (m > 0 && df_layout_ok(DF_Q, probe)) {
+            if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
+            double* t = reinterpret_cast<double*>(w + L.off[0]);
+            bto_status e = df_gemv_n(m, n, 1.0, A, lda, x, 0.0, nullptr, t,
+                                     reinterpret_cast<double*>(w + L.off[1]), dp, ws, 0, st);
+            if (e != BTO_OK) return e;
+            return df_gemv_t(m, n, beta, A, lda, t, 0.0, nullptr, y, reinterpret_cast<double*>(w + L.off[2]), dp,
+                             ws, 1, st);
+        }
+        if (ws_layout(BTO_OP_ATAX, BTO_FORM_FUSED, m, n, BTO_F64, d, &L) != BTO_OK) return BTO_ERR_CUDA;
+    }
     const AtaxPlan ap = atax_plan(m, n, d);
     // The status word reads BTO_OK after every form; the group-band kernel
     // clears it below together with its flags.
@@ -375,7 +391,13 @@ bto_status atax_impl(int64_t m, int64_t n, double beta, const double* A, int64_t
 extern "C" bto_status bto_atax(int64_t m, int64_t n, double beta, const double* A, int64_t lda,
                                const double* x, double* y, void* ws, size_t ws_bytes,
                                bto_stream_t stream) {
-    return atax_impl(m, n, beta, A, lda, x, y, ws, ws_bytes, -1, 2000000000ull, stream);
+    return atax_impl(BTO_FORM_FUSED, m, n, beta, A, lda, x, y, ws, ws_bytes, -1, 2000000000ull, stream);
+}
+
+extern "C" bto_status bto_atax_df(int64_t m, int64_t n, double beta, const double* A, int64_t lda,
+                                  const double* x, double* y, void* ws, size_t ws_bytes,
+                                  bto_stream_t stream) {
+    return atax_impl(BTO_FORM_DF, m, n, beta, A, lda, x, y, ws, ws_bytes, -1, 2000000000ull, stream);
 }
 
 // Fault injection for tests (declared in bto.h's testing section): band
@@ -386,6 +408,6 @@ extern "C" bto_status bto_debug_atax_stall(int64_t m, int64_t n, double beta, co
                                            size_t ws_bytes, int64_t stall_band, int timeout_ms,
                                            bto_stream_t stream) {
     if (timeout_ms < 1 || timeout_ms > 10000) { set_invalid_arg(11); return BTO_ERR_INVALID_VALUE; }
-    return atax_impl(m, n, beta, A, lda, x, y, ws, ws_bytes, stall_band,
+    return atax_impl(BTO_FORM_FUSED, m, n, beta, A, lda, x, y, ws, ws_bytes, stall_band,
                      (unsigned long long)timeout_ms * 1000000ull, stream);
 }

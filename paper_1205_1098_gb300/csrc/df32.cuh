@@ -109,5 +109,70 @@ DF_HD f2 df_mac(f2 acc, f2 a, f2 b) {
 
 DF_HD double to_f64(f2 v) { return (double)v.hi + (double)v.lo; }
 
+// ---------------------------------------------------------------- sweep split
+// The split the double-float matrix sweeps use, from the two 32-bit words of
+// an FP64 number (hw: sign, exponent, top 20 fraction bits; lw: low 32
+// fraction bits), in nine integer and one FP32 operation:
+//   hi: sign, exponent rebased to FP32, fraction bits 51..29 (truncated);
+//   lo: fraction bits 28..6: the FP32 number with hi's sign and exponent
+//       and those bits as its fraction, minus hi's sign and exponent alone
+//       (exact), times 2^-23 (exact unless it underflows).
+// |x - (hi + lo)| < 2^-46 |x| (47 significant bits kept); exact for zero,
+// FP32 values and integers below 2^47.  Valid for x = 0 and for
+// 2^-100 <= |x| < 2^128; FP64 subnormals below 2^-1042 (high word zero
+// apart from the sign) give |hi| + |lo| < 2^-145.  The sweeps check the
+// narrower operating ranges below and recompute anything outside them in
+// FP64.
+constexpr uint32_t kSplitBias = 0x38000000u;      // (1023 - 127) << 20
+// Operating ranges as bounds on the high word without its sign (ax):
+// matrix elements 2^-70 <= |a| < 2^60, vector elements 2^-30 <= |v| < 2^30
+// (or exactly zero).  Then every product |a v| lies in [2^-100, 2^90): its
+// double-float parts stay normal in FP32, and sums of up to 2^31 of them
+// stay below 2^121.
+constexpr uint32_t kMatLo = 953u << 20, kMatHi = 1083u << 20;
+constexpr uint32_t kVecLo = 993u << 20, kVecHi = 1053u << 20;
+
+DF_HD uint32_t float_bits(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof u);
+    return u;
+}
+
+DF_HD void split_words(uint32_t hw, uint32_t lw, float& hi, float& lo) {
+    const uint32_t ax = hw & 0x7fffffffu;
+#if defined(__CUDA_ARCH__)
+    const uint32_t t = (uint32_t)__viaddmax_s32((int)ax, -(int)kSplitBias, 0);   // zero -> 0
+    const uint32_t hb = __funnelshift_l(lw, t, 3) | (hw & 0x80000000u);
+#else
+    const int32_t ti = (int32_t)ax - (int32_t)kSplitBias;
+    const uint32_t t = ti > 0 ? (uint32_t)ti : 0u;
+    const uint32_t hb = ((t << 3) | (lw >> 29)) | (hw & 0x80000000u);
+#endif
+    const uint32_t base = hb & 0xff800000u;                      // sign and exponent of hi
+    const uint32_t mx = base | ((lw >> 6) & 0x7fffffu);
+    hi = float_of(hb);
+    lo = (float_of(mx) - float_of(base)) * 0x1p-23f;
+}
+
+DF_HD void split_double(double x, float& hi, float& lo) {
+    const uint64_t u = bits_of(x);
+    split_words((uint32_t)(u >> 32), (uint32_t)u, hi, lo);
+}
+
+// An FP32 number as the two words of the equal FP64 number, by integer
+// operations; subnormal FP32 inputs (below 2^-126) become signed zero.
+DF_HD void f32_to_f64_words(float f, uint32_t& hw, uint32_t& lw) {
+    const uint32_t u = float_bits(f), ax = u & 0x7fffffffu;
+    hw = (ax >= 0x00800000u ? (ax >> 3) + kSplitBias : 0u) | (u & 0x80000000u);
+    lw = ax >= 0x00800000u ? u << 29 : 0u;
+}
+
+DF_HD double f64_of_words(uint32_t hw, uint32_t lw) {
+    const uint64_t u = ((uint64_t)hw << 32) | lw;
+    double d;
+    std::memcpy(&d, &u, sizeof d);
+    return d;
+}
+
 }  // namespace df
 }  // namespace bto

@@ -165,6 +165,45 @@ struct LpArgs {
 // load-instruction sweep instead.
 bool lp_tma_launch(int a_type, int mode, const LpArgs& a, int grid, int bps, cudaStream_t st, bto_status* out);
 
+// ------------------------------------------------------------ double-float form
+// Sweeps of the FP64 matrix sequences with double-float arithmetic on the
+// FP32 pipes (df_tma.cu): q = A p and s = A^T r together (BICGK), q alone,
+// s alone, GEMVER's first pass (B = A + u1 v1^T + u2 v2^T written in FP64,
+// s = B^T r), and q over two matrices (GESUMMV).  Tiles as the reduced-
+// precision form: column panels of whole 16-column units, row blocks of
+// whole 256-row chunks; partials in FP64 for the panel engine's combine.
+enum DfMode { DF_QS = 0, DF_Q = 1, DF_S = 2, DF_G1 = 3, DF_Q2 = 4 };
+
+struct DfArgs {
+    int64_t m, n;
+    const double* A; int64_t lda;
+    const double* B; int64_t ldb;      // second matrix (DF_Q2)
+    double* Bout; int64_t ldbo;        // formed matrix (DF_G1), may equal A
+    const double* p;                   // column-indexed vector (DF_QS, DF_Q, DF_Q2)
+    const double* r;                   // row-indexed vector (DF_QS, DF_S; DF_G1: y)
+    const double* u1; const double* v1; const double* u2; const double* v2;
+    double* qpart; double* qpart2; double* spart;
+    int64_t ldq, lds, tcmax;
+    int NR, NC; int64_t ntiles; int reverse;
+    int* status;                       // device status word (timeouts of bounded waits)
+};
+PanelPlan df_plan(int64_t m, int64_t n, int sms);
+// True when the matrices suit the tensor-map copies the sweep is built on
+// (16-byte aligned bases, even leading dimensions, sizes below 2^31).
+bool df_layout_ok(int mode, const DfArgs& a);
+// Launches the sweep (the layout must pass df_layout_ok).
+bto_status df_launch(int mode, const DfArgs& a, const PanelPlan& pl, cudaStream_t st);
+// Arguments of a sweep over A with the plan's tiles; the status word at ws.
+DfArgs df_args(int64_t m, int64_t n, const double* A, int64_t lda, const PanelPlan& pl, void* ws);
+// out = alpha A v (+ beta y when y != NULL) and out = alpha A^T v (+ beta y):
+// a single-product sweep and its combine (m or n = 0: the combine alone).
+bto_status df_gemv_n(int64_t m, int64_t n, double alpha, const double* A, int64_t lda, const double* v,
+                     double beta, const double* y, double* out, double* qpart, const PanelPlan& pl, void* ws,
+                     int reverse, cudaStream_t st);
+bto_status df_gemv_t(int64_t m, int64_t n, double alpha, const double* A, int64_t lda, const double* v,
+                     double beta, const double* y, double* out, double* spart, const PanelPlan& pl, void* ws,
+                     int reverse, cudaStream_t st);
+
 // ------------------------------------------------------------ ATAX group bands
 // A cooperative grid of G blocks is cut into NG groups of S; group g takes
 // the bands of TB rows g, g + NG, ...; block r of a group owns a fixed slice
@@ -190,8 +229,20 @@ struct WsLayout {
 };
 bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type,
                      const DeviceInfo& d, WsLayout* out);
+// Workspace of the double-float forms (form BTO_FORM_DF or BTO_FORM_DF_UNFUSED):
+// room for the double-float sweeps' partials and for the FP64 form the call
+// runs instead when the layout does not suit the tensor-map copies.
+bto_status df_ws_layout(int op, int form, int64_t m, int64_t n, const DeviceInfo& d, WsLayout* out);
 // Validates ws against the layout; sets the invalid-arg position on failure.
 bto_status check_ws(const void* ws, size_t ws_bytes, const WsLayout& L, int pos_ws);
+
+// ------------------------------------------------------------ BLAS-1/2 building blocks
+// Kernels of the unfused forms (unfused_f64.cu), one per BLAS call.
+bto_status dcopy(int64_t n, const double* x, double* y, int sms, cudaStream_t st);
+bto_status dcopy_mat(int64_t m, int64_t n, const double* A, int64_t lda, double* B, int64_t ldb,
+                     int sms, cudaStream_t st);
+bto_status dger(int64_t m, int64_t n, const double* x, const double* y, double* A, int64_t lda,
+                int sms, cudaStream_t st);
 
 // ------------------------------------------------------------ vector helpers
 int vector_grid(int sms);                     // blocks of the reduction kernels

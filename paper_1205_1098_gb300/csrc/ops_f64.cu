@@ -16,6 +16,10 @@ size_t region(size_t& cur, size_t bytes) {
 
 bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type, const DeviceInfo& d,
                      WsLayout* out) {
+    if (form == BTO_FORM_DF || form == BTO_FORM_DF_UNFUSED) {
+        if (a_type != BTO_F64) return BTO_ERR_UNSUPPORTED;
+        return df_ws_layout(op, form, m, n, d, out);
+    }
     // Reduced-precision storage exists for the fused BICGK, GEMVER, ATAX and
     // GESUMMV forms (bto_*_ex); their partials take the FP64 form's space.
     if (a_type != BTO_F64 &&
@@ -85,11 +89,26 @@ bool prepare(int op, int form, int64_t m, int64_t n, DeviceInfo* d, WsLayout* L)
 
 double* wsd(void* ws, size_t off) { return reinterpret_cast<double*>(static_cast<char*>(ws) + off); }
 
+// The double-float form runs on the plan and workspace regions of df_plan /
+// df_ws_layout, after clearing the status word; when the matrices do not suit
+// its tensor-map copies, the FP64 form runs instead, on its own regions of
+// the same workspace (df_ws_layout makes room for both).
+// The status word is cleared on either path (true with *e set on failure).
+bool df_ready(int form, int mode, const DfArgs& a, cudaStream_t st, bto_status* e) {
+    *e = BTO_OK;
+    if (form != BTO_FORM_DF) return false;
+    if (cudaMemsetAsync(a.status, 0, sizeof(int), st) != cudaSuccess) {
+        *e = BTO_ERR_CUDA;
+        return true;
+    }
+    return a.m > 0 && a.n > 0 && df_layout_ok(mode, a);
+}
+
 }  // namespace
 
-extern "C" bto_status bto_bicgk(int64_t m, int64_t n, const double* A, int64_t lda,
-                                const double* p, const double* r, double* q, double* s,
-                                void* ws, size_t ws_bytes, bto_stream_t stream) {
+static bto_status run_bicgk(int form, int64_t m, int64_t n, const double* A, int64_t lda,
+                            const double* p, const double* r, double* q, double* s,
+                            void* ws, size_t ws_bytes, bto_stream_t stream) {
     clear_invalid_arg();
     Check c;
     c.size(1, m); c.size(2, n);
@@ -102,11 +121,26 @@ extern "C" bto_status bto_bicgk(int64_t m, int64_t n, const double* A, int64_t l
     c.disjoint(8, s, vbytes(n), A, Ab); c.disjoint(8, s, vbytes(n), p, vbytes(n));
     c.disjoint(8, s, vbytes(n), r, vbytes(m));
     DeviceInfo d; WsLayout L;
-    if (c.ok() && !prepare(BTO_OP_BICGK, BTO_FORM_FUSED, m, n, &d, &L)) return BTO_ERR_CUDA;
+    if (c.ok() && !prepare(BTO_OP_BICGK, form, m, n, &d, &L)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(9, ws, ws_bytes, L);
     if (!c.ok()) return c.finish();
 
     cudaStream_t st = (cudaStream_t)stream;
+    {
+        const PanelPlan dp = df_plan(m, n, d.sms);
+        DfArgs a = df_args(m, n, A, lda, dp, ws);
+        a.p = p; a.r = r; a.qpart = wsd(ws, L.off[0]); a.spart = wsd(ws, L.off[1]);
+        bto_status e;
+        if (df_ready(form, DF_QS, a, st, &e)) {
+            if (e != BTO_OK || (e = df_launch(DF_QS, a, dp, st)) != BTO_OK) return e;
+            CombineJob j[2] = {};
+            j[0] = {q, m, a.qpart, dp.ldq, dp.NC, 1.0, nullptr, 0, 0, 0.0, nullptr, 0.0};
+            j[1] = {s, n, a.spart, dp.lds, dp.NR, 1.0, nullptr, 0, 0, 0.0, nullptr, 0.0};
+            return launch_combine(j, 2, st);
+        }
+        if (form == BTO_FORM_DF && ws_layout(BTO_OP_BICGK, BTO_FORM_FUSED, m, n, BTO_F64, d, &L) != BTO_OK)
+            return BTO_ERR_CUDA;
+    }
     const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_BICGK, BTO_FORM_FUSED);
     PanelArgs a{};
     a.m = m; a.n = n; a.A = A; a.lda = lda; a.p = p; a.r = r;
@@ -120,9 +154,9 @@ extern "C" bto_status bto_bicgk(int64_t m, int64_t n, const double* A, int64_t l
     return launch_combine(j, 2, st);
 }
 
-extern "C" bto_status bto_dgemv(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
-                                const double* x, double beta, const double* y, double* z,
-                                void* ws, size_t ws_bytes, bto_stream_t stream) {
+static bto_status run_dgemv(int form, int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                            const double* x, double beta, const double* y, double* z,
+                            void* ws, size_t ws_bytes, bto_stream_t stream) {
     clear_invalid_arg();
     Check c;
     c.size(1, m); c.size(2, n);
@@ -133,11 +167,22 @@ extern "C" bto_status bto_dgemv(int64_t m, int64_t n, double alpha, const double
     c.disjoint(9, z, vbytes(m), A, Ab); c.disjoint(9, z, vbytes(m), x, vbytes(n));
     if (z != y) c.disjoint(9, z, vbytes(m), y, vbytes(m));
     DeviceInfo d; WsLayout L;
-    if (c.ok() && !prepare(BTO_OP_DGEMV, BTO_FORM_FUSED, m, n, &d, &L)) return BTO_ERR_CUDA;
+    if (c.ok() && !prepare(BTO_OP_DGEMV, form, m, n, &d, &L)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(10, ws, ws_bytes, L);
     if (!c.ok()) return c.finish();
 
     cudaStream_t st = (cudaStream_t)stream;
+    {
+        const PanelPlan dp = df_plan(m, n, d.sms);
+        DfArgs a = df_args(m, n, A, lda, dp, ws);
+        bto_status e;
+        if (df_ready(form, DF_Q, a, st, &e)) {
+            if (e != BTO_OK) return e;
+            return df_gemv_n(m, n, alpha, A, lda, x, beta, y, z, wsd(ws, L.off[0]), dp, ws, 0, st);
+        }
+        if (form == BTO_FORM_DF && ws_layout(BTO_OP_DGEMV, BTO_FORM_FUSED, m, n, BTO_F64, d, &L) != BTO_OK)
+            return BTO_ERR_CUDA;
+    }
     const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_DGEMV, BTO_FORM_FUSED);
     PanelArgs a{};
     a.m = m; a.n = n; a.A = A; a.lda = lda; a.p = x;
@@ -149,10 +194,10 @@ extern "C" bto_status bto_dgemv(int64_t m, int64_t n, double alpha, const double
     return launch_combine(&j, 1, st);
 }
 
-extern "C" bto_status bto_gesummv(int64_t m, int64_t n, double alpha, const double* A,
-                                  int64_t lda, double beta, const double* B, int64_t ldb,
-                                  const double* x, double* y, void* ws, size_t ws_bytes,
-                                  bto_stream_t stream) {
+static bto_status run_gesummv(int form, int64_t m, int64_t n, double alpha, const double* A,
+                              int64_t lda, double beta, const double* B, int64_t ldb,
+                              const double* x, double* y, void* ws, size_t ws_bytes,
+                              bto_stream_t stream) {
     clear_invalid_arg();
     Check c;
     c.size(1, m); c.size(2, n);
@@ -164,11 +209,24 @@ extern "C" bto_status bto_gesummv(int64_t m, int64_t n, double alpha, const doub
     c.disjoint(10, y, vbytes(m), A, Ab); c.disjoint(10, y, vbytes(m), B, Bb);
     c.disjoint(10, y, vbytes(m), x, vbytes(n));
     DeviceInfo d; WsLayout L;
-    if (c.ok() && !prepare(BTO_OP_GESUMMV, BTO_FORM_FUSED, m, n, &d, &L)) return BTO_ERR_CUDA;
+    if (c.ok() && !prepare(BTO_OP_GESUMMV, form, m, n, &d, &L)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(11, ws, ws_bytes, L);
     if (!c.ok()) return c.finish();
 
     cudaStream_t st = (cudaStream_t)stream;
+    {
+        const PanelPlan dp = df_plan(m, n, d.sms);
+        DfArgs a = df_args(m, n, A, lda, dp, ws);
+        a.B = B; a.ldb = ldb; a.p = x; a.qpart = wsd(ws, L.off[0]); a.qpart2 = wsd(ws, L.off[1]);
+        bto_status e;
+        if (df_ready(form, DF_Q2, a, st, &e)) {
+            if (e != BTO_OK || (e = df_launch(DF_Q2, a, dp, st)) != BTO_OK) return e;
+            CombineJob j = {y, m, a.qpart, dp.ldq, dp.NC, alpha, a.qpart2, dp.ldq, dp.NC, beta, nullptr, 0.0};
+            return launch_combine(&j, 1, st);
+        }
+        if (form == BTO_FORM_DF && ws_layout(BTO_OP_GESUMMV, BTO_FORM_FUSED, m, n, BTO_F64, d, &L) != BTO_OK)
+            return BTO_ERR_CUDA;
+    }
     const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_GESUMMV, BTO_FORM_FUSED);
     PanelArgs a{};
     a.m = m; a.n = n; a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.p = x;
@@ -180,10 +238,10 @@ extern "C" bto_status bto_gesummv(int64_t m, int64_t n, double alpha, const doub
     return launch_combine(&j, 1, st);
 }
 
-extern "C" bto_status bto_dgemvt(int64_t m, int64_t n, double alpha, double beta,
-                                 const double* A, int64_t lda, const double* y, const double* z,
-                                 double* x, double* w, void* ws, size_t ws_bytes,
-                                 bto_stream_t stream) {
+static bto_status run_dgemvt(int form, int64_t m, int64_t n, double alpha, double beta,
+                             const double* A, int64_t lda, const double* y, const double* z,
+                             double* x, double* w, void* ws, size_t ws_bytes,
+                             bto_stream_t stream) {
     clear_invalid_arg();
     Check c;
     c.size(1, m); c.size(2, n);
@@ -196,11 +254,25 @@ extern "C" bto_status bto_dgemvt(int64_t m, int64_t n, double alpha, double beta
     c.disjoint(10, w, vbytes(m), A, Ab); c.disjoint(10, w, vbytes(m), y, vbytes(m));
     c.disjoint(10, w, vbytes(m), z, vbytes(n)); c.disjoint(10, w, vbytes(m), x, vbytes(n));
     DeviceInfo d; WsLayout L;
-    if (c.ok() && !prepare(BTO_OP_DGEMVT, BTO_FORM_FUSED, m, n, &d, &L)) return BTO_ERR_CUDA;
+    if (c.ok() && !prepare(BTO_OP_DGEMVT, form, m, n, &d, &L)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(11, ws, ws_bytes, L);
     if (!c.ok()) return c.finish();
 
     cudaStream_t st = (cudaStream_t)stream;
+    {
+        const PanelPlan dp = df_plan(m, n, d.sms);
+        DfArgs a = df_args(m, n, A, lda, dp, ws);
+        bto_status e;
+        if (df_ready(form, DF_S, a, st, &e)) {
+            if (e != BTO_OK) return e;
+            // x = beta A^T y + z, then w = alpha A x with panels in reverse (L2 reuse).
+            if ((e = df_gemv_t(m, n, beta, A, lda, y, 1.0, z, x, wsd(ws, L.off[1]), dp, ws, 0, st)) != BTO_OK)
+                return e;
+            return df_gemv_n(m, n, alpha, A, lda, x, 0.0, nullptr, w, wsd(ws, L.off[0]), dp, ws, 1, st);
+        }
+        if (form == BTO_FORM_DF && ws_layout(BTO_OP_DGEMVT, BTO_FORM_FUSED, m, n, BTO_F64, d, &L) != BTO_OK)
+            return BTO_ERR_CUDA;
+    }
     const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_DGEMVT, BTO_FORM_FUSED);
     PanelArgs a{};
     a.m = m; a.n = n; a.A = A; a.lda = lda; a.r = y;
@@ -218,12 +290,12 @@ extern "C" bto_status bto_dgemvt(int64_t m, int64_t n, double alpha, double beta
     return launch_combine(&jw, 1, st);
 }
 
-extern "C" bto_status bto_gemver(int64_t m, int64_t n, double alpha, double beta,
-                                 const double* A, int64_t lda, const double* u1,
-                                 const double* v1, const double* u2, const double* v2,
-                                 const double* y, const double* z, double* B, int64_t ldb,
-                                 double* x, double* w, void* ws, size_t ws_bytes,
-                                 bto_stream_t stream) {
+static bto_status run_gemver(int form, int64_t m, int64_t n, double alpha, double beta,
+                             const double* A, int64_t lda, const double* u1,
+                             const double* v1, const double* u2, const double* v2,
+                             const double* y, const double* z, double* B, int64_t ldb,
+                             double* x, double* w, void* ws, size_t ws_bytes,
+                             bto_stream_t stream) {
     clear_invalid_arg();
     Check c;
     c.size(1, m); c.size(2, n);
@@ -245,11 +317,27 @@ extern "C" bto_status bto_gemver(int64_t m, int64_t n, double alpha, double beta
     for (int k = 0; k < 6; k++) c.disjoint(16, w, vbytes(m), ins[k], inb[k]);
     c.disjoint(16, w, vbytes(m), x, vbytes(n));
     DeviceInfo d; WsLayout L;
-    if (c.ok() && !prepare(BTO_OP_GEMVER, BTO_FORM_FUSED, m, n, &d, &L)) return BTO_ERR_CUDA;
+    if (c.ok() && !prepare(BTO_OP_GEMVER, form, m, n, &d, &L)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(17, ws, ws_bytes, L);
     if (!c.ok()) return c.finish();
 
     cudaStream_t st = (cudaStream_t)stream;
+    {
+        const PanelPlan dp = df_plan(m, n, d.sms);
+        DfArgs a = df_args(m, n, A, lda, dp, ws);
+        a.Bout = B; a.ldbo = ldb; a.u1 = u1; a.v1 = v1; a.u2 = u2; a.v2 = v2; a.r = y;
+        a.spart = wsd(ws, L.off[1]);
+        bto_status e;
+        if (df_ready(form, DF_G1, a, st, &e)) {
+            if (e != BTO_OK || (e = df_launch(DF_G1, a, dp, st)) != BTO_OK) return e;
+            CombineJob jx = {x, n, a.spart, dp.lds, dp.NR, beta, nullptr, 0, 0, 0.0, z, 1.0};
+            if ((e = launch_combine(&jx, 1, st)) != BTO_OK) return e;
+            // w = alpha B x over the new B, last-written panels first (L2 reuse).
+            return df_gemv_n(m, n, alpha, B, ldb, x, 0.0, nullptr, w, wsd(ws, L.off[0]), dp, ws, 1, st);
+        }
+        if (form == BTO_FORM_DF && ws_layout(BTO_OP_GEMVER, BTO_FORM_FUSED, m, n, BTO_F64, d, &L) != BTO_OK)
+            return BTO_ERR_CUDA;
+    }
     const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_GEMVER, BTO_FORM_FUSED);
     PanelArgs a{};
     a.m = m; a.n = n; a.A = A; a.lda = lda; a.Bout = B; a.ldb = ldb;
@@ -270,4 +358,59 @@ extern "C" bto_status bto_gemver(int64_t m, int64_t n, double alpha, double beta
     if ((e = launch_panel(PM_Q, b, pl, st)) != BTO_OK) return e;
     CombineJob jw = {w, m, b.qpart, pl.ldq, pl.NC, alpha, nullptr, 0, 0, 0.0, nullptr, 0.0};
     return launch_combine(&jw, 1, st);
+}
+
+extern "C" bto_status bto_bicgk(int64_t m, int64_t n, const double* A, int64_t lda, const double* p,
+                                const double* r, double* q, double* s, void* ws, size_t ws_bytes,
+                                bto_stream_t stream) {
+    return run_bicgk(BTO_FORM_FUSED, m, n, A, lda, p, r, q, s, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_bicgk_df(int64_t m, int64_t n, const double* A, int64_t lda, const double* p,
+                                   const double* r, double* q, double* s, void* ws, size_t ws_bytes,
+                                   bto_stream_t stream) {
+    return run_bicgk(BTO_FORM_DF, m, n, A, lda, p, r, q, s, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_dgemv(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                                const double* x, double beta, const double* y, double* z, void* ws,
+                                size_t ws_bytes, bto_stream_t stream) {
+    return run_dgemv(BTO_FORM_FUSED, m, n, alpha, A, lda, x, beta, y, z, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_dgemv_df(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                                   const double* x, double beta, const double* y, double* z, void* ws,
+                                   size_t ws_bytes, bto_stream_t stream) {
+    return run_dgemv(BTO_FORM_DF, m, n, alpha, A, lda, x, beta, y, z, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_gesummv(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                                  double beta, const double* B, int64_t ldb, const double* x, double* y,
+                                  void* ws, size_t ws_bytes, bto_stream_t stream) {
+    return run_gesummv(BTO_FORM_FUSED, m, n, alpha, A, lda, beta, B, ldb, x, y, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_gesummv_df(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                                     double beta, const double* B, int64_t ldb, const double* x, double* y,
+                                     void* ws, size_t ws_bytes, bto_stream_t stream) {
+    return run_gesummv(BTO_FORM_DF, m, n, alpha, A, lda, beta, B, ldb, x, y, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_dgemvt(int64_t m, int64_t n, double alpha, double beta, const double* A,
+                                 int64_t lda, const double* y, const double* z, double* x, double* w,
+                                 void* ws, size_t ws_bytes, bto_stream_t stream) {
+    return run_dgemvt(BTO_FORM_FUSED, m, n, alpha, beta, A, lda, y, z, x, w, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_dgemvt_df(int64_t m, int64_t n, double alpha, double beta, const double* A,
+                                    int64_t lda, const double* y, const double* z, double* x, double* w,
+                                    void* ws, size_t ws_bytes, bto_stream_t stream) {
+    return run_dgemvt(BTO_FORM_DF, m, n, alpha, beta, A, lda, y, z, x, w, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_gemver(int64_t m, int64_t n, double alpha, double beta, const double* A,
+                                 int64_t lda, const double* u1, const double* v1, const double* u2,
+                                 const double* v2, const double* y, const double* z, double* B, int64_t ldb,
+                                 double* x, double* w, void* ws, size_t ws_bytes, bto_stream_t stream) {
+    return run_gemver(BTO_FORM_FUSED, m, n, alpha, beta, A, lda, u1, v1, u2, v2, y, z, B, ldb, x, w, ws,
+                      ws_bytes, stream);
+}
+extern "C" bto_status bto_gemver_df(int64_t m, int64_t n, double alpha, double beta, const double* A,
+                                    int64_t lda, const double* u1, const double* v1, const double* u2,
+                                    const double* v2, const double* y, const double* z, double* B, int64_t ldb,
+                                    double* x, double* w, void* ws, size_t ws_bytes, bto_stream_t stream) {
+    return run_gemver(BTO_FORM_DF, m, n, alpha, beta, A, lda, u1, v1, u2, v2, y, z, B, ldb, x, w, ws,
+                      ws_bytes, stream);
 }

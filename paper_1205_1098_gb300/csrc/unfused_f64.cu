@@ -39,7 +39,9 @@ __global__ void dger_kernel(int64_t m, int64_t n, const double* __restrict__ x,
     }
 }
 
-int egrid(int64_t n, int sms) {
+}  // namespace
+
+static int egrid(int64_t n, int sms) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, ceil_div(n, kThreads)));
 }
 
@@ -80,6 +82,8 @@ bto_status dcopy_mat(int64_t m, int64_t n, const double* A, int64_t lda, double*
     return BTO_OK;
 }
 
+namespace {
+
 // out = alpha A v (+ beta y if y != NULL): dgemv with trans = 'N'.
 bto_status dgemv_n(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
                    const double* v, double beta, const double* y, double* out, double* qpart,
@@ -115,11 +119,38 @@ struct Ctx {
     double* at(int k) const { return reinterpret_cast<double*>(w + L.off[k]); }
 };
 
-bool make_ctx(int op, int64_t m, int64_t n, void* ws, Ctx* c) {
+bool make_ctx(int op, int form, int64_t m, int64_t n, void* ws, Ctx* c) {
     if (!device_info(&c->d)) return false;
-    if (ws_layout(op, BTO_FORM_UNFUSED, m, n, BTO_F64, c->d, &c->L) != BTO_OK) return false;
+    if (ws_layout(op, form, m, n, BTO_F64, c->d, &c->L) != BTO_OK) return false;
     c->pl = panel_plan(m, n, c->d.sms, op, BTO_FORM_UNFUSED);
     c->w = static_cast<char*>(ws);
+    return true;
+}
+
+// The double-float form of an unfused sequence: each dgemv is a
+// double-float single-product sweep and its combine, on df_plan's tiles and
+// df_ws_layout's regions.  False (the FP64 form runs, on its own regions of
+// the same workspace) when a matrix does not suit the tensor-map copies.
+bool df_unfused_ready(int form, int op, int64_t m, int64_t n, const double* A, int64_t lda, const double* B,
+                      int64_t ldb, Ctx* X, cudaStream_t st, bto_status* e) {
+    *e = BTO_OK;
+    if (form != BTO_FORM_DF_UNFUSED) return false;
+    const PanelPlan dp = df_plan(m, n, X->d.sms);
+    DfArgs a = df_args(m, n, A, lda, dp, X->w);
+    bool ok = m > 0 && n > 0 && df_layout_ok(DF_Q, a);
+    if (ok && B) {
+        a.A = B; a.lda = ldb;
+        ok = df_layout_ok(DF_Q, a);
+    }
+    // The status word reads BTO_OK after either path.
+    *e = cudaMemsetAsync(X->w, 0, sizeof(int), st) == cudaSuccess ? BTO_OK : BTO_ERR_CUDA;
+    if (!ok) {
+        // FP64 regions of the same workspace.
+        if (*e == BTO_OK && ws_layout(op, BTO_FORM_UNFUSED, m, n, BTO_F64, X->d, &X->L) != BTO_OK)
+            *e = BTO_ERR_CUDA;
+        return false;
+    }
+    X->pl = dp;
     return true;
 }
 
@@ -130,7 +161,7 @@ bool make_ctx(int op, int64_t m, int64_t n, void* ws, Ctx* c) {
 
 using namespace bto;
 
-extern "C" bto_status bto_unfused_bicgk(int64_t m, int64_t n, const double* A, int64_t lda,
+static bto_status run_unfused_bicgk(int form, int64_t m, int64_t n, const double* A, int64_t lda,
                                         const double* p, const double* r, double* q, double* s,
                                         void* ws, size_t ws_bytes, bto_stream_t stream) {
     clear_invalid_arg();
@@ -145,17 +176,24 @@ extern "C" bto_status bto_unfused_bicgk(int64_t m, int64_t n, const double* A, i
     c.disjoint(8, s, vbytes(n), A, Ab); c.disjoint(8, s, vbytes(n), p, vbytes(n));
     c.disjoint(8, s, vbytes(n), r, vbytes(m));
     Ctx x;
-    if (c.ok() && !make_ctx(BTO_OP_BICGK, m, n, ws, &x)) return BTO_ERR_CUDA;
+    if (c.ok() && !make_ctx(BTO_OP_BICGK, form, m, n, ws, &x)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(9, ws, ws_bytes, x.L);
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
+    bto_status e;
+    if (df_unfused_ready(form, BTO_OP_BICGK, m, n, A, lda, nullptr, 0, &x, st, &e)) {
+        TRY(e);
+        TRY(df_gemv_n(m, n, 1.0, A, lda, p, 0.0, nullptr, q, x.at(0), x.pl, ws, 0, st));
+        return df_gemv_t(m, n, 1.0, A, lda, r, 0.0, nullptr, s, x.at(1), x.pl, ws, 0, st);
+    }
+    TRY(e);
     // dgemv('N', m, n, 1.0, A, lda, p, 1, 0.0, q, 1)
     TRY(dgemv_n(m, n, 1.0, A, lda, p, 0.0, nullptr, q, x.at(0), x.pl, st));
     // dgemv('T', m, n, 1.0, A, lda, r, 1, 0.0, s, 1)
     return dgemv_t(m, n, 1.0, A, lda, r, 0.0, nullptr, s, x.at(1), x.pl, st);
 }
 
-extern "C" bto_status bto_unfused_atax(int64_t m, int64_t n, double beta, const double* A,
+static bto_status run_unfused_atax(int form, int64_t m, int64_t n, double beta, const double* A,
                                        int64_t lda, const double* x, double* y, void* ws,
                                        size_t ws_bytes, bto_stream_t stream) {
     clear_invalid_arg();
@@ -167,17 +205,26 @@ extern "C" bto_status bto_unfused_atax(int64_t m, int64_t n, double beta, const 
     c.ptr(6, x, n > 0); c.ptr(7, y, n > 0);
     c.disjoint(7, y, vbytes(n), A, Ab); c.disjoint(7, y, vbytes(n), x, vbytes(n));
     Ctx X;
-    if (c.ok() && !make_ctx(BTO_OP_ATAX, m, n, ws, &X)) return BTO_ERR_CUDA;
+    if (c.ok() && !make_ctx(BTO_OP_ATAX, form, m, n, ws, &X)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(8, ws, ws_bytes, X.L);
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
+    bto_status e;
+    if (df_unfused_ready(form, BTO_OP_ATAX, m, n, A, lda, nullptr, 0, &X, st, &e)) {
+        TRY(e);
+        double* t = X.at(0);
+        TRY(df_gemv_n(m, n, 1.0, A, lda, x, 0.0, nullptr, t, X.at(1), X.pl, ws, 0, st));   // t0 = A x
+        TRY(df_gemv_t(m, n, 1.0, A, lda, t, 0.0, nullptr, y, X.at(2), X.pl, ws, 0, st));   // t1 = A^T t0
+        return dscal(n, beta, y, X.d.sms, st);                                              // y = t1 beta
+    }
+    TRY(e);
     double* t = X.at(0);
     TRY(dgemv_n(m, n, 1.0, A, lda, x, 0.0, nullptr, t, X.at(1), X.pl, st));    // t0 = A x
     TRY(dgemv_t(m, n, 1.0, A, lda, t, 0.0, nullptr, y, X.at(2), X.pl, st));    // t1 = A^T t0
     return dscal(n, beta, y, X.d.sms, st);                                       // y = t1 beta
 }
 
-extern "C" bto_status bto_unfused_gemver(int64_t m, int64_t n, double alpha, double beta,
+static bto_status run_unfused_gemver(int form, int64_t m, int64_t n, double alpha, double beta,
                                          const double* A, int64_t lda, const double* u1,
                                          const double* v1, const double* u2, const double* v2,
                                          const double* y, const double* z, double* B, int64_t ldb,
@@ -203,11 +250,22 @@ extern "C" bto_status bto_unfused_gemver(int64_t m, int64_t n, double alpha, dou
     for (int k = 0; k < 6; k++) c.disjoint(16, w, vbytes(m), ins[k], inb[k]);
     c.disjoint(16, w, vbytes(m), x, vbytes(n));
     Ctx X;
-    if (c.ok() && !make_ctx(BTO_OP_GEMVER, m, n, ws, &X)) return BTO_ERR_CUDA;
+    if (c.ok() && !make_ctx(BTO_OP_GEMVER, form, m, n, ws, &X)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(17, ws, ws_bytes, X.L);
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
     const int sms = X.d.sms;
+    bto_status e;
+    if (df_unfused_ready(form, BTO_OP_GEMVER, m, n, B, ldb, nullptr, 0, &X, st, &e)) {
+        TRY(e);
+        TRY(dcopy_mat(m, n, A, lda, B, ldb, sms, st));                 // B = A
+        TRY(dger(m, n, u1, v1, B, ldb, sms, st));                      // B += u1 v1^T
+        TRY(dger(m, n, u2, v2, B, ldb, sms, st));                      // B += u2 v2^T
+        TRY(dcopy(n, z, x, sms, st));                                  // x = z
+        TRY(df_gemv_t(m, n, beta, B, ldb, y, 1.0, x, x, X.at(1), X.pl, ws, 0, st));      // x = beta B^T y + x
+        return df_gemv_n(m, n, alpha, B, ldb, x, 0.0, nullptr, w, X.at(0), X.pl, ws, 0, st);   // w = alpha B x
+    }
+    TRY(e);
     TRY(dcopy_mat(m, n, A, lda, B, ldb, sms, st));                 // B = A
     TRY(dger(m, n, u1, v1, B, ldb, sms, st));                      // B += u1 v1^T
     TRY(dger(m, n, u2, v2, B, ldb, sms, st));                      // B += u2 v2^T
@@ -216,7 +274,7 @@ extern "C" bto_status bto_unfused_gemver(int64_t m, int64_t n, double alpha, dou
     return dgemv_n(m, n, alpha, B, ldb, x, 0.0, nullptr, w, X.at(0), X.pl, st);   // w = alpha B x
 }
 
-extern "C" bto_status bto_unfused_gesummv(int64_t m, int64_t n, double alpha, const double* A,
+static bto_status run_unfused_gesummv(int form, int64_t m, int64_t n, double alpha, const double* A,
                                           int64_t lda, double beta, const double* B, int64_t ldb,
                                           const double* x, double* y, void* ws, size_t ws_bytes,
                                           bto_stream_t stream) {
@@ -231,15 +289,22 @@ extern "C" bto_status bto_unfused_gesummv(int64_t m, int64_t n, double alpha, co
     c.disjoint(10, y, vbytes(m), A, Ab); c.disjoint(10, y, vbytes(m), B, Bb);
     c.disjoint(10, y, vbytes(m), x, vbytes(n));
     Ctx X;
-    if (c.ok() && !make_ctx(BTO_OP_GESUMMV, m, n, ws, &X)) return BTO_ERR_CUDA;
+    if (c.ok() && !make_ctx(BTO_OP_GESUMMV, form, m, n, ws, &X)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(11, ws, ws_bytes, X.L);
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
+    bto_status e;
+    if (df_unfused_ready(form, BTO_OP_GESUMMV, m, n, A, lda, B, ldb, &X, st, &e)) {
+        TRY(e);
+        TRY(df_gemv_n(m, n, alpha, A, lda, x, 0.0, nullptr, y, X.at(0), X.pl, ws, 0, st));   // y = alpha A x
+        return df_gemv_n(m, n, beta, B, ldb, x, 1.0, y, y, X.at(0), X.pl, ws, 0, st);        // y = beta B x + y
+    }
+    TRY(e);
     TRY(dgemv_n(m, n, alpha, A, lda, x, 0.0, nullptr, y, X.at(0), X.pl, st));   // y = alpha A x
     return dgemv_n(m, n, beta, B, ldb, x, 1.0, y, y, X.at(0), X.pl, st);         // y = beta B x + y
 }
 
-extern "C" bto_status bto_unfused_dgemv(int64_t m, int64_t n, double alpha, const double* A,
+static bto_status run_unfused_dgemv(int form, int64_t m, int64_t n, double alpha, const double* A,
                                         int64_t lda, const double* x, double beta,
                                         const double* y, double* z, void* ws, size_t ws_bytes,
                                         bto_stream_t stream) {
@@ -253,15 +318,22 @@ extern "C" bto_status bto_unfused_dgemv(int64_t m, int64_t n, double alpha, cons
     c.disjoint(9, z, vbytes(m), A, Ab); c.disjoint(9, z, vbytes(m), x, vbytes(n));
     c.disjoint(9, z, vbytes(m), y, vbytes(m));
     Ctx X;
-    if (c.ok() && !make_ctx(BTO_OP_DGEMV, m, n, ws, &X)) return BTO_ERR_CUDA;
+    if (c.ok() && !make_ctx(BTO_OP_DGEMV, form, m, n, ws, &X)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(10, ws, ws_bytes, X.L);
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
+    bto_status e;
+    if (df_unfused_ready(form, BTO_OP_DGEMV, m, n, A, lda, nullptr, 0, &X, st, &e)) {
+        TRY(e);
+        TRY(dcopy(m, y, z, X.d.sms, st));                                                         // z = y
+        return df_gemv_n(m, n, alpha, A, lda, x, beta, z, z, X.at(0), X.pl, ws, 0, st);          // z = alpha A x + beta z
+    }
+    TRY(e);
     TRY(dcopy(m, y, z, X.d.sms, st));                                               // z = y
     return dgemv_n(m, n, alpha, A, lda, x, beta, z, z, X.at(0), X.pl, st);          // z = alpha A x + beta z
 }
 
-extern "C" bto_status bto_unfused_dgemvt(int64_t m, int64_t n, double alpha, double beta,
+static bto_status run_unfused_dgemvt(int form, int64_t m, int64_t n, double alpha, double beta,
                                          const double* A, int64_t lda, const double* y,
                                          const double* z, double* x, double* w, void* ws,
                                          size_t ws_bytes, bto_stream_t stream) {
@@ -277,11 +349,19 @@ extern "C" bto_status bto_unfused_dgemvt(int64_t m, int64_t n, double alpha, dou
     c.disjoint(10, w, vbytes(m), A, Ab); c.disjoint(10, w, vbytes(m), y, vbytes(m));
     c.disjoint(10, w, vbytes(m), z, vbytes(n)); c.disjoint(10, w, vbytes(m), x, vbytes(n));
     Ctx X;
-    if (c.ok() && !make_ctx(BTO_OP_DGEMVT, m, n, ws, &X)) return BTO_ERR_CUDA;
+    if (c.ok() && !make_ctx(BTO_OP_DGEMVT, form, m, n, ws, &X)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(11, ws, ws_bytes, X.L);
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
     const int sms = X.d.sms;
+    bto_status e;
+    if (df_unfused_ready(form, BTO_OP_DGEMVT, m, n, A, lda, nullptr, 0, &X, st, &e)) {
+        TRY(e);
+        TRY(dcopy(n, z, x, sms, st));                                                           // x = z
+        TRY(df_gemv_t(m, n, beta, A, lda, y, 1.0, x, x, X.at(1), X.pl, ws, 0, st));            // x = beta A^T y + x
+        return df_gemv_n(m, n, alpha, A, lda, x, 0.0, nullptr, w, X.at(0), X.pl, ws, 0, st);   // w = alpha A x
+    }
+    TRY(e);
     TRY(dcopy(n, z, x, sms, st));                                                  // x = z
     TRY(dgemv_t(m, n, beta, A, lda, y, 1.0, x, x, X.at(1), X.pl, st));            // x = beta A^T y + x
     return dgemv_n(m, n, alpha, A, lda, x, 0.0, nullptr, w, X.at(0), X.pl, st);   // w = alpha A x
@@ -300,7 +380,7 @@ extern "C" bto_status bto_unfused_axpydot(int64_t n, double alpha, const double*
     c.disjoint(7, r, 8, w, vbytes(n)); c.disjoint(7, r, 8, v, vbytes(n));
     c.disjoint(7, r, 8, u, vbytes(n)); c.disjoint(7, r, 8, z, vbytes(n));
     Ctx X;
-    if (c.ok() && !make_ctx(BTO_OP_AXPYDOT, 0, n, ws, &X)) return BTO_ERR_CUDA;
+    if (c.ok() && !make_ctx(BTO_OP_AXPYDOT, BTO_FORM_UNFUSED, 0, n, ws, &X)) return BTO_ERR_CUDA;
     if (c.ok()) c.ws(8, ws, ws_bytes, X.L);
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
@@ -344,4 +424,71 @@ extern "C" bto_status bto_unfused_vadd(int64_t n, const double* w, const double*
     TRY(dcopy(n, w, x, d.sms, st));            // x = w
     TRY(daxpy(n, 1.0, y, x, d.sms, st));       // x = y + x
     return daxpy(n, 1.0, z, x, d.sms, st);     // x = z + x
+}
+
+extern "C" bto_status bto_unfused_bicgk(int64_t m, int64_t n, const double* A, int64_t lda, const double* p,
+                                        const double* r, double* q, double* s, void* ws, size_t ws_bytes,
+                                        bto_stream_t stream) {
+    return run_unfused_bicgk(BTO_FORM_UNFUSED, m, n, A, lda, p, r, q, s, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_unfused_bicgk_df(int64_t m, int64_t n, const double* A, int64_t lda, const double* p,
+                                           const double* r, double* q, double* s, void* ws, size_t ws_bytes,
+                                           bto_stream_t stream) {
+    return run_unfused_bicgk(BTO_FORM_DF_UNFUSED, m, n, A, lda, p, r, q, s, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_unfused_atax(int64_t m, int64_t n, double beta, const double* A, int64_t lda,
+                                       const double* x, double* y, void* ws, size_t ws_bytes, bto_stream_t stream) {
+    return run_unfused_atax(BTO_FORM_UNFUSED, m, n, beta, A, lda, x, y, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_unfused_atax_df(int64_t m, int64_t n, double beta, const double* A, int64_t lda,
+                                          const double* x, double* y, void* ws, size_t ws_bytes,
+                                          bto_stream_t stream) {
+    return run_unfused_atax(BTO_FORM_DF_UNFUSED, m, n, beta, A, lda, x, y, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_unfused_gemver(int64_t m, int64_t n, double alpha, double beta, const double* A,
+                                         int64_t lda, const double* u1, const double* v1, const double* u2,
+                                         const double* v2, const double* y, const double* z, double* B,
+                                         int64_t ldb, double* x, double* w, void* ws, size_t ws_bytes,
+                                         bto_stream_t stream) {
+    return run_unfused_gemver(BTO_FORM_UNFUSED, m, n, alpha, beta, A, lda, u1, v1, u2, v2, y, z, B, ldb, x, w,
+                              ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_unfused_gemver_df(int64_t m, int64_t n, double alpha, double beta, const double* A,
+                                            int64_t lda, const double* u1, const double* v1, const double* u2,
+                                            const double* v2, const double* y, const double* z, double* B,
+                                            int64_t ldb, double* x, double* w, void* ws, size_t ws_bytes,
+                                            bto_stream_t stream) {
+    return run_unfused_gemver(BTO_FORM_DF_UNFUSED, m, n, alpha, beta, A, lda, u1, v1, u2, v2, y, z, B, ldb, x,
+                              w, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_unfused_gesummv(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                                          double beta, const double* B, int64_t ldb, const double* x, double* y,
+                                          void* ws, size_t ws_bytes, bto_stream_t stream) {
+    return run_unfused_gesummv(BTO_FORM_UNFUSED, m, n, alpha, A, lda, beta, B, ldb, x, y, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_unfused_gesummv_df(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                                             double beta, const double* B, int64_t ldb, const double* x,
+                                             double* y, void* ws, size_t ws_bytes, bto_stream_t stream) {
+    return run_unfused_gesummv(BTO_FORM_DF_UNFUSED, m, n, alpha, A, lda, beta, B, ldb, x, y, ws, ws_bytes,
+                               stream);
+}
+extern "C" bto_status bto_unfused_dgemv(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                                        const double* x, double beta, const double* y, double* z, void* ws,
+                                        size_t ws_bytes, bto_stream_t stream) {
+    return run_unfused_dgemv(BTO_FORM_UNFUSED, m, n, alpha, A, lda, x, beta, y, z, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_unfused_dgemv_df(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
+                                           const double* x, double beta, const double* y, double* z, void* ws,
+                                           size_t ws_bytes, bto_stream_t stream) {
+    return run_unfused_dgemv(BTO_FORM_DF_UNFUSED, m, n, alpha, A, lda, x, beta, y, z, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_unfused_dgemvt(int64_t m, int64_t n, double alpha, double beta, const double* A,
+                                         int64_t lda, const double* y, const double* z, double* x, double* w,
+                                         void* ws, size_t ws_bytes, bto_stream_t stream) {
+    return run_unfused_dgemvt(BTO_FORM_UNFUSED, m, n, alpha, beta, A, lda, y, z, x, w, ws, ws_bytes, stream);
+}
+extern "C" bto_status bto_unfused_dgemvt_df(int64_t m, int64_t n, double alpha, double beta, const double* A,
+                                            int64_t lda, const double* y, const double* z, double* x, double* w,
+                                            void* ws, size_t ws_bytes, bto_stream_t stream) {
+    return run_unfused_dgemvt(BTO_FORM_DF_UNFUSED, m, n, alpha, beta, A, lda, y, z, x, w, ws, ws_bytes, stream);
 }

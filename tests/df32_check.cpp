@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdint>
 #include <cmath>
+#include <cstring>
 #include "df32.cuh"
 
 using namespace bto::df;
@@ -83,6 +84,66 @@ int main() {
         const double err = std::fabs((double)((quad)to_f64(acc) - exact));
         // Relative to the sum of magnitudes (the condition-free bound): within 1e-13.
         if (err > 1e-13 * (double)mag) return fail("dot product error", err, (double)mag);
+    }
+    // The sweep split: hi + lo is x with its 6 lowest fraction bits cleared
+    // (47 significant bits), exactly, over 2^-100 <= |x| < 2^128 and for zero.
+    for (int i = 0; i < 2000000; i++) {
+        const int ex = -100 + (int)(next_u64() % 228);                 // -100 .. 127
+        double x = std::ldexp(1.0 + unit(), ex);
+        if (next_u64() & 1) x = -x;
+        float hi, lo;
+        split_double(x, hi, lo);
+        const uint64_t kept = bits_of(x) & ~0x3full;
+        double want;
+        std::memcpy(&want, &kept, sizeof want);
+        if ((double)hi + (double)lo != want) return fail("sweep split is not x truncated to 47 bits", x, lo);
+        if (std::fabs(x - want) >= std::ldexp(std::fabs(x), -46)) return fail("sweep split error", x, want);
+        if (lo != 0.0f && std::fabs((double)lo) >= std::ldexp(std::fabs((double)hi), -23))
+            return fail("sweep split lo not below hi's last bit", hi, lo);
+        if ((std::signbit(hi) != std::signbit(x)) || (lo != 0.0f && std::signbit(lo) != std::signbit(x)))
+            return fail("sweep split sign", x, lo);
+    }
+    for (int i = 0; i < 200000; i++) {
+        const float f = (float)((unit() - 0.5) * std::ldexp(1.0, (int)(next_u64() % 60) - 30));
+        float hi, lo;
+        split_double((double)f, hi, lo);
+        if (hi != f || lo != 0.0f) return fail("sweep split: FP32 value not exact", f, lo);
+        const double k = (double)(next_u64() >> 17);                   // below 2^47
+        split_double(next_u64() & 1 ? -k : k, hi, lo);
+        if (std::fabs((double)hi + (double)lo) != k) return fail("sweep split: integer below 2^47 not exact", k, lo);
+    }
+    {
+        float hi, lo;
+        split_double(0.0, hi, lo);
+        if (hi != 0.0f || lo != 0.0f || std::signbit(hi)) return fail("sweep split of +0", hi, lo);
+        split_double(-0.0, hi, lo);
+        if (hi != 0.0f || lo != 0.0f || !std::signbit(hi)) return fail("sweep split of -0", hi, lo);
+    }
+    // FP64 subnormals whose high word is zero apart from the sign: near zero.
+    for (int i = 0; i < 200000; i++) {
+        const uint64_t u = (next_u64() & 0xffffffffull) | ((next_u64() & 1) << 63);
+        double x;
+        std::memcpy(&x, &u, sizeof x);
+        float hi, lo;
+        split_double(x, hi, lo);
+        if (!(std::fabs((double)hi) + std::fabs((double)lo) < std::ldexp(1.0, -145)))
+            return fail("sweep split of a small subnormal is not near zero", x, hi);
+    }
+    // The operating ranges are inside the split's valid range.
+    if (kMatLo < (1023u - 100u) << 20 || kMatHi > (1023u + 128u) << 20 || kVecLo < kMatLo || kVecHi > kMatHi)
+        return fail("operating range constants", (double)kMatLo, (double)kMatHi);
+    // FP32 -> FP64 words: exact for normal values and zero; subnormals to zero.
+    for (int i = 0; i < 2000000; i++) {
+        const uint32_t u = (uint32_t)next_u64();
+        float f;
+        std::memcpy(&f, &u, sizeof f);
+        if (!std::isfinite(f)) continue;
+        uint32_t hw, lw;
+        f32_to_f64_words(f, hw, lw);
+        const double d = f64_of_words(hw, lw);
+        const bool sub = (u & 0x7fffffffu) < 0x00800000u;
+        if (sub ? (d != 0.0 || std::signbit(d) != std::signbit(f)) : d != (double)f)
+            return fail("f32_to_f64_words", f, d);
     }
     std::printf("ok\n");
     return 0;

@@ -10,6 +10,16 @@ from gpu_util import Out, dev, p, ws, sync
 
 KINDS = {"uniform": synth.KIND_UNIFORM, "integer": synth.KIND_INTEGER}
 
+# Form name -> (entry point name pattern, workspace form code).
+FORMS = {"fused": ("bto_%s", bto.BTO_FORM_FUSED), "unfused": ("bto_unfused_%s", bto.BTO_FORM_UNFUSED),
+         "df": ("bto_%s_df", bto.BTO_FORM_DF), "df_unfused": ("bto_unfused_%s_df", bto.BTO_FORM_DF_UNFUSED)}
+
+
+def entry(kernel, form):
+    """The entry point of `kernel` in `form` and its workspace form code."""
+    name, code = FORMS[form]
+    return getattr(bto, name % kernel), code
+
 
 def _v(seed, aid, n, kind):
     return synth.vector(seed, aid, n, kind)
@@ -24,8 +34,8 @@ def run_bicgk(m, n, lda, kind, seed=1, form="fused", alpha=None, beta=None):
     pv, rv = _v(seed, 1, n, kind), _v(seed, 2, m, kind)
     dA, dp, dr = dev(A), dev(pv), dev(rv)
     q, s = Out(m), Out(n)
-    w, nb = ws("bicgk", 0 if form == "fused" else 1, m, n)
-    f = bto.bto_bicgk if form == "fused" else bto.bto_unfused_bicgk
+    f, code = entry("bicgk", form)
+    w, nb = ws("bicgk", code, m, n)
     f(m, n, p(dA), lda, p(dp), p(dr), q.ptr(), s.ptr(), p(w), nb, None)
     sync()
     qo, so = O.bicgk(m, n, A, pv, rv)
@@ -37,11 +47,11 @@ def run_atax(m, n, lda, kind, seed=1, form="fused", alpha=None, beta=1.5):
     xv = _v(seed, 1, n, kind)
     dA, dx = dev(A), dev(xv)
     y = Out(n)
-    w, nb = ws("atax", 0 if form == "fused" else 1, m, n)
-    f = bto.bto_atax if form == "fused" else bto.bto_unfused_atax
+    f, code = entry("atax", form)
+    w, nb = ws("atax", code, m, n)
     f(m, n, beta, p(dA), lda, p(dx), y.ptr(), p(w), nb, None)
     sync()
-    if form == "fused" and m > 0 and n > 0:
+    if form != "unfused" and m > 0 and n > 0:
         assert bto.bto_device_status(p(w)) == 0
     return {"y": (y.host(), O.atax(m, n, beta, A, xv))}
 
@@ -56,8 +66,8 @@ def run_gemver(m, n, lda, kind, seed=1, form="fused", alpha=1.5, beta=1.2, ldb=N
     d = [dev(a) for a in (u1, v1, u2, v2, yv, zv)]
     B = Out(ldb * n if n else 0)
     x, w_ = Out(n), Out(m)
-    wk, nb = ws("gemver", 0 if form == "fused" else 1, m, n)
-    f = bto.bto_gemver if form == "fused" else bto.bto_unfused_gemver
+    f, code = entry("gemver", form)
+    wk, nb = ws("gemver", code, m, n)
     f(m, n, alpha, beta, p(dA), lda, *[p(t) for t in d], B.ptr(), ldb, x.ptr(), w_.ptr(), p(wk), nb, None)
     sync()
     Bo, xo, wo = O.gemver(m, n, alpha, beta, A, u1, v1, u2, v2, yv, zv)
@@ -71,8 +81,8 @@ def run_gesummv(m, n, lda, kind, seed=1, form="fused", alpha=1.5, beta=-0.75):
     xv = _v(seed, 2, n, kind)
     dA, dB, dx = dev(A), dev(Bm), dev(xv)
     y = Out(m)
-    w, nb = ws("gesummv", 0 if form == "fused" else 1, m, n)
-    f = bto.bto_gesummv if form == "fused" else bto.bto_unfused_gesummv
+    f, code = entry("gesummv", form)
+    w, nb = ws("gesummv", code, m, n)
     f(m, n, alpha, p(dA), lda, beta, p(dB), lda, p(dx), y.ptr(), p(w), nb, None)
     sync()
     return {"y": (y.host(), O.gesummv(m, n, alpha, A, beta, Bm, xv))}
@@ -83,8 +93,8 @@ def run_dgemv(m, n, lda, kind, seed=1, form="fused", alpha=1.5, beta=-0.5):
     xv, yv = _v(seed, 1, n, kind), _v(seed, 2, m, kind)
     dA, dx, dy = dev(A), dev(xv), dev(yv)
     z = Out(m)
-    w, nb = ws("dgemv", 0 if form == "fused" else 1, m, n)
-    f = bto.bto_dgemv if form == "fused" else bto.bto_unfused_dgemv
+    f, code = entry("dgemv", form)
+    w, nb = ws("dgemv", code, m, n)
     f(m, n, alpha, p(dA), lda, p(dx), beta, p(dy), z.ptr(), p(w), nb, None)
     sync()
     return {"z": (z.host(), O.dgemv(m, n, alpha, A, xv, beta, yv))}
@@ -95,8 +105,8 @@ def run_dgemvt(m, n, lda, kind, seed=1, form="fused", alpha=1.5, beta=1.2):
     yv, zv = _v(seed, 1, m, kind), _v(seed, 2, n, kind)
     dA, dy, dz = dev(A), dev(yv), dev(zv)
     x, w_ = Out(n), Out(m)
-    w, nb = ws("dgemvt", 0 if form == "fused" else 1, m, n)
-    f = bto.bto_dgemvt if form == "fused" else bto.bto_unfused_dgemvt
+    f, code = entry("dgemvt", form)
+    w, nb = ws("dgemvt", code, m, n)
     f(m, n, alpha, beta, p(dA), lda, p(dy), p(dz), x.ptr(), w_.ptr(), p(w), nb, None)
     sync()
     xo, wo = O.dgemvt(m, n, alpha, beta, A, yv, zv)
@@ -107,8 +117,8 @@ def run_axpydot(n, kind, seed=1, form="fused", alpha=0.75, compensated=False):
     wv, vv, uv = (_v(seed, k, n, kind) for k in (0, 1, 2))
     dw, dv, du = dev(wv), dev(vv), dev(uv)
     z, r = Out(n), Out(1)
-    w, nb = ws("axpydot", 0 if form == "fused" else 1, 0, n)
-    f = bto.bto_axpydot if form == "fused" else bto.bto_unfused_axpydot
+    f, code = entry("axpydot", form)
+    w, nb = ws("axpydot", code, 0, n)
     f(n, alpha, p(dw), p(dv), p(du), z.ptr(), r.ptr(), p(w), nb, None)
     sync()
     zo, ro = O.axpydot(n, alpha, wv, vv, uv, compensated=compensated)

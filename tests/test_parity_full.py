@@ -1,5 +1,6 @@
 """Parity at the benchmark's full sizes (n = 16384 matrices, 2^26 vectors),
-in the launch configuration the benchmark times.  Matrices are generated on
+in the launch configuration the benchmark times, for the FP64 form and the
+double-float form of the matrix sequences.  Matrices are generated on
 the device by the seeded fill; the oracle recomputes sampled outputs from
 the same generator's rows and columns on the host, by running on the
 sub-problem that determines each sampled output exactly."""
@@ -10,6 +11,7 @@ import torch
 import oracle as O
 import paper_1205_1098_gb300 as bto
 import synth
+from f64_cases import entry
 from gpu_util import TOL64, Out, dev, p, relerr, sync, ws
 
 pytestmark = pytest.mark.gpu
@@ -17,6 +19,11 @@ pytestmark = pytest.mark.gpu
 N = 16384
 SEED = 1
 NSAMP = 48
+FORMS = ["fused", "df"]
+# GEMVER's B: the FP64 form rounds A + u1 v1^T + u2 v2^T twice like the
+# oracle (a few ulps apart); the double-float form keeps 47 bits of A and
+# rounds its hi + lo sum once (within 2^-45 relative per element).
+B_TOL = {"fused": 1e-15, "df": 1e-13}
 
 
 @pytest.fixture(scope="module")
@@ -45,11 +52,12 @@ def _cols(aid, cols):
     return synth.matrix_cols(SEED, aid, N, N, cols)
 
 
-def test_bicgk_full(A):
+@pytest.mark.parametrize("form", FORMS)
+def test_bicgk_full(A, form):
     pv, rv = synth.vector(SEED, 1, N), synth.vector(SEED, 2, N)
     q, s = Out(N), Out(N)
-    wk, nb = ws("bicgk", 0, N, N)
-    bto.bto_bicgk(N, N, p(A), N, dev(pv), dev(rv), q.ptr(), s.ptr(), p(wk), nb, None)
+    wk, nb = ws("bicgk", entry("bicgk", form)[1], N, N)
+    entry("bicgk", form)[0](N, N, p(A), N, dev(pv), dev(rv), q.ptr(), s.ptr(), p(wk), nb, None)
     sync()
     qh, sh = q.host(), s.host()
     I = _samples(11, N)
@@ -63,13 +71,14 @@ def test_bicgk_full(A):
     assert abs(np.dot(rv, qh) - np.dot(sh, pv)) < 1e-12 * scale
 
 
-def test_gesummv_full(A):
+@pytest.mark.parametrize("form", FORMS)
+def test_gesummv_full(A, form):
     Bm = torch.empty(N * N, dtype=torch.float64, device="cuda")
     bto.bto_fill_f64(SEED, 1, 0, N, N, 0, p(Bm), N, None)
     xv = synth.vector(SEED, 2, N)
     y = Out(N)
-    wk, nb = ws("gesummv", 0, N, N)
-    bto.bto_gesummv(N, N, 1.5, p(A), N, -0.75, p(Bm), N, dev(xv), y.ptr(), p(wk), nb, None)
+    wk, nb = ws("gesummv", entry("gesummv", form)[1], N, N)
+    entry("gesummv", form)[0](N, N, 1.5, p(A), N, -0.75, p(Bm), N, dev(xv), y.ptr(), p(wk), nb, None)
     sync()
     del Bm
     I = _samples(12, N)
@@ -78,11 +87,12 @@ def test_gesummv_full(A):
     assert relerr(y.host()[I], yo) < TOL64
 
 
-def test_dgemv_full(A):
+@pytest.mark.parametrize("form", FORMS)
+def test_dgemv_full(A, form):
     xv, yv = synth.vector(SEED, 1, N), synth.vector(SEED, 2, N)
     z = Out(N)
-    wk, nb = ws("dgemv", 0, N, N)
-    bto.bto_dgemv(N, N, 1.5, p(A), N, dev(xv), -0.5, dev(yv), z.ptr(), p(wk), nb, None)
+    wk, nb = ws("dgemv", entry("dgemv", form)[1], N, N)
+    entry("dgemv", form)[0](N, N, 1.5, p(A), N, dev(xv), -0.5, dev(yv), z.ptr(), p(wk), nb, None)
     sync()
     I = _samples(13, N)
     R = _rows(0, I)
@@ -95,11 +105,12 @@ def _gemver_vectors():
     return {k: synth.vector(SEED, ids[k], N) for k in ("u1", "v1", "u2", "v2", "y", "z")}
 
 
-def test_gemver_full_dense(A):
+@pytest.mark.parametrize("form", FORMS)
+def test_gemver_full_dense(A, form):
     v = _gemver_vectors()
     B, x, w = Out(N * N), Out(N), Out(N)
-    wk, nb = ws("gemver", 0, N, N)
-    bto.bto_gemver(N, N, 1.5, 1.2, p(A), N, *[dev(v[k]) for k in ("u1", "v1", "u2", "v2", "y", "z")],
+    wk, nb = ws("gemver", entry("gemver", form)[1], N, N)
+    entry("gemver", form)[0](N, N, 1.5, 1.2, p(A), N, *[dev(v[k]) for k in ("u1", "v1", "u2", "v2", "y", "z")],
                    B.ptr(), N, x.ptr(), w.ptr(), p(wk), nb, None)
     sync()
     J = _samples(14, N, 24)
@@ -110,13 +121,14 @@ def test_gemver_full_dense(A):
     for k, j in enumerate(J):
         Bo, xo, _ = O.gemver(N, 1, 1.5, 1.2, C[:, k:k + 1], v["u1"], v["v1"][j:j + 1], v["u2"],
                              v["v2"][j:j + 1], v["y"], v["z"][j:j + 1])
-        assert relerr(Bt[j].cpu().numpy(), Bo[:, 0]) < 1e-15
+        assert relerr(Bt[j].cpu().numpy(), Bo[:, 0]) < B_TOL[form]
         xs.append(xh[j]); xref.append(xo[0])
     assert relerr(xs, xref) < TOL64
     del B
 
 
-def test_gemver_full_sparse_y(A):
+@pytest.mark.parametrize("form", FORMS)
+def test_gemver_full_sparse_y(A, form):
     # With a single non-zero y_k, x = beta B_k,: y_k + z needs row k of B only,
     # and w_i = alpha B_i,: x needs row i: the oracle on the rows {k} U I is exact.
     v = _gemver_vectors()
@@ -124,8 +136,8 @@ def test_gemver_full_sparse_y(A):
     yv = np.zeros(N)
     yv[k0] = v["y"][k0]
     B, x, w = Out(N * N), Out(N), Out(N)
-    wk, nb = ws("gemver", 0, N, N)
-    bto.bto_gemver(N, N, 1.5, 1.2, p(A), N, dev(v["u1"]), dev(v["v1"]), dev(v["u2"]),
+    wk, nb = ws("gemver", entry("gemver", form)[1], N, N)
+    entry("gemver", form)[0](N, N, 1.5, 1.2, p(A), N, dev(v["u1"]), dev(v["v1"]), dev(v["u2"]),
                    dev(v["v2"]), dev(yv), dev(v["z"]), B.ptr(), N, x.ptr(), w.ptr(),
                    p(wk), nb, None)
     sync()
@@ -139,14 +151,15 @@ def test_gemver_full_sparse_y(A):
     assert relerr(w.host()[I], wo) < TOL64
 
 
-def test_dgemvt_full(A):
+@pytest.mark.parametrize("form", FORMS)
+def test_dgemvt_full(A, form):
     k0 = 777
     yv = np.zeros(N)
     yv[k0] = synth.vector(SEED, 1, N)[k0]
     zv = synth.vector(SEED, 2, N)
     x, w = Out(N), Out(N)
-    wk, nb = ws("dgemvt", 0, N, N)
-    bto.bto_dgemvt(N, N, 1.5, 1.2, p(A), N, dev(yv), dev(zv), x.ptr(), w.ptr(), p(wk), nb, None)
+    wk, nb = ws("dgemvt", entry("dgemvt", form)[1], N, N)
+    entry("dgemvt", form)[0](N, N, 1.5, 1.2, p(A), N, dev(yv), dev(zv), x.ptr(), w.ptr(), p(wk), nb, None)
     sync()
     I = np.concatenate([[k0], _samples(16, N, 24)])
     sub = np.asfortranarray(_rows(0, I))
@@ -155,7 +168,7 @@ def test_dgemvt_full(A):
     # dense y: x_j needs column j only
     yd = synth.vector(SEED, 1, N)
     x2, w2 = Out(N), Out(N)
-    bto.bto_dgemvt(N, N, 1.5, 1.2, p(A), N, dev(yd), dev(zv), x2.ptr(), w2.ptr(), p(wk), nb, None)
+    entry("dgemvt", form)[0](N, N, 1.5, 1.2, p(A), N, dev(yd), dev(zv), x2.ptr(), w2.ptr(), p(wk), nb, None)
     sync()
     J = _samples(17, N, 24)
     C = _cols(0, J)
@@ -163,15 +176,16 @@ def test_dgemvt_full(A):
     assert relerr(x2.host()[J], xo2) < TOL64
 
 
-def test_atax_full(A):
+@pytest.mark.parametrize("form", FORMS)
+def test_atax_full(A, form):
     # Sparse x (4 non-zeros at K): t = A[:, K] x_K, y_j = beta A[:, j]^T t; the
     # oracle on the columns K U {j} gives y_j exactly.
     K = np.array([3, 4000, 9001, 16383])
     xv = np.zeros(N)
     xv[K] = synth.vector(SEED, 1, N)[K]
     y = Out(N)
-    wk, nb = ws("atax", 0, N, N)
-    bto.bto_atax(N, N, 1.5, p(A), N, dev(xv), y.ptr(), p(wk), nb, None)
+    wk, nb = ws("atax", entry("atax", form)[1], N, N)
+    entry("atax", form)[0](N, N, 1.5, p(A), N, dev(xv), y.ptr(), p(wk), nb, None)
     assert bto.bto_device_status(p(wk)) == 0
     yh = y.host()
     J = _samples(18, N, 32)
@@ -186,9 +200,10 @@ def test_atax_full(A):
     # dense x: the unfused form reads A twice; both forms must agree
     xd = synth.vector(SEED, 1, N)
     y1, y2 = Out(N), Out(N)
-    bto.bto_atax(N, N, 1.0, p(A), N, dev(xd), y1.ptr(), p(wk), nb, None)
-    wk2, nb2 = ws("atax", 1, N, N)
-    bto.bto_unfused_atax(N, N, 1.0, p(A), N, dev(xd), y2.ptr(), p(wk2), nb2, None)
+    entry("atax", form)[0](N, N, 1.0, p(A), N, dev(xd), y1.ptr(), p(wk), nb, None)
+    uf = "unfused" if form == "fused" else "df_unfused"
+    wk2, nb2 = ws("atax", entry("atax", uf)[1], N, N)
+    entry("atax", uf)[0](N, N, 1.0, p(A), N, dev(xd), y2.ptr(), p(wk2), nb2, None)
     sync()
     assert relerr(y1.host(), y2.host()) < TOL64
 

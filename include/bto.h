@@ -642,20 +642,23 @@ bto_status bto_unfused_vadd(int64_t n, const double *w, const double *y, const d
  * instead of the FP64 unit, which on this GPU issues two FMAs per clock per
  * SM, too few to keep up with HBM.  Data in and out are FP64; only the
  * arithmetic differs from the FP64 form:
- *   - each matrix element keeps 47 of its 53 significant bits (the low 6
- *     fraction bits are dropped); each product is exact up to the dropped
- *     low-part product (below 2^-47 of it); sums are compensated (TwoSum);
- *     the final reduction over tiles is FP64.  Normwise relative error
- *     against exact FP64 arithmetic: about 1e-14 on ordinary data (the FP64
- *     form's contract is 1e-12); integer-valued data below 2^24 in
- *     magnitude give exact results, as in the FP64 form.
+ *   - each matrix and vector element keeps 47 of its 53 significant bits
+ *     (the low 6 fraction bits are dropped); each product is exact up to
+ *     the dropped low-part product (below 2^-47 of it); sums are
+ *     compensated (TwoSum); the final reduction over tiles is FP64.
+ *     Normwise relative error against exact FP64 arithmetic: about 1e-14 on
+ *     ordinary data (the FP64 form's contract is 1e-12); integer-valued data
+ *     below 2^24 in magnitude give exact results, as in the FP64 form.
  *   - GEMVER's B is hi + lo rounded once to FP64: within 2^-45 relative of
  *     the exact A + u1 v1^T + u2 v2^T (the FP64 form rounds twice); x and w
  *     are computed from that B.
- *   - Operating range: matrix elements zero or of magnitude in [2^-70, 2^60),
- *     vector elements zero or in [2^-30, 2^30).  A 256-row chunk of a tile
- *     whose data fall outside it, or whose results are not finite, is
- *     recomputed in FP64 (NaN and Inf propagate as in the FP64 form).
+ *   - FP32's exponent range: values below 2^-127 in magnitude count as zero
+ *     and products below about 2^-100 lose low-order bits, an absolute error
+ *     below 2^-126 times the other factor per element (the underflow term of
+ *     the error bound).  Values of 2^128 or more, Inf, NaN, and products or
+ *     sums beyond FP32's range make a 256-row chunk's results non-finite;
+ *     such a chunk is recomputed in FP64, so those inputs propagate as in
+ *     the FP64 form.
  *   - Layout: the matrices are copied by the tensor memory accelerator, which
  *     needs 16-byte aligned matrix pointers and even leading dimensions (and
  *     m, n < 2^31).  Otherwise the call runs the FP64 form with the same

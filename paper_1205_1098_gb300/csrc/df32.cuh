@@ -112,25 +112,20 @@ DF_HD double to_f64(f2 v) { return (double)v.hi + (double)v.lo; }
 // ---------------------------------------------------------------- sweep split
 // The split the double-float matrix sweeps use, from the two 32-bit words of
 // an FP64 number (hw: sign, exponent, top 20 fraction bits; lw: low 32
-// fraction bits), in nine integer and one FP32 operation:
-//   hi: sign, exponent rebased to FP32, fraction bits 51..29 (truncated);
+// fraction bits), by integer operations and two FP32 operations:
+//   hi: sign, exponent rebased to FP32 and clamped to [0, 255], fraction
+//       bits 51..29 (truncated);
 //   lo: fraction bits 28..6: the FP32 number with hi's sign and exponent
 //       and those bits as its fraction, minus hi's sign and exponent alone
 //       (exact), times 2^-23 (exact unless it underflows).
-// |x - (hi + lo)| < 2^-46 |x| (47 significant bits kept); exact for zero,
-// FP32 values and integers below 2^47.  Valid for x = 0 and for
-// 2^-100 <= |x| < 2^128; FP64 subnormals below 2^-1042 (high word zero
-// apart from the sign) give |hi| + |lo| < 2^-145.  The sweeps check the
-// narrower operating ranges below and recompute anything outside them in
-// FP64.
+// For 2^-100 <= |x| < 2^128: |x - (hi + lo)| < 2^-46 |x| (47 significant
+// bits kept), exact for FP32 values and integers below 2^47.  Zero gives
+// hi = lo = 0 (signed as x).  Below 2^-127 the value is flushed: |hi| + |lo|
+// < 2^-145.  At 2^128 and above, and for Inf and NaN, hi is Inf or NaN, so
+// that anything computed from it is not finite and the sweeps' finiteness
+// check sends the data to FP64.
 constexpr uint32_t kSplitBias = 0x38000000u;      // (1023 - 127) << 20
-// Operating ranges as bounds on the high word without its sign (ax):
-// matrix elements 2^-70 <= |a| < 2^60, vector elements 2^-30 <= |v| < 2^30
-// (or exactly zero).  Then every product |a v| lies in [2^-100, 2^90): its
-// double-float parts stay normal in FP32, and sums of up to 2^31 of them
-// stay below 2^121.
-constexpr uint32_t kMatLo = 953u << 20, kMatHi = 1083u << 20;
-constexpr uint32_t kVecLo = 993u << 20, kVecHi = 1053u << 20;
+constexpr uint32_t kSplitTop = 0x0ff00000u;       // FP32 exponent 255, pre-shift
 
 DF_HD uint32_t float_bits(float f) {
     uint32_t u;
@@ -141,11 +136,12 @@ DF_HD uint32_t float_bits(float f) {
 DF_HD void split_words(uint32_t hw, uint32_t lw, float& hi, float& lo) {
     const uint32_t ax = hw & 0x7fffffffu;
 #if defined(__CUDA_ARCH__)
-    const uint32_t t = (uint32_t)__viaddmax_s32((int)ax, -(int)kSplitBias, 0);   // zero -> 0
+    const uint32_t t = min((uint32_t)__viaddmax_s32((int)ax, -(int)kSplitBias, 0), kSplitTop);
     const uint32_t hb = __funnelshift_l(lw, t, 3) | (hw & 0x80000000u);
 #else
     const int32_t ti = (int32_t)ax - (int32_t)kSplitBias;
-    const uint32_t t = ti > 0 ? (uint32_t)ti : 0u;
+    const uint32_t t0 = ti > 0 ? (uint32_t)ti : 0u;
+    const uint32_t t = t0 < kSplitTop ? t0 : kSplitTop;
     const uint32_t hb = ((t << 3) | (lw >> 29)) | (hw & 0x80000000u);
 #endif
     const uint32_t base = hb & 0xff800000u;                      // sign and exponent of hi
@@ -167,11 +163,40 @@ DF_HD void f32_to_f64_words(float f, uint32_t& hw, uint32_t& lw) {
     lw = ax >= 0x00800000u ? u << 29 : 0u;
 }
 
+// The same in four integer operations, exact for normal FP32 numbers; a
+// signed zero becomes +-2^-127 and a subnormal a number of that order.
+DF_HD void f32_to_f64_words_fast(float f, uint32_t& hw, uint32_t& lw) {
+    const uint32_t u = float_bits(f);
+    const uint32_t sx = (uint32_t)((int32_t)u >> 3);             // sign copied into bits 31..28
+    hw = (sx & 0x8fffffffu) + kSplitBias;
+    lw = u << 29;
+}
+
 DF_HD double f64_of_words(uint32_t hw, uint32_t lw) {
     const uint64_t u = ((uint64_t)hw << 32) | lw;
     double d;
     std::memcpy(&d, &u, sizeof d);
     return d;
+}
+
+}  // namespace df
+}  // namespace bto
+
+namespace bto {
+namespace df {
+
+// A double-float value hi + lo (|lo| <= half an FP32 ulp of hi), given as hi
+// and nlo = -lo, rounded once to FP64: the FP64 sum of hi and -nlo, both
+// converted by f32_to_f64_words_fast.  A zero nlo converts to +-2^-127,
+// below half an FP64 ulp of any |hi| >= 2^-73; for hi = +0 (with nlo = +0,
+// as the renormalisation yields for an exact zero sum) the two +2^-127 cancel
+// exactly.  Callers keep |hi| >= 2^-73 or zero, or accept an absolute error
+// of order 2^-126.
+DF_HD double pair_to_f64(float hi, float nlo) {
+    uint32_t h1, l1, h2, l2;
+    f32_to_f64_words_fast(hi, h1, l1);
+    f32_to_f64_words_fast(nlo, h2, l2);
+    return f64_of_words(h1, l1) - f64_of_words(h2, l2);
 }
 
 }  // namespace df

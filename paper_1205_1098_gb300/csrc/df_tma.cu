@@ -19,10 +19,13 @@
 //     Ogita, Rump and Oishi), two rows per packed FP32 instruction;
 //   - each 256-row chunk's sums become FP64 and add into FP64 partials, which
 //     the panel engine's fixed-order FP64 combine reduces over the tiles.
-// Error: each product carries a relative error below 2^-45 and each
+// Error: each product keeps a relative error below 2^-45 and each
 // compensated sum an error of order 2^-47 times its sum of magnitudes, so
 // results stay within about 1e-14 normwise of exact FP64 arithmetic on
-// ordinary data (the FP64 form's contract is 1e-12).
+// ordinary data (the FP64 form's contract is 1e-12).  FP32's exponent range
+// adds an underflow term: an element below 2^-127 in magnitude counts as
+// zero, and products below about 2^-100 lose low-order bits, each an absolute
+// error below 2^-126 times the other factor.
 //
 // Data movement: the matrix streams through shared memory as 256 x 16 boxes
 // of FP64 (32 KB) copied by the tensor memory accelerator into a five-stage
@@ -34,17 +37,15 @@
 // lanes.  Row vectors of the next chunk are copied into shared memory
 // asynchronously while the current chunk runs.
 //
-// Operating range.  Matrix elements must be zero or of magnitude in
-// [2^-70, 2^60), vector elements zero or in [2^-30, 2^30): then every
-// product and its error terms are normal FP32 numbers and no FP32 sum can
-// overflow.  Lanes check their elements as they split them (two integer
-// min/max operations per element); chunk results are checked for
-// finiteness.  A 256-row chunk of a tile that fails either check is
-// recomputed in FP64 from the matrix in global memory, so NaN, Inf and
-// values outside the range get plain FP64 semantics.  In GEMVER's first
-// pass a failing lane forms its B elements in FP64 before storing them (the
-// matrix may be overwritten in place), and the chunk's column sums are then
-// recomputed in FP64 from the stored B.
+// Out of range.  An element of 2^128 or more in magnitude, Inf or NaN splits
+// into a non-finite hi part, and a product or sum beyond FP32's range
+// overflows, so either makes the chunk's results non-finite.  Chunk results
+// are checked for finiteness; a 256-row chunk of a tile that fails is
+// recomputed in FP64 from the matrix in global memory, so those inputs get
+// plain FP64 semantics.  In GEMVER's first pass a lane whose B values come
+// out non-finite forms its B elements in FP64 from then on (the matrix may
+// be overwritten in place), and the chunk's column sums are recomputed in
+// FP64 from the stored B.
 //
 // Every mbarrier wait is bounded by %globaltimer (2 s) and a shared abort
 // flag; on expiry the block records BTO_ERR_TIMEOUT in the status word and
@@ -107,37 +108,13 @@ __device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, f
     rl = (al + bl) + e;
 }
 
-// Splits the two FP64 values of d (two rows) into packed hi and lo parts and
-// folds their magnitudes (high words without sign) into the lane's range
-// trackers: mn = min(ax - 1) over the elements (zero wraps to the maximum and
-// is ignored), mx = max(ax).
-__device__ __forceinline__ void split_pair(double2 d, float2& H, float2& L, uint32_t& mn, uint32_t& mx) {
-    const uint32_t h0 = (uint32_t)__double2hiint(d.x), l0 = (uint32_t)__double2loint(d.x);
-    const uint32_t h1 = (uint32_t)__double2hiint(d.y), l1 = (uint32_t)__double2loint(d.y);
-    split_words(h0, l0, H.x, L.x);
-    split_words(h1, l1, H.y, L.y);
-    const uint32_t a0 = h0 & 0x7fffffffu, a1 = h1 & 0x7fffffffu;
-    mn = __viaddmin_u32(a0, 0xffffffffu, mn);
-    mn = __viaddmin_u32(a1, 0xffffffffu, mn);
-    mx = __vimax3_u32(mx, a0, a1);
+// Splits the two FP64 values of d (two rows) into packed hi and lo parts.
+__device__ __forceinline__ void split_pair(double2 d, float2& H, float2& L) {
+    split_words((uint32_t)__double2hiint(d.x), (uint32_t)__double2loint(d.x), H.x, L.x);
+    split_words((uint32_t)__double2hiint(d.y), (uint32_t)__double2loint(d.y), H.y, L.y);
 }
-__device__ __forceinline__ bool out_of_range(uint32_t mn, uint32_t mx, uint32_t lo, uint32_t hi) {
-    return mn < lo - 1u || mx >= hi;
-}
-__device__ __forceinline__ void split_vec(double v, float& h, float& l, uint32_t& mn, uint32_t& mx) {
-    const uint32_t hw = (uint32_t)__double2hiint(v), lw = (uint32_t)__double2loint(v);
-    split_words(hw, lw, h, l);
-    const uint32_t ax = hw & 0x7fffffffu;
-    mn = __viaddmin_u32(ax, 0xffffffffu, mn);
-    mx = max(mx, ax);
-}
-// hi + lo as the nearest FP64 number: both parts converted by integer
-// operations, one FP64 add.
-__device__ __forceinline__ double df_to_f64(float h, float l) {
-    uint32_t h1, l1, h2, l2;
-    df::f32_to_f64_words(h, h1, l1);
-    df::f32_to_f64_words(l, h2, l2);
-    return __hiloint2double((int)h1, (int)l1) + __hiloint2double((int)h2, (int)l2);
+__device__ __forceinline__ void split_vec(double v, float& h, float& l) {
+    split_words((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), h, l);
 }
 
 // Transposing butterfly over 8 column partials (hi, lo) per lane: lane l
@@ -169,6 +146,8 @@ __device__ __forceinline__ void butterfly8(float (&h)[8], float (&l)[8], int lan
 // Sum over the lane's 8 rows of a * v for one column: a as packed row pairs
 // (AH, AL), v as packed row pairs (VH, its negation NVH, VL).  Returns the
 // double-float sum (sh, sl).
+// NEG_LO: AL holds the negated low parts (-a_lo).
+template <bool NEG_LO = false>
 __device__ __forceinline__ void col_partial(const float2 (&AH)[4], const float2 (&AL)[4], const float2 (&VH)[4],
                                             const float2 (&NVH)[4], const float2 (&VL)[4], float& sh, float& sl) {
     float2 Pn[4], Lx[4];
@@ -176,7 +155,7 @@ __device__ __forceinline__ void col_partial(const float2 (&AH)[4], const float2 
     for (int h = 0; h < 4; h++) {
         Pn[h] = mul2(AH[h], NVH[h]);                          // -(a_hi v_hi)
         const float2 E = fma2(AH[h], VH[h], Pn[h]);           // its rounding error, exact
-        Lx[h] = fma2(AL[h], VH[h], fma2(AH[h], VL[h], E));    // + cross terms
+        Lx[h] = fma2(AL[h], NEG_LO ? NVH[h] : VH[h], fma2(AH[h], VL[h], E));    // + cross terms
     }
     float2 s01, e01, s23, e23, s, e;
     two_sum2(Pn[0], Pn[1], s01, e01);
@@ -223,10 +202,8 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
     float* v2l = v2h + a.tcmax;
     __shared__ int s_abort_;
     __shared__ int s_bad[2];
-    __shared__ int s_vbad[2];
     volatile int* s_abort_p = &s_abort_;
     volatile int* s_badp = s_bad;
-    volatile int* s_vbadp = s_vbad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
 
     if (tid == 0) {
@@ -236,7 +213,6 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
         }
         *s_abort_p = 0;
         s_badp[0] = s_badp[1] = 0;
-        s_vbadp[0] = s_vbadp[1] = 0;
         fence_mbar_init();
     }
     __syncthreads();
@@ -280,8 +256,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
     int slot = 0;            // ring slot of the next stage
     uint32_t ph = 0;         // parity of its use
     long long chunk = 0;     // chunks processed by this block (flag parity)
-    int tile_no = 0;
-    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, tile_no++) {
+    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int64_t tt = a.reverse ? (a.ntiles - 1 - t) : t;
         const int64_t cb = tt / a.NR, rb = tt % a.NR;
         const int64_t c0 = lp_col_at(a.n, a.NC, cb, kBoxC), c1 = lp_col_at(a.n, a.NC, cb + 1, kBoxC);
@@ -290,31 +265,27 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
         const int ncols_u = (ncols + kBoxC - 1) / kBoxC * kBoxC;
 
         // Column vectors of the tile, split once (zero beyond the matrix).
-        {
-            uint32_t mn = 0xffffffffu, mx = 0u;
-            for (int k = tid; k < ncols_u; k += kCT) {
-                if (HAS_S) sacc[k] = 0.0;
-                if (HAS_Q || MODE == DF_G1) {
-                    const double v = k < ncols ? __ldg((MODE == DF_G1 ? a.v1 : a.p) + c0 + k) : 0.0;
-                    split_vec(v, vph[k], vpl[k], mn, mx);
-                }
-                if (MODE == DF_G1) {
-                    const double v = k < ncols ? __ldg(a.v2 + c0 + k) : 0.0;
-                    split_vec(v, v2h[k], v2l[k], mn, mx);
-                }
+        for (int k = tid; k < ncols_u; k += kCT) {
+            if (HAS_S) sacc[k] = 0.0;
+            if (HAS_Q || MODE == DF_G1) {
+                const double v = k < ncols ? __ldg((MODE == DF_G1 ? a.v1 : a.p) + c0 + k) : 0.0;
+                split_vec(v, vph[k], vpl[k]);
             }
-            if (out_of_range(mn, mx, df::kVecLo, df::kVecHi)) s_vbadp[tile_no & 1] = 1;
+            if (MODE == DF_G1) {
+                const double v = k < ncols ? __ldg(a.v2 + c0 + k) : 0.0;
+                split_vec(v, v2h[k], v2l[k]);
+            }
         }
         // Row vectors of the tile's first chunk.
         auto stage_rows = [&](int64_t R, int buf) {
             if (NRV == 0) return;
             const int64_t i = R + tid;
-            const double* src[3] = {MODE == DF_G1 ? a.u1 : a.r, a.u2, a.r};
 #pragma unroll
             for (int v = 0; v < NRV; v++) {
+                const double* src = v == 0 ? (MODE == DF_G1 ? a.u1 : a.r) : (v == 1 ? a.u2 : a.r);
                 double* dst = rowv + ((size_t)buf * kMaxRowVecs + v) * kBoxR + tid;
                 if (i < r1) {
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src[v] + i) : "memory");
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src + i) : "memory");
                 } else {
                     *dst = 0.0;
                 }
@@ -323,8 +294,6 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
         };
         stage_rows(r0, 0);
         named_bar(1, kCT);
-        const bool vbad = s_vbadp[tile_no & 1] != 0;
-        if (tid == 0) s_vbadp[(tile_no + 1) & 1] = 0;
 
         int rbuf = 0;
         for (int64_t R0 = r0; R0 < r1; R0 += kBoxR, chunk++, rbuf ^= 1) {
@@ -333,7 +302,6 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
             if (R0 + kBoxR < r1) stage_rows(R0 + kBoxR, rbuf ^ 1);
 
             // The lane's rows: pair h holds rows R0 + 64h + 2 lane + {0, 1}.
-            uint32_t rmn = 0xffffffffu, rmx = 0u;
             float2 RH[4], NRH[4], RL[4];         // r (or y) parts
             float2 U1H[4], U1L[4], U2H[4], U2L[4];
             const double* rv = rowv + (size_t)rbuf * kMaxRowVecs * kBoxR;
@@ -343,22 +311,21 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                 if (HAS_S) {
                     const int vi = MODE == DF_G1 ? 2 : 0;
                     float hx, lx, hy, ly;
-                    split_vec(rv[vi * kBoxR + row], hx, lx, rmn, rmx);
-                    split_vec(rv[vi * kBoxR + row + 1], hy, ly, rmn, rmx);
+                    split_vec(rv[vi * kBoxR + row], hx, lx);
+                    split_vec(rv[vi * kBoxR + row + 1], hy, ly);
                     RH[h] = f2(hx, hy); NRH[h] = f2(-hx, -hy); RL[h] = f2(lx, ly);
                 }
                 if (MODE == DF_G1) {
                     float hx, lx, hy, ly;
-                    split_vec(rv[row], hx, lx, rmn, rmx);
-                    split_vec(rv[row + 1], hy, ly, rmn, rmx);
+                    split_vec(rv[row], hx, lx);
+                    split_vec(rv[row + 1], hy, ly);
                     U1H[h] = f2(hx, hy); U1L[h] = f2(lx, ly);
-                    split_vec(rv[kBoxR + row], hx, lx, rmn, rmx);
-                    split_vec(rv[kBoxR + row + 1], hy, ly, rmn, rmx);
+                    split_vec(rv[kBoxR + row], hx, lx);
+                    split_vec(rv[kBoxR + row + 1], hy, ly);
                     U2H[h] = f2(hx, hy); U2L[h] = f2(lx, ly);
                 }
             }
-            bool lbad = vbad || out_of_range(rmn, rmx, df::kVecLo, df::kVecHi);
-            uint32_t amn = 0xffffffffu, amx = 0u;
+            bool lbad = false;               // GEMVER: this lane forms its B in FP64
             float2 QH[4], QL[4], QH2[4], QL2[4];
 #pragma unroll
             for (int h = 0; h < 4; h++) {
@@ -393,7 +360,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
 #pragma unroll
                                 for (int h = 0; h < 4; h++) {
                                     D[h] = col[h * 32 + lane];
-                                    split_pair(D[h], AH[h], AL[h], amn, amx);
+                                    split_pair(D[h], AH[h], AL[h]);
                                 }
                                 if (HAS_Q) {
                                     const float p_h = vph[lc], p_l = vpl[lc];
@@ -403,7 +370,10 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                                         const float2 Pn = mul2(AH[h], NPH);
                                         const float2 E = fma2(AH[h], PH, Pn);
                                         float2 s, e;
-                                        if (u == 0) {
+                                        // A's columns take turns between two accumulator
+                                        // sets (B's in GESUMMV), so consecutive updates of
+                                        // a row are independent.
+                                        if (MODE == DF_Q2 ? u == 0 : cc == 0) {
                                             two_sum_n(QH[h], Pn, s, e);
                                             QH[h] = s;
                                             QL[h] = fma2(AL[h], PH, fma2(AH[h], PL, add2(QL[h], add2(E, e))));
@@ -418,11 +388,10 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                                     col_partial(AH, AL, RH, NRH, RL, sh[2 * gs + cc], sl[2 * gs + cc]);
                                 if (MODE == DF_G1) {
                                     // B = A + u1 v1^T + u2 v2^T in double-float, stored in FP64.
-                                    lbad = lbad || out_of_range(amn, amx, df::kMatLo, df::kMatHi);
                                     const float w1h = vph[lc], w1l = vpl[lc], w2h = v2h[lc], w2l = v2l[lc];
                                     const float2 V1H = f2(w1h, w1h), NV1H = f2(-w1h, -w1h), V1L = f2(w1l, w1l);
                                     const float2 V2H = f2(w2h, w2h), NV2H = f2(-w2h, -w2h), V2L = f2(w2l, w2l);
-                                    float2 BH[4], BL[4];
+                                    float2 BH[4], NBL[4];    // hi and negated lo of B
 #pragma unroll
                                     for (int h = 0; h < 4; h++) {
                                         const float2 P1n = mul2(U1H[h], NV1H);
@@ -436,8 +405,13 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                                         two_sum_n(s1, P2n, s2, e2);
                                         const float2 low = add2(add2(AL[h], L), add2(e1, e2));
                                         BH[h] = add2(s2, low);
-                                        BL[h] = rsub2(rsub2(s2, BH[h]), low);     // low - (BH - s2)
+                                        NBL[h] = rsub2(low, rsub2(s2, BH[h]));    // (BH - s2) - low
                                     }
+                                    // Anything out of FP32's range (a huge or non-finite
+                                    // input, an overflow) shows as a non-finite hi part:
+                                    // from here on the lane forms B in FP64.
+                                    const float2 ck = add2(add2(BH[0], BH[1]), add2(BH[2], BH[3]));
+                                    lbad = lbad || !isfinite(ck.x + ck.y);
                                     const int64_t col_g = cs + c;
                                     double* bcol = a.Bout + col_g * a.ldbo;
 #pragma unroll
@@ -445,8 +419,8 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                                         const int64_t i0 = R0 + 64 * h + 2 * lane;
                                         double b0, b1;
                                         if (!lbad) {
-                                            b0 = df_to_f64(BH[h].x, BL[h].x);
-                                            b1 = df_to_f64(BH[h].y, BL[h].y);
+                                            b0 = df::pair_to_f64(BH[h].x, NBL[h].x);
+                                            b1 = df::pair_to_f64(BH[h].y, NBL[h].y);
                                         } else {
                                             // FP64 for the whole lane once anything it holds is out of range.
                                             const double v1j = col_g < c1 ? __ldg(a.v1 + col_g) : 0.0;
@@ -462,7 +436,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                                             }
                                         }
                                     }
-                                    col_partial(BH, BL, RH, NRH, RL, sh[2 * gs + cc], sl[2 * gs + cc]);
+                                    col_partial<true>(BH, NBL, RH, NRH, RL, sh[2 * gs + cc], sl[2 * gs + cc]);
                                 }
                             }
                             __syncwarp();
@@ -485,10 +459,18 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
             }
 
             // ---- chunk end: rows of q, check, write or recompute in FP64
-            lbad = lbad || out_of_range(amn, amx, df::kMatLo, df::kMatHi);
             const int fl = (int)(chunk & 1);
             if (lbad) s_badp[fl] = 1;
             double qv = 0.0, qv2 = 0.0;
+            if (MODE == DF_QS || MODE == DF_Q) {
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    float2 s, e;
+                    two_sum2(QH[h], QH2[h], s, e);
+                    QH[h] = s;
+                    QL[h] = add2(add2(QL[h], QL2[h]), e);
+                }
+            }
 #pragma unroll
             for (int pass = 0; pass < (MODE == DF_Q2 ? 2 : (HAS_Q ? 1 : 0)); pass++) {
                 if (pass == 1) named_bar(1, kCT);

@@ -129,9 +129,54 @@ int main() {
         if (!(std::fabs((double)hi) + std::fabs((double)lo) < std::ldexp(1.0, -145)))
             return fail("sweep split of a small subnormal is not near zero", x, hi);
     }
-    // The operating ranges are inside the split's valid range.
-    if (kMatLo < (1023u - 100u) << 20 || kMatHi > (1023u + 128u) << 20 || kVecLo < kMatLo || kVecHi > kMatHi)
-        return fail("operating range constants", (double)kMatLo, (double)kMatHi);
+    // Flushed below 2^-127; not finite from 2^128 up and for Inf and NaN.
+    for (int i = 0; i < 200000; i++) {
+        const int ex = -1022 + (int)(next_u64() % (1022 - 128));        // -1022 .. -129
+        double x = std::ldexp(1.0 + unit(), ex);
+        if (next_u64() & 1) x = -x;
+        float hi, lo;
+        split_double(x, hi, lo);
+        if (!(std::fabs((double)hi) + std::fabs((double)lo) < std::ldexp(1.0, -145)))
+            return fail("sweep split does not flush below 2^-127", x, hi);
+        const double big = std::ldexp(1.0 + unit(), 128 + (int)(next_u64() % 895)) * ((next_u64() & 1) ? -1 : 1);
+        split_double(big, hi, lo);
+        if (std::isfinite(hi)) return fail("sweep split of a value >= 2^128 is finite", big, hi);
+    }
+    {
+        float hi, lo;
+        split_double(INFINITY, hi, lo);
+        if (!(std::isinf(hi) && hi > 0)) return fail("sweep split of +Inf", INFINITY, hi);
+        split_double(-INFINITY, hi, lo);
+        if (!(std::isinf(hi) && hi < 0)) return fail("sweep split of -Inf", -INFINITY, hi);
+        split_double(NAN, hi, lo);
+        if (std::isfinite(hi)) return fail("sweep split of NaN is finite", NAN, hi);
+    }
+    // Fast FP32 -> FP64 words: exact on normal values, +-2^-127 for zeros.
+    for (int i = 0; i < 2000000; i++) {
+        const uint32_t u = (uint32_t)next_u64();
+        float f;
+        std::memcpy(&f, &u, sizeof f);
+        if (!std::isfinite(f) || (u & 0x7fffffffu) < 0x00800000u) continue;
+        uint32_t hw, lw;
+        f32_to_f64_words_fast(f, hw, lw);
+        if (f64_of_words(hw, lw) != (double)f) return fail("f32_to_f64_words_fast", f, f64_of_words(hw, lw));
+    }
+    {
+        uint32_t hw, lw;
+        f32_to_f64_words_fast(0.0f, hw, lw);
+        if (f64_of_words(hw, lw) != std::ldexp(1.0, -127)) return fail("fast conversion of +0", 0, 0);
+        f32_to_f64_words_fast(-0.0f, hw, lw);
+        if (f64_of_words(hw, lw) != -std::ldexp(1.0, -127)) return fail("fast conversion of -0", 0, 0);
+    }
+    // A renormalised pair (hi, lo) given as (hi, -lo) rounds once to FP64.
+    for (int i = 0; i < 2000000; i++) {
+        const float h = (float)std::ldexp(1.0 + unit(), -73 + (int)(next_u64() % 190)) * ((next_u64() & 1) ? -1.f : 1.f);
+        float l = (float)(std::ldexp(unit() - 0.5, -24) * (double)h);
+        if (next_u64() % 8 == 0) l = 0.0f;
+        const f2 r = fast_two_sum(h, l);                                 // |lo| <= half an ulp of hi
+        if (pair_to_f64(r.hi, -r.lo) != (double)r.hi + (double)r.lo) return fail("pair_to_f64", r.hi, r.lo);
+    }
+    if (pair_to_f64(0.0f, 0.0f) != 0.0) return fail("pair_to_f64 of an exact zero", 0, 0);
     // FP32 -> FP64 words: exact for normal values and zero; subnormals to zero.
     for (int i = 0; i < 2000000; i++) {
         const uint32_t u = (uint32_t)next_u64();

@@ -181,14 +181,26 @@ class Suite:
             self.big[k] = torch.empty(N, **f64)
         self.r = torch.empty(1, **f64)
         self.ws = {}
-        for form in (0, 1):
+        for form in (0, 1, 2, 3):
+            ks = KERNELS if form < 2 else [k for k in KERNELS if k in MATRIX_KERNELS]
+            if not ks:
+                continue
             size = max(bto.bto_workspace_bytes(k, form, m if k in MATRIX_KERNELS else 0,
-                                               n if k in MATRIX_KERNELS else N) for k in KERNELS)
+                                               n if k in MATRIX_KERNELS else N) for k in ks)
             self.ws[form] = (torch.empty(size, dtype=torch.uint8, device="cuda"), size)
         torch.cuda.synchronize()
 
     def call(self, k, form=0):
+        """form 0 fused, 1 unfused, 2 double-float fused, 3 double-float unfused
+        (the vector kernels have no double-float form and run as forms 0 / 1)."""
         b, v, g, m, n, N = self.bto, self.vec, self.big, self.m, self.n, self.N
+        if form >= 2 and k in MATRIX_KERNELS:
+            df = {"bicgk": "bicgk", "atax": "atax", "gesummv": "gesummv", "gemver": "gemver", "dgemv": "dgemv",
+                  "dgemvt": "dgemvt"}[k]
+            f = getattr(b, ("bto_unfused_%s_df" if form == 3 else "bto_%s_df") % df)
+            ws, wb = self.ws[form]
+            return self._matrix_call(k, f, ws, wb)
+        form = form - 2 if form >= 2 else form
         ws, wb = self.ws[form]
         u = form == 1
         if k == "bicgk":
@@ -215,6 +227,94 @@ class Suite:
             (b.bto_unfused_waxpby if u else b.bto_waxpby)(N, ALPHA, g["xx"], -0.25, g["yy"], g["w_wx"], None)
         elif k == "vadd":
             (b.bto_unfused_vadd if u else b.bto_vadd)(N, g["w"], g["yy"], g["zz"], g["x_va"], None)
+
+
+def _matrix_call(self, k, f, ws, wb):
+    m, n, v = self.m, self.n, self.vec
+    if k == "bicgk":
+        f(m, n, self.A, m, v["p"], v["r"], v["q"], v["s"], ws, wb, None)
+    elif k == "atax":
+        f(m, n, BETA, self.A, m, v["x"], v["y_atax"], ws, wb, None)
+    elif k == "gesummv":
+        f(m, n, ALPHA, self.A, m, -0.75, self.B2, m, v["x"], v["y_ges"], ws, wb, None)
+    elif k == "gemver":
+        f(m, n, ALPHA, BETA, self.A, m, v["u1"], v["v1"], v["u2"], v["v2"], v["gy"], v["gz"], self.Bout, m,
+          v["gx"], v["gw"], ws, wb, None)
+    elif k == "dgemv":
+        f(m, n, ALPHA, self.A, m, v["x"], -0.5, v["ym"], v["z_dgemv"], ws, wb, None)
+    elif k == "dgemvt":
+        f(m, n, ALPHA, BETA, self.A, m, v["ym"], v["zn"], v["tx"], v["tw"], ws, wb, None)
+
+
+Suite._matrix_call = _matrix_call
+
+# Array ids of the suite's device fills (bto_fill_f64 with seed SEED).
+SUITE_AIDS = {"A": 0, "B2": 1, "p": 1, "r": 2, "x": 3, "ym": 4, "zn": 5, "u1": 11, "v1": 12, "u2": 13, "v2": 14,
+              "gy": 15, "gz": 16}
+
+
+def sampled_errors(suite, nsamp=16):
+    """Normwise relative error of sampled outputs of the matrix kernels the
+    suite last ran, against the oracle on the sub-problems that determine
+    them exactly (rows of A for A v, columns for A^T v; GEMVER's x_j from
+    column j of B = A + u1 v1^T + u2 v2^T)."""
+    import oracle as O
+    import synth
+    m, n = suite.m, suite.n
+    vec = {k: synth.vector(SEED, SUITE_AIDS[k], m if k in ("r", "ym", "u1", "u2", "gy") else n)
+           for k in ("p", "r", "x", "ym", "zn", "u1", "v1", "u2", "v2", "gy", "gz")}
+    host = {k: suite.vec[k].cpu().numpy() for k in ("q", "s", "y_ges", "z_dgemv", "tx", "gx")}
+    I = np.unique(np.linspace(0, m - 1, nsamp).astype(np.int64))
+    J = np.unique(np.linspace(0, n - 1, nsamp).astype(np.int64))
+    RA, RB = synth.matrix_rows(SEED, 0, m, n, I), synth.matrix_rows(SEED, 1, m, n, I)
+    CA = synth.matrix_cols(SEED, 0, m, n, J)
+
+    def rel(g, o):
+        g, o = np.asarray(g), np.asarray(o)
+        return float(np.linalg.norm(g - o) / np.linalg.norm(o))
+
+    q_o = [O.bicgk(1, n, RA[k:k + 1], vec["p"], vec["r"][i:i + 1])[0][0] for k, i in enumerate(I)]
+    s_o = [O.bicgk(m, 1, CA[:, k:k + 1], vec["p"][j:j + 1], vec["r"])[1][0] for k, j in enumerate(J)]
+    y_o = [O.gesummv(1, n, ALPHA, RA[k:k + 1], -0.75, RB[k:k + 1], vec["x"])[0] for k in range(len(I))]
+    z_o = [O.dgemv(1, n, ALPHA, RA[k:k + 1], vec["x"], -0.5, vec["ym"][i:i + 1])[0] for k, i in enumerate(I)]
+    x_o = [O.dgemvt(m, 1, ALPHA, BETA, CA[:, k:k + 1], vec["ym"], vec["zn"][j:j + 1])[0][0] for k, j in enumerate(J)]
+    g_o = [O.gemver(m, 1, ALPHA, BETA, CA[:, k:k + 1], vec["u1"], vec["v1"][j:j + 1], vec["u2"],
+                    vec["v2"][j:j + 1], vec["gy"], vec["gz"][j:j + 1])[1][0] for k, j in enumerate(J)]
+    return {"bicgk_q": rel(host["q"][I], q_o), "bicgk_s": rel(host["s"][J], s_o),
+            "gesummv_y": rel(host["y_ges"][I], y_o), "dgemv_z": rel(host["z_dgemv"][I], z_o),
+            "dgemvt_x": rel(host["tx"][J], x_o), "gemver_x": rel(host["gx"][J], g_o),
+            "samples": "%d rows and %d columns, evenly spaced" % (len(I), len(J))}
+
+
+def df_form(torch, suite, steps, warmup, dist, hbm, kern64):
+    """The double-float form of the matrix kernels (bto_*_df) beside its
+    unfused form (bto_unfused_*_df), inside the same suite step (the vector
+    kernels run their FP64 forms)."""
+    m, n, N = suite.m, suite.n, suite.N
+    ms, kern = timed_steps(torch, suite, steps, warmup, 2, dist)
+    spread = dict(timed_steps.spread)
+    errs = sampled_errors(suite)
+    ums, ukern = timed_steps(torch, suite, steps, max(3, warmup // 2), 3, dist)
+    per = {}
+    for k in MATRIX_KERNELS:
+        t = kern[k] * 1e-3
+        gbs = compulsory_bytes(k, m, n, N) / t / 1e9
+        med, p10, p90 = spread[k]
+        per[k] = {"ms": round(kern[k], 4), "ms_p10": round(p10, 4), "ms_p90": round(p90, 4),
+                  "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3),
+                  "unfused_ms": round(ukern[k], 4),
+                  "unfused_own_gbs": round(unfused_bytes(k, m, n, N) / (ukern[k] * 1e-3) / 1e9, 1),
+                  "fused_speedup": round(ukern[k] / kern[k], 3),
+                  "byte_ratio": round(unfused_bytes(k, m, n, N) / compulsory_bytes(k, m, n, N), 3),
+                  "speedup_vs_fp64_form": round(kern64[k] / kern[k], 3)}
+    dom = max(MATRIX_KERNELS, key=lambda k: kern[k])
+    step_bytes = suite_bytes(m, n, N)
+    return {"ms_per_step": round(ms, 4), "value": round(step_bytes / (ms * 1e-3) / 1e9, 1),
+            "unit": "GB/s of fused compulsory bytes (same suite, matrix kernels in the double-float form)",
+            "unfused_ms_per_step": round(ums, 4), "kernels": per, "err_vs_oracle": errs,
+            "tolerance": 1e-12,
+            "roofline": {"kernel": "bto_%s_df (all launches of one call)" % dom, "bound": "hbm",
+                         "achieved": per[dom]["gbs"], "peak": hbm, "unit": "GB/s", "frac": per[dom]["hbm_frac"]}}
 
 
 def timed_steps(torch, suite, steps, warmup, form, dist, per_kernel=True):
@@ -414,7 +514,9 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": round(1e3 * secs / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (SplitMix64 uniform[-1,1), seed 1)",
-        "config": {"workload": WORKLOAD, "parallelism": "single"},
+        "config": {"workload": "FP64 kernel suite sample: %dx%d column-major matrices, %d-element vectors "
+                               "(a bounded sample of the 16384x16384 / 2^26 workload)" % (ns, ns, nv),
+                   "parallelism": "single"},
         "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -911,6 +1013,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
+    ap.add_argument("--no-df", action="store_true", help="skip the double-float form")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--only", default=None, help="comma-separated kernels (profiling runs)")
     ap.add_argument("--no-batched", action="store_true")
@@ -1058,6 +1161,10 @@ def main():
             per[k]["fused_speedup"] = round(ukern[k] / kern[k], 3)
             per[k]["byte_ratio"] = round(unfused_bytes(k, m, n, N) / compulsory_bytes(k, m, n, N), 3)
 
+    dff = None
+    if not args.no_df:
+        dff = df_form(torch, suite, args.steps, args.warmup, dist, hbm, kern)
+
     # Roofline of the dominant kernel (largest share of the step).
     dom = max(KERNELS, key=lambda k: kern[k])
     d = per[dom]
@@ -1147,6 +1254,7 @@ def main():
                        "l2": "every input is larger than L2 (2 GiB matrices, 512 MiB vectors); no flush"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "kernels": per, "unfused": unfused,
+            "df_form_n16384": dff,
             "precision_form_n32768": prec,
             "batched_4096": batched,
             "mrhs_8192_k64": mrhs,

@@ -518,6 +518,17 @@ typedef struct bto_serve_cfg {
 typedef struct bto_serve_stats {
     int64_t served, batches, direct, rejected;
     double wall_s, peak_bytes;    /* run time; high-water mark of the arena in use */
+    /* Diagnostics of the loop itself (seconds on the loop's clock):          */
+    double max_gap_s, max_gap_at_s;   /* longest time between two passes of the loop, and when */
+    double max_admit_s;               /* longest single admission (plan, copy, launches)      */
+    double max_complete_s;            /* longest completion scan                              */
+    double max_oversleep_s;           /* longest overshoot of an idle sleep                   */
+    int64_t max_fifo;                 /* deepest FIFO of arrived, unadmitted requests         */
+    int64_t fifo_at_max_gap;          /* its depth when the longest gap ended                 */
+    int64_t sleeps;                   /* idle sleeps taken                                    */
+    int64_t blocking_copies;          /* batch plans too large for their staging slice,      */
+                                      /* copied with a wait on the stream                    */
+    double max_query_s;               /* longest single completion-event query (driver call) */
 } bto_serve_stats;
 
 bto_status bto_serve_run(const bto_serve_cfg *cfg, int64_t count, const bto_serve_req *req,

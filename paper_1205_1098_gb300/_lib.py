@@ -353,7 +353,11 @@ class ServeCfg(ctypes.Structure):
 class ServeStats(ctypes.Structure):
     """bto_serve_stats of include/bto.h."""
     _fields_ = [("served", ctypes.c_int64), ("batches", ctypes.c_int64), ("direct", ctypes.c_int64),
-                ("rejected", ctypes.c_int64), ("wall_s", ctypes.c_double), ("peak_bytes", ctypes.c_double)]
+                ("rejected", ctypes.c_int64), ("wall_s", ctypes.c_double), ("peak_bytes", ctypes.c_double),
+                ("max_gap_s", ctypes.c_double), ("max_gap_at_s", ctypes.c_double), ("max_admit_s", ctypes.c_double),
+                ("max_complete_s", ctypes.c_double), ("max_oversleep_s", ctypes.c_double),
+                ("max_fifo", ctypes.c_int64), ("fifo_at_max_gap", ctypes.c_int64), ("sleeps", ctypes.c_int64),
+                ("blocking_copies", ctypes.c_int64), ("max_query_s", ctypes.c_double)]
 
 
 def bto_serve_run(cfg, count, reqs, res, stats):

@@ -861,6 +861,8 @@ bool batch_plan_build(BatchPlan* b, int count, const bto_batch_desc* descs, int 
     return true;
 }
 
+size_t batch_plan_image_bytes(const BatchPlan* b) { return image_bytes(b->p, true); }
+
 bto_status batch_plan_submit(const BatchPlan* b, void* ws, size_t ws_bytes, void* staging, size_t staging_bytes,
                              cudaStream_t st) {
     return submit_plan(b->p, ws, ws_bytes, staging, staging_bytes, st);

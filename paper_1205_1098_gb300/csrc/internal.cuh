@@ -140,6 +140,8 @@ bool batch_plan_build(BatchPlan* b, int count, const bto_batch_desc* descs, int 
 // pinned `staging` buffer when it is large enough (the caller keeps it until
 // the stream has passed the copy) or a pageable copy that is waited for, and
 // launches the kernels of the non-empty queues, each grid at most its items.
+// Bytes batch_plan_submit copies (it needs that much staging to avoid a wait).
+size_t batch_plan_image_bytes(const BatchPlan* b);
 bto_status batch_plan_submit(const BatchPlan* b, void* ws, size_t ws_bytes, void* staging, size_t staging_bytes,
                              cudaStream_t st);
 

@@ -83,15 +83,32 @@ class Server {
         t0_ = std::chrono::steady_clock::now();
         int64_t next = 0;
         bool closed = false;
+        double last = 0.0;
         for (;;) {
             const double tn = now();
+            if (tn - last > dg_.max_gap_s) {
+                dg_.max_gap_s = tn - last;
+                dg_.max_gap_at_s = tn;
+                gap_mark_ = true;
+            }
+            last = tn;
             if (c_.max_wall > 0 && tn > c_.max_wall) closed = true;
             while (!closed && next < count_ && rq_[next].t <= tn) pending_.push_back(next++);
+            dg_.max_fifo = std::max<int64_t>(dg_.max_fifo, (int64_t)pending_.size());
+            if (gap_mark_) {
+                dg_.fifo_at_max_gap = (int64_t)pending_.size();
+                gap_mark_ = false;
+            }
+            const double tc = now();
             const bool progressed = complete();
+            dg_.max_complete_s = std::max(dg_.max_complete_s, now() - tc);
             bool launched = false;
             for (int si = 0; si < c_.nstreams && !pending_.empty(); si++)
                 if (!slots_[si].busy) {
-                    if (!admit(si)) break;
+                    const double ta = now();
+                    const bool ok = admit(si);
+                    dg_.max_admit_s = std::max(dg_.max_admit_s, now() - ta);
+                    if (!ok) break;
                     launched = true;
                 }
             const bool idle = std::none_of(slots_.begin(), slots_.end(), [](const Slot& s) { return s.busy; });
@@ -99,10 +116,25 @@ class Server {
             if (!progressed && !launched && idle && pending_.empty() && next < count_) {
                 // Nothing to do before the next arrival.
                 const double gap = rq_[next].t - now();
-                if (gap > 300e-6) std::this_thread::sleep_for(std::chrono::duration<double>(gap - 200e-6));
+                if (gap > 300e-6) {
+                    const double want = gap - 200e-6, ts = now();
+                    std::this_thread::sleep_for(std::chrono::duration<double>(want));
+                    dg_.max_oversleep_s = std::max(dg_.max_oversleep_s, now() - ts - want);
+                    dg_.sleeps++;
+                }
             }
         }
         stats->wall_s = now();
+        stats->max_gap_s = dg_.max_gap_s;
+        stats->max_gap_at_s = dg_.max_gap_at_s;
+        stats->max_admit_s = dg_.max_admit_s;
+        stats->max_complete_s = dg_.max_complete_s;
+        stats->max_oversleep_s = dg_.max_oversleep_s;
+        stats->max_fifo = dg_.max_fifo;
+        stats->fifo_at_max_gap = dg_.fifo_at_max_gap;
+        stats->sleeps = dg_.sleeps;
+        stats->blocking_copies = dg_.blocking_copies;
+        stats->max_query_s = dg_.max_query_s;
         stats->served = served_;
         stats->batches = batches_;
         stats->direct = direct_;
@@ -238,6 +270,7 @@ class Server {
         }
         for (int64_t j : s.reqs) stamp_admit(j, 0);
         void* stage = status_ ? static_cast<char*>(c_.staging) + kGranule + (size_t)si * stage_each_ : nullptr;
+        if (!stage || batch_plan_image_bytes(plan_) > stage_each_) dg_.blocking_copies++;
         const bto_status e = batch_plan_submit(plan_, at(s.ws), s.ws.bytes, stage, stage_each_, st);
         if (e != BTO_OK) { fail_now(si, e); return true; }
         arm(si, st);
@@ -291,7 +324,9 @@ class Server {
         for (int si = 0; si < c_.nstreams; si++) {
             Slot& s = slots_[si];
             if (!s.busy) continue;
+            const double tq = now();
             const cudaError_t q = cudaEventQuery(s.ev);
+            dg_.max_query_s = std::max(dg_.max_query_s, now() - tq);
             if (q == cudaErrorNotReady) continue;
             const double td = now();
             int status = BTO_OK;
@@ -338,6 +373,8 @@ class Server {
     size_t stage_each_ = 0;
     std::chrono::steady_clock::time_point t0_;
     int64_t served_ = 0, batches_ = 0, direct_ = 0, rejected_ = 0;
+    bto_serve_stats dg_{};   // diagnostics only
+    bool gap_mark_ = false;
     bto_status failed_ = BTO_OK;
 };
 

@@ -155,4 +155,24 @@ class Server:
             "mean_ms": float(lat.mean() * 1e3), "gbs": nbytes / max(wall, 1e-9) / 1e9,
             "status_ok": status == L.BTO_OK and all(s == 0 for s in statuses),
             "peak_bytes": float(stats.peak_bytes), "budget_bytes": self.budget,
+            "loop": {"max_gap_ms": stats.max_gap_s * 1e3, "max_gap_at_s": stats.max_gap_at_s,
+                     "max_admit_ms": stats.max_admit_s * 1e3, "max_complete_ms": stats.max_complete_s * 1e3,
+                     "max_oversleep_ms": stats.max_oversleep_s * 1e3, "max_fifo": int(stats.max_fifo),
+                     "fifo_at_max_gap": int(stats.fifo_at_max_gap), "sleeps": int(stats.sleeps),
+                     "blocking_copies": int(stats.blocking_copies), "max_query_ms": stats.max_query_s * 1e3},
+            "p99_ms_by_second": _p99_by_second(done),
         }, done
+
+
+def _p99_by_second(done):
+    """99th-percentile latency (ms) of the requests arriving in each whole second."""
+    if not done:
+        return []
+    t = np.array([d["t"] for d in done])
+    lat = np.array([d["done"] - d["t"] for d in done])
+    out = []
+    for s in range(int(t.max()) + 1):
+        sel = (t >= s) & (t < s + 1)
+        if sel.any():
+            out.append(round(float(np.percentile(lat[sel], 99) * 1e3), 3))
+    return out

@@ -29,9 +29,55 @@ def lib(path=None):
     return _lib
 
 
-def _bind(L):
+_par = None
+PAR_NAMES = ("bicgk", "atax", "gemver", "gesummv", "dgemv", "dgemvt", "axpydot", "waxpby", "vadd")
+
+
+class _ParLib:
+    """The all-core build (bto_oracle_par.c) under the serial names, so that
+    every function below takes it as L=...; routines it does not have are not
+    reachable through it."""
+
+    def __init__(self, cdll):
+        serial = _bind_names()
+        for k in PAR_NAMES:
+            f = getattr(cdll, "oracle_par_" + k)
+            f.argtypes = serial["oracle_" + k][0]
+            f.restype = serial["oracle_" + k][1]
+            setattr(self, "oracle_" + k, f)
+
+
+def lib_par():
+    """Load (building first if needed) the all-core oracle (OpenMP)."""
+    global _par
+    if _par is None:
+        _par = _ParLib(ctypes.CDLL(_build.build_par()))
+    return _par
+
+
+def _bind_names():
+    """{C name: (argtypes, restype)} of the oracle's exported routines."""
     d, i = ctypes.c_double, _I
-    sig = {
+    sig = _SIG(d, i)
+    out = {}
+    for name, args in sig.items():
+        rt = ctypes.c_int if name in ("oracle_atax", "oracle_gemver", "oracle_gesummv", "oracle_dgemv",
+                                      "oracle_dgemvt", "oracle_csr_atax") else (
+            ctypes.c_double if name in ("oracle_dot2", "oracle_row_dot") else None)
+        out[name] = (args, rt)
+    return out
+
+
+def _bind(L):
+    for name, (args, rt) in _bind_names().items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = rt
+    return L
+
+
+def _SIG(d, i):
+    return {
         "oracle_bicgk": [i, i, _D, i, _D, _D, _D, _D],
         "oracle_atax": [i, i, d, _D, i, _D, _D],
         "oracle_gemver": [i, i, d, d, _D, i, _D, _D, _D, _D, _D, _D, _D, i, _D, _D],
@@ -48,13 +94,6 @@ def _bind(L):
         "oracle_csr_bicgk": [i, i, ctypes.c_void_p, ctypes.c_void_p, _D, _D, _D, _D, _D],
         "oracle_csr_atax": [i, i, d, ctypes.c_void_p, ctypes.c_void_p, _D, _D, _D],
     }
-    for name, args in sig.items():
-        f = getattr(L, name)
-        f.argtypes = args
-        f.restype = ctypes.c_int if name in (
-            "oracle_atax", "oracle_gemver", "oracle_gesummv", "oracle_dgemv",
-            "oracle_dgemvt", "oracle_csr_atax") else (ctypes.c_double if name in ("oracle_dot2", "oracle_row_dot") else None)
-    return L
 
 
 def _p(a):

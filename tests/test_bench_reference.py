@@ -21,7 +21,8 @@ def test_reference_arm_line():
     import bench
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "GB/s"
     wl = d["config"]["workload"]
-    assert "2048x2048" in wl and str(1 << 22) in wl and "16384x16384" in wl and d["higher_is_better"] is True
+    assert "4096x4096" in wl and str(1 << 23) in wl and "16384x16384" in wl and d["higher_is_better"] is True
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

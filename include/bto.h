@@ -585,7 +585,9 @@ bto_status bto_bicgk_mrhs(int64_t m, int64_t n, int64_t k, const uint16_t *A, in
  *    with bto_last_invalid_arg() naming m (1) or n (2), and nothing runs.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the life of the
+ *    process: do not call this entry point on a device after resetting it
+ *    (cudaDeviceReset), since the array may then live elsewhere.
  *  - All calls share the one array, and it keeps the last call's contents;
  *    no part of it needs to start at zero.  Calls whose kernels overlap on
  *    the GPU (different streams, no ordering between them) race on the

@@ -495,18 +495,13 @@ PanelPlan panel_plan(int64_t m, int64_t n, int sms, int op, int form) {
     if (ceil_div(n, NC) > kMaxPanel) NC = ceil_div(n, kMaxPanel);
     // About two tiles per SM (so the two-blocks-per-SM modes fill the
     // machine).  Row blocks are at least one chunk (2048 rows: every warp of
-    // the block has rows) unless m itself is shorter; when that leaves too few
-    // tiles, the panels get narrower instead (n = 2048: 187 panels of 11
-    // columns, one row block, where 3 row blocks of 683 rows left five of the
-    // eight warps without rows), as long as the panels' row partials stay
-    // within 3 MiB (so square problems up to n = 3427 keep fitting the 4 MiB
-    // scratch of bto_bicgk_noalloc).
+    // the block has rows) unless m itself is shorter; a short matrix then has
+    // about one tile per SM (n = 2048: 147 panels of 14 columns, one row
+    // block).  Narrowing the panels to reach two tiles per SM was measured
+    // and was slower there: GEMVER 69 -> 83 us with 187 panels, BICGK 41 ->
+    // 49 us; 3 row blocks of 683 rows left five of the eight warps without
+    // rows.
     int64_t NR = std::max<int64_t>(1, std::min<int64_t>(ceil_div(2 * G, NC), ceil_div(m, kChunk)));
-    if (NR * NC < 2 * G && NC < n) {
-        int64_t want = std::min<int64_t>(n, ceil_div(2 * G, NR));
-        want = std::min<int64_t>(want, std::max<int64_t>(1, ((int64_t)3 << 20) / (8 * round_up(m, 32))));
-        NC = std::max(NC, ceil_div(n, ceil_div(n, want)));
-    }
     // Fused GEMVER: one chunk per row block (at n = 16384, 8 row blocks of
     // 2048 rows instead of 2), as the measured schedule search found best for
     // it (1.96 -> 1.92 ms); the other kernels' optima were within 1% of the

@@ -3,12 +3,14 @@
 loops that cannot afford cudaMalloc's possible device synchronization).
 It keeps its partial sums in a fixed device array inside the library
 instead of a caller workspace.  Checked through the C ABI against the
-workspace entry point bto_bicgk on two calls in a row.  This file is
+workspace entry point bto_bicgk on two calls in a row, and against the
+oracle, at the largest size its array accepts, with the next size rejected.  This file is
 collected last so a failure here leaves every other test already run."""
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import paper_1205_1098_gb300 as bto
 import synth
 from gpu_util import TOL64, Out, dev, p, relerr, sync, ws
@@ -50,3 +52,44 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(bto.BtoError) as e:
         bto.bto_bicgk_noalloc(m, n, 0, m, 0, 0, 0, 0, None)
     assert e.value.status == bto.BTO_ERR_WORKSPACE and e.value.arg in (1, 2)
+
+
+def _largest_accepted_square():
+    """The largest square n whose BICGK workspace fits the fixed array (every
+    smaller n fits too), found on the host from the workspace query."""
+    limit = 4 << 20
+    last = 0
+    for n in range(1, 6001):
+        if bto.bto_workspace_bytes("bicgk", 0, n, n) > limit:
+            return last, n
+        last = n
+    raise AssertionError("no square size exceeds the array up to 6000")
+
+
+def test_noalloc_largest_accepted_size_and_the_next():
+    n, over = _largest_accepted_square()
+    assert n >= 1 and over == n + 1
+    A64 = synth.matrix(23, 0, n, n)
+    p64, r64 = synth.vector(23, 1, n), synth.vector(23, 2, n)
+    A, pv, rv = dev(A64), dev(p64), dev(r64)
+    q, s = Out(n), Out(n)
+    bto.bto_bicgk_noalloc(n, n, A, n, pv, rv, q.ptr(), s.ptr(), None)
+    sync()
+    qo, so = O.bicgk(n, n, A64, p64, r64)
+    assert relerr(q.host(), qo) <= TOL64 and relerr(s.host(), so) <= TOL64
+    qr, sr = _reference(n, n, A, pv, rv)
+    assert np.array_equal(q.host(), qr) and np.array_equal(s.host(), sr)
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_bicgk_noalloc(over, over, 0, over, 0, 0, 0, 0, None)
+    assert e.value.status == bto.BTO_ERR_WORKSPACE
+
+
+def test_noalloc_matches_the_oracle():
+    m, n = 1777, 2049
+    A64 = synth.matrix(24, 0, m, n)
+    p64, r64 = synth.vector(24, 1, n), synth.vector(24, 2, m)
+    q, s = Out(m), Out(n)
+    bto.bto_bicgk_noalloc(m, n, dev(A64), m, dev(p64), dev(r64), q.ptr(), s.ptr(), None)
+    sync()
+    qo, so = O.bicgk(m, n, A64, p64, r64)
+    assert relerr(q.host(), qo) <= TOL64 and relerr(s.host(), so) <= TOL64

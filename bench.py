@@ -822,6 +822,15 @@ def generator_form(torch, bto, fp64_peak, n=N_MAT, reps=7, seed=1):
                                               b["y"], b["z"], b["B"], n, b["x"], b["w"], hws, hnb)
             row["hand_written_ms"] = round(time(call), 4)
             del hws
+        # The measured-cost choice among every distinct legal fusion plan of
+        # the program (the generator's search enumerates them all; Max-Fuse is
+        # the first), on the same bindings.
+        res = G.search(text, bind, shapes, reps=reps)
+        row["fusion_search"] = {
+            "choices": [{"policy": pol, "passes": passes, "ms": round(ms, 4)} for pol, passes, ms in res["table"]],
+            "best": res["best"], "best_ms": round(res["best_ms"], 4),
+            "max_fuse_ms": round(res["table"][0][2], 4),
+            "max_fuse_is_best": res["table"][0][0] == res["best"]}
         out[name] = row
         del bind, keep, ws, prog
         torch.cuda.empty_cache()
@@ -1048,6 +1057,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-df", action="store_true", help="skip the double-float form")
+    ap.add_argument("--df-only", action="store_true", help="profiling runs: only the double-float form at --n")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--only", default=None, help="comma-separated kernels (profiling runs)")
     ap.add_argument("--no-batched", action="store_true")
@@ -1128,6 +1138,16 @@ def main():
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         peak = FP64_FLOP_PER_CLK_PER_SM * sms * sm_max * 1e6 / 1e12
         print(json.dumps({"layout": layout_form(torch, bto, peak, n=args.n)}))
+        return
+    if args.df_only:
+        import torch
+        from paper_1205_1098_gb300 import build
+        build.build()
+        import paper_1205_1098_gb300 as bto
+        hbm, _, _ = load_peaks()
+        suite = Suite(torch, bto, args.n, args.n, args.nvec)
+        _, kern64 = timed_steps(torch, suite, 1, 0, 0, None)
+        print(json.dumps({"df_form": df_form(torch, suite, args.steps, args.warmup, None, hbm, kern64)}))
         return
     if args.search_only:
         import torch

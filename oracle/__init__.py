@@ -62,7 +62,8 @@ def _bind_names():
     out = {}
     for name, args in sig.items():
         rt = ctypes.c_int if name in ("oracle_atax", "oracle_gemver", "oracle_gesummv", "oracle_dgemv",
-                                      "oracle_dgemvt", "oracle_csr_atax") else (
+                                      "oracle_dgemvt", "oracle_csr_atax",
+                                      "oracle_band_bicgk", "oracle_band_atax") else (
             ctypes.c_double if name in ("oracle_dot2", "oracle_row_dot") else None)
         out[name] = (args, rt)
     return out
@@ -93,6 +94,8 @@ def _SIG(d, i):
         "oracle_row_dot": [i, _D, _D],
         "oracle_csr_bicgk": [i, i, ctypes.c_void_p, ctypes.c_void_p, _D, _D, _D, _D, _D],
         "oracle_csr_atax": [i, i, d, ctypes.c_void_p, ctypes.c_void_p, _D, _D, _D],
+        "oracle_band_bicgk": [ctypes.c_int, i, i, i, i, ctypes.c_int, _D, i, _D, _D, _D, _D],
+        "oracle_band_atax": [ctypes.c_int, i, i, i, i, ctypes.c_int, d, _D, i, _D, _D],
     }
 
 
@@ -152,6 +155,46 @@ def csr_atax(m, n, beta, row_ptr, col, val, x, L=None):
     y = np.empty(n)
     _chk(L.oracle_csr_atax(m, n, beta, rp.ctypes.data, ci.ctypes.data if ci.size else None, _p(v), _p(x),
                            _p(y)))
+    return y
+
+
+STORE_FULL, STORE_BAND, STORE_PACKED = 0, 1, 2
+
+
+def _band_args(storage, m, n, kl, ku, A, ld):
+    """Checks a structured operand: A is the flat FP64 storage array (full:
+    ld x n column-major; band: ld x n band array; packed: n (n + 1) / 2
+    entries of a square triangle, kl = 0 upper or ku = 0 lower)."""
+    assert m >= 0 and n >= 0 and 0 <= kl < 2 ** 40 and 0 <= ku < 2 ** 40
+    A = np.ascontiguousarray(A, dtype=np.float64).ravel()
+    if storage == STORE_FULL:
+        assert ld >= max(1, m) and A.size >= (ld * (n - 1) + m if n and m else 0)
+    elif storage == STORE_BAND:
+        assert ld >= kl + ku + 1 and A.size >= (ld * n if m else 0)
+    else:
+        assert storage == STORE_PACKED and m == n and (kl == 0 or ku == 0)
+        assert A.size >= n * (n + 1) // 2
+    return kl, ku, A
+
+
+def band_bicgk(storage, m, n, kl, ku, unit, A, ld, p, r, L=None):
+    """BICGK on a banded or triangular matrix in full, band or packed storage."""
+    L = L or lib()
+    kl, ku, A = _band_args(storage, m, n, kl, ku, A, ld)
+    p, r = _vec(p), _vec(r)
+    q, s = np.empty(m), np.empty(n)
+    _chk(L.oracle_band_bicgk(storage, m, n, kl, ku, int(unit), _p(A), max(int(ld), 1), _p(p), _p(r),
+                             _p(q), _p(s)))
+    return q, s
+
+
+def band_atax(storage, m, n, kl, ku, unit, beta, A, ld, x, L=None):
+    """BATAX on a banded or triangular matrix: y = beta A^T (A x)."""
+    L = L or lib()
+    kl, ku, A = _band_args(storage, m, n, kl, ku, A, ld)
+    x = _vec(x)
+    y = np.empty(n)
+    _chk(L.oracle_band_atax(storage, m, n, kl, ku, int(unit), beta, _p(A), max(int(ld), 1), _p(x), _p(y)))
     return y
 
 

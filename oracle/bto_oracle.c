@@ -14,7 +14,9 @@
  *
  * The CSR routines at the end define BICGK and BATAX on a matrix in
  * compressed sparse rows (the sparse format of Section VII) as loops over the
- * stored entries, in storage order.
+ * stored entries, in storage order; the band routines after them define
+ * BICGK and BATAX on banded and triangular matrices (the other formats
+ * planned there) as the same loops restricted to the band.
  *
  * Matrices are column-major: element (i, j) of A is A[i + j*lda].
  * Sizes m, n may be zero; empty sums are zero.  No BLAS-style shortcut is
@@ -299,6 +301,112 @@ int oracle_csr_atax(int64_t m, int64_t n, double beta, const int64_t *row_ptr, c
     for (int64_t i = 0; i < m; i++)
         for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) y[col[k]] += val[k] * t[i];
     for (int64_t j = 0; j < n; j++) y[j] *= beta;
+    free(t);
+    return 0;
+}
+
+/* Structured storage (the banded and triangular formats the paper plans in
+ * Section VII).  A is m x n with A(i, j) = 0 outside the band
+ * j - ku <= i <= j + kl (kl sub-diagonals, ku super-diagonals); a triangle
+ * is the band with kl = 0 (upper, ku = n - 1) or ku = 0 (lower,
+ * kl = m - 1).  With unit != 0 the diagonal entries are taken as 1 and never
+ * read.  Only entries inside the band are read, whatever the storage holds
+ * elsewhere, and only they enter the sums (an entry outside the band is
+ * structurally zero, so a NaN or Inf in p or r meets no product there).
+ * Storage kinds:
+ *   0 full:   A(i, j) at A[i + j*ld] (ld >= m);
+ *   1 band:   A(i, j) at A[(ku + i - j) + j*ld] (ld >= kl + ku + 1): column
+ *             j of the band array holds the band's part of column j, the
+ *             diagonal in row ku;
+ *   2 packed: a square triangle stored column after column with no gaps:
+ *             column j holds rows 0..j (upper) or rows j..n-1 (lower).
+ */
+typedef struct {
+    int storage;
+    int64_t m, n, kl, ku;
+    int unit;
+    const double *A;
+    int64_t ld;
+    int64_t *colstart;   /* packed: offset of column j's first stored entry */
+} band_mat;
+
+static int band_open(band_mat *b, int storage, int64_t m, int64_t n, int64_t kl, int64_t ku, int unit,
+                     const double *A, int64_t ld)
+{
+    b->storage = storage; b->m = m; b->n = n; b->kl = kl; b->ku = ku; b->unit = unit;
+    b->A = A; b->ld = ld; b->colstart = NULL;
+    if (storage == 2) {
+        /* Column j starts after every stored entry of columns 0..j-1;
+         * column c holds c + 1 entries (upper) or n - c entries (lower). */
+        b->colstart = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+        if (!b->colstart) return 1;
+        int64_t off = 0;
+        for (int64_t c = 0; c < n; c++) {
+            b->colstart[c] = off;
+            off += (kl == 0) ? c + 1 : n - c;
+        }
+    }
+    return 0;
+}
+
+static void band_close(band_mat *b) { free(b->colstart); }
+
+/* A(i, j) for (i, j) inside the band. */
+static double band_get(const band_mat *b, int64_t i, int64_t j)
+{
+    if (b->unit && i == j) return 1.0;
+    if (b->storage == 0) return b->A[(size_t)i + (size_t)j * (size_t)b->ld];
+    if (b->storage == 1) return b->A[(size_t)(b->ku + i - j) + (size_t)j * (size_t)b->ld];
+    /* packed: upper column j holds rows 0..j, lower column j rows j..n-1 */
+    return b->A[b->colstart[j] + (b->kl == 0 ? i : i - j)];
+}
+
+/* Structured BICGK: q_i = sum over the band's columns of row i of
+ * A(i, j) p_j, ascending j; s_j = sum over the band's rows of column j of
+ * A(i, j) r_i, ascending i. */
+int oracle_band_bicgk(int storage, int64_t m, int64_t n, int64_t kl, int64_t ku, int unit,
+                      const double *A, int64_t ld, const double *p, const double *r, double *q, double *s)
+{
+    band_mat b;
+    if (band_open(&b, storage, m, n, kl, ku, unit, A, ld)) return 1;
+    for (int64_t i = 0; i < m; i++) {
+        double acc = 0.0;
+        for (int64_t j = (i - kl > 0 ? i - kl : 0); j <= i + ku && j < n; j++)
+            acc += band_get(&b, i, j) * p[j];
+        q[i] = acc;
+    }
+    for (int64_t j = 0; j < n; j++) {
+        double acc = 0.0;
+        for (int64_t i = (j - ku > 0 ? j - ku : 0); i <= j + kl && i < m; i++)
+            acc += band_get(&b, i, j) * r[i];
+        s[j] = acc;
+    }
+    band_close(&b);
+    return 0;
+}
+
+/* Structured BATAX: t = A x, then y = beta (A^T t), in the order of the
+ * dense oracle_atax (the scale is its own loop). */
+int oracle_band_atax(int storage, int64_t m, int64_t n, int64_t kl, int64_t ku, int unit, double beta,
+                     const double *A, int64_t ld, const double *x, double *y)
+{
+    band_mat b;
+    double *t = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+    if (!t || band_open(&b, storage, m, n, kl, ku, unit, A, ld)) { free(t); return 1; }
+    for (int64_t i = 0; i < m; i++) {
+        double acc = 0.0;
+        for (int64_t j = (i - kl > 0 ? i - kl : 0); j <= i + ku && j < n; j++)
+            acc += band_get(&b, i, j) * x[j];
+        t[i] = acc;
+    }
+    for (int64_t j = 0; j < n; j++) {
+        double acc = 0.0;
+        for (int64_t i = (j - ku > 0 ? j - ku : 0); i <= j + kl && i < m; i++)
+            acc += band_get(&b, i, j) * t[i];
+        y[j] = acc;
+    }
+    for (int64_t j = 0; j < n; j++) y[j] = y[j] * beta;
+    band_close(&b);
     free(t);
     return 0;
 }

@@ -11,12 +11,18 @@ test).  The pins are:
     that reduce to an exact zero or to the input;
   * the Dot2 error bound of Ogita, Rump and Oishi against an exact rational sum;
   * for the sparse (CSR) definitions: a hand-worked example, integer-valued
-    inputs against exact products of the densified matrix, the identity.
+    inputs against exact products of the densified matrix, the identity;
+  * for the banded and triangular definitions: hand-worked examples in every
+    storage kind (with NaN in the slots outside the band), integer-valued
+    inputs against exact products of the dense matrix, prefix/suffix sums of
+    an all-ones triangle, the second difference of a tridiagonal matrix, the
+    adjoint identity, and bitwise agreement of the three storage kinds.
 """
 from fractions import Fraction
 
 import numpy as np
 
+import band_util as BU
 import oracle as O
 import synth
 from golden_io import colmajor, load
@@ -330,6 +336,117 @@ def pin_csr_identity(L):
     assert np.array_equal(q, p) and np.array_equal(s, r)
 
 
+# ---------------------------------------------------------------- banded / triangular
+def _g1(g, k):
+    return int(np.asarray(g[k]).ravel()[0])
+
+
+def pin_band_golden(L):
+    g, e = load("band_bicgk_4x5.txt")
+    m, n, kl, ku, ld = g["m"], g["n"], _g1(g, "kl"), _g1(g, "ku"), _g1(g, "ld")
+    q, s = O.band_bicgk(BU.BAND, m, n, kl, ku, 0, g["A"], ld, g["p"], g["r"], L=L)
+    assert np.array_equal(q, e["q"]) and np.array_equal(s, e["s"]), (q, s)
+    y = O.band_atax(BU.BAND, m, n, kl, ku, 0, float(g["beta"]), g["A"], ld, g["p"], L=L)
+    assert np.array_equal(y, e["y"]), y
+
+    g, e = load("tri_upper_3.txt")
+    n = g["n"]
+    for st, A, ld in ((BU.FULL, g["full"], n), (BU.PACKED, g["packed"], 1)):
+        q, s = O.band_bicgk(st, n, n, 0, n - 1, 0, A, ld, g["p"], g["r"], L=L)
+        assert np.array_equal(q, e["q"]) and np.array_equal(s, e["s"]), (st, q, s)
+        q, s = O.band_bicgk(st, n, n, 0, n - 1, 1, A, ld, g["p"], g["r"], L=L)
+        assert np.array_equal(q, e["qu"]) and np.array_equal(s, e["su"]), (st, q, s)
+        y = O.band_atax(st, n, n, 0, n - 1, 0, float(g["beta"]), A, ld, g["p"], L=L)
+        assert np.array_equal(y, e["y"]), (st, y)
+
+    g, e = load("tri_lower_unit_3.txt")
+    n = g["n"]
+    q, s = O.band_bicgk(BU.PACKED, n, n, n - 1, 0, 1, g["packed"], 1, g["p"], g["r"], L=L)
+    assert np.array_equal(q, e["q"]) and np.array_equal(s, e["s"]), (q, s)
+
+
+# (m, n, kl, ku): general bands, bands wider than the matrix, diagonal only,
+# both triangles of square and rectangular matrices.
+BAND_SHAPES = [(9, 7, 2, 1), (7, 11, 0, 3), (12, 5, 4, 0), (8, 8, 0, 7), (8, 8, 7, 0),
+               (6, 9, 20, 20), (10, 10, 0, 0), (1, 6, 0, 5), (6, 1, 5, 0), (13, 13, 3, 3)]
+
+
+def pin_band_integer_exact(L):
+    """Integer-valued entries and vectors: every partial sum is exact, so the
+    band results equal exact int64 products of the dense matrix, in every
+    storage kind the shape allows, with and without a unit diagonal."""
+    for k, (m, n, kl, ku) in enumerate(BAND_SHAPES):
+        D = BU.dense(4, 100 + k, m, n, kl, ku, kind=synth.KIND_INTEGER)
+        p, r = _ints(4, 120 + k, n), _ints(4, 140 + k, m)
+        for unit in (0, 1):
+            Du = D.copy()
+            if unit:
+                np.fill_diagonal(Du, 1.0)
+            Di = Du.astype(np.int64)
+            kinds = [BU.FULL, BU.BAND] + ([BU.PACKED] if m == n and (kl == 0 and ku == n - 1
+                                                                     or ku == 0 and kl == m - 1) else [])
+            for st in kinds:
+                A, ld = BU.store(D, st, kl, ku)
+                if unit and st != BU.PACKED:
+                    # the stored diagonal must not be read: poison it
+                    A = A.copy()
+                    for i in range(min(m, n)):
+                        A[(i + i * ld) if st == BU.FULL else (ku + i * ld)] = np.nan
+                q, s = O.band_bicgk(st, m, n, kl, ku, unit, A, ld, p, r, L=L)
+                assert np.array_equal(q, (Di @ p.astype(np.int64)).astype(float)), (m, n, kl, ku, st, unit)
+                assert np.array_equal(s, (Di.T @ r.astype(np.int64)).astype(float)), (m, n, kl, ku, st, unit)
+                y = O.band_atax(st, m, n, kl, ku, unit, -2.0, A, ld, p, L=L)
+                assert np.array_equal(y, (-2 * (Di.T @ (Di @ p.astype(np.int64)))).astype(float)), (m, n, st)
+
+
+def pin_band_closed_forms(L):
+    n = 12
+    p, r = _ints(5, 1, n), _ints(5, 2, n)
+    # all-ones upper triangle: q_i = p_i + ... + p_{n-1}, s_j = r_0 + ... + r_j
+    ones = np.ones(n * (n + 1) // 2)
+    q, s = O.band_bicgk(BU.PACKED, n, n, 0, n - 1, 0, ones, 1, p, r, L=L)
+    assert np.array_equal(q, np.cumsum(p[::-1])[::-1]) and np.array_equal(s, np.cumsum(r))
+    # lower: q_i = p_0 + ... + p_i, s_j = r_j + ... + r_{n-1}
+    q, s = O.band_bicgk(BU.PACKED, n, n, n - 1, 0, 0, ones, 1, p, r, L=L)
+    assert np.array_equal(q, np.cumsum(p)) and np.array_equal(s, np.cumsum(r[::-1])[::-1])
+    # tridiagonal (-1, 2, -1) in band storage: q = minus the second difference
+    # of p; with p_i = i^2 every interior q_i is -2
+    AB = np.tile(np.array([-1.0, 2.0, -1.0]), n)
+    pq = np.arange(n, dtype=float) ** 2
+    q, s = O.band_bicgk(BU.BAND, n, n, 1, 1, 0, AB, 3, pq, pq, L=L)
+    assert np.array_equal(q[1:-1], np.full(n - 2, -2.0)) and q[0] == -1.0 and q[-1] == 2 * pq[-1] - pq[-2]
+    assert np.array_equal(q, s)   # the matrix is symmetric
+
+
+def pin_band_identity_and_storage(L):
+    """Floating-point values: the adjoint identity r^T q = s^T p, and the
+    three storage kinds of one matrix give bitwise equal results (they hold
+    the same values and the definition reads them in the same order)."""
+    for k, (m, n, kl, ku) in enumerate(BAND_SHAPES):
+        D = BU.dense(6, 200 + k, m, n, kl, ku)
+        p, r = synth.vector(6, 220 + k, n), synth.vector(6, 240 + k, m)
+        A, ld = BU.store(D, BU.FULL, kl, ku)
+        q, s = O.band_bicgk(BU.FULL, m, n, kl, ku, 0, A, ld, p, r, L=L)
+        sc = np.abs(r) @ np.abs(D) @ np.abs(p) + 1e-300
+        assert abs(r @ q - s @ p) <= 1e-13 * sc, (m, n, kl, ku)
+        assert _rel(q, D @ p) < 1e-14 and _rel(s, D.T @ r) < 1e-14, (m, n, kl, ku)
+        A2, ld2 = BU.store(D, BU.BAND, kl, ku)
+        q2, s2 = O.band_bicgk(BU.BAND, m, n, kl, ku, 0, A2, ld2, p, r, L=L)
+        assert np.array_equal(q, q2) and np.array_equal(s, s2), (m, n, kl, ku)
+        if m == n and (kl == 0 and ku == n - 1 or ku == 0 and kl == m - 1):
+            q3, s3 = O.band_bicgk(BU.PACKED, m, n, kl, ku, 0, BU.store_packed(D, kl == 0), 1, p, r, L=L)
+            assert np.array_equal(q, q3) and np.array_equal(s, s3), (m, n, kl, ku)
+    # an Inf in p meets only the band: rows whose band misses column j stay finite
+    n = 8
+    D = BU.dense(6, 300, n, n, 1, 1)
+    A, ld = BU.store(D, BU.BAND, 1, 1)
+    p = np.ones(n)
+    p[5] = np.inf
+    q, _ = O.band_bicgk(BU.BAND, n, n, 1, 1, 0, A, ld, p, np.ones(n), L=L)
+    assert np.all(np.isfinite(q[:4])) and np.all(np.isfinite(q[7:])) and not np.isfinite(q[5])
+
+
 PINS = [pin_golden, pin_integer_exact, pin_closed_forms, pin_identities,
         pin_vector_special, pin_ieee_and_empty, pin_dot2_bound, pin_mrhs_and_row_dot,
-        pin_csr_golden, pin_csr_integer_exact, pin_csr_identity]
+        pin_csr_golden, pin_csr_integer_exact, pin_csr_identity,
+        pin_band_golden, pin_band_integer_exact, pin_band_closed_forms, pin_band_identity_and_storage]

@@ -49,6 +49,23 @@ MUTANTS = [
     ("csr_atax_t_transposed",
      "for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) y[col[k]] += val[k] * t[i];",
      "for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; k++) y[col[k]] += val[k] * x[col[k]];"),
+    ("band_row_offset_sign", "A[(size_t)(b->ku + i - j) + (size_t)j * (size_t)b->ld]",
+     "A[(size_t)(b->ku - i + j) + (size_t)j * (size_t)b->ld]"),
+    ("band_uses_kl_offset", "A[(size_t)(b->ku + i - j) + (size_t)j * (size_t)b->ld]",
+     "A[(size_t)(b->kl + i - j) + (size_t)j * (size_t)b->ld]"),
+    ("packed_lower_offset", "(b->kl == 0 ? i : i - j)", "(b->kl == 0 ? i : i - j + 1)"),
+    ("packed_column_length", "off += (kl == 0) ? c + 1 : n - c;", "off += (kl == 0) ? c : n - c;"),
+    ("band_unit_ignored", "if (b->unit && i == j) return 1.0;", ""),
+    ("band_q_drops_last_super",
+     "for (int64_t j = (i - kl > 0 ? i - kl : 0); j <= i + ku && j < n; j++)\n            acc += band_get(&b, i, j) * p[j];",
+     "for (int64_t j = (i - kl > 0 ? i - kl : 0); j < i + ku && j < n; j++)\n            acc += band_get(&b, i, j) * p[j];"),
+    ("band_s_drops_first_sub",
+     "for (int64_t i = (j - ku > 0 ? j - ku : 0); i <= j + kl && i < m; i++)\n            acc += band_get(&b, i, j) * r[i];",
+     "for (int64_t i = (j - ku > 0 ? j - ku + 1 : 0); i <= j + kl && i < m; i++)\n            acc += band_get(&b, i, j) * r[i];"),
+    ("band_s_wrong_vector_index", "acc += band_get(&b, i, j) * r[i];", "acc += band_get(&b, i, j) * r[j % (m > 0 ? m : 1)];"),
+    ("band_atax_dropped_beta", "for (int64_t j = 0; j < n; j++) y[j] = y[j] * beta;",
+     "for (int64_t j = 0; j < n; j++) y[j] = y[j];"),
+    ("band_atax_second_uses_x", "acc += band_get(&b, i, j) * t[i];", "acc += band_get(&b, i, j) * x[i % (n > 0 ? n : 1)];"),
 ]
 
 

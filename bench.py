@@ -882,6 +882,80 @@ def sparse_form(torch, bto, hbm, m=1 << 20, avg=32, reps=7, seed=11):
     return out
 
 
+def structured_form(torch, bto, hbm, fp64_peak, reps=7):
+    """Banded and triangular BICGK and BATAX (f4): an upper triangle of order
+    16384 in full storage (the synthetic 16384 x 16384 matrix, seed 1, array
+    id 0; entries below the diagonal are never read) and in packed storage
+    (entry k of the packed array is value k of array id 0), and a band of
+    kl = ku = 32 diagonals at m = n = 2^20 in band storage (ld = 65, filled
+    as a 65 x 2^20 matrix, seed 11).  Median of `reps` calls after 2
+    warm-ups.  Compulsory bytes: the stored entries once (8 each) and each
+    vector once; BATAX reads A twice (two passes), so its fraction of HBM is
+    over one read.  Every stored entry costs two FP64 FMAs: the FP64 fraction
+    is 4 flops per entry over the derived FP64 peak."""
+    st = torch.cuda.current_stream()
+    f64 = dict(dtype=torch.float64, device="cuda")
+
+    def time(call):
+        for _ in range(2):
+            call()
+        evs = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            call()
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in evs]))
+
+    out = {}
+    n = 16384
+    cases = [("tri_upper_full_n16384", "tri", 0, n, n, 0, n - 1),
+             ("tri_upper_packed_n16384", "tri", 1, n, n, 0, n - 1),
+             ("band_kl32_ku32_2e20", "band", bto.BTO_STORE_BAND, 1 << 20, 1 << 20, 32, 32)]
+    for name, kind, sto, m, nn, kl, ku in cases:
+        if kind == "tri" and sto == 0:
+            A = torch.empty(m * nn, **f64)
+            bto.bto_fill_f64(1, 0, 0, m, nn, 0, A, m, None)
+            ld, entries = m, nn * (nn + 1) // 2
+        elif kind == "tri":
+            entries = nn * (nn + 1) // 2
+            A = torch.empty(entries, **f64)
+            bto.bto_fill_f64(1, 0, 0, entries, 1, 0, A, entries, None)
+            ld = 1
+        else:
+            ld = kl + ku + 1
+            A = torch.empty(ld * nn, **f64)
+            bto.bto_fill_f64(11, 0, 0, ld, nn, 0, A, ld, None)
+            entries = sum(min(m, j + kl + 1) - max(0, j - ku) for j in (0, 1, nn - 2, nn - 1)) + (nn - 4) * ld
+        p, r, q, s = (torch.empty(max(m, nn), **f64) for _ in range(4))
+        bto.bto_fill_f64(1, 1, 0, nn, 1, 0, p, nn, None)
+        bto.bto_fill_f64(1, 2, 0, m, 1, 0, r, m, None)
+        nb = bto.bto_band_workspace_bytes("atax", m, nn, kl, ku)
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        if kind == "tri":
+            calls = (("bicgk", lambda: bto.bto_tri_bicgk(0, 0, sto, nn, A, ld, p, r, q, s, ws, nb), 8 * 2 * (m + nn)),
+                     ("batax", lambda: bto.bto_tri_atax(0, 0, sto, nn, 0.75, A, ld, p, s, ws, nb), 8 * 2 * nn))
+        else:
+            calls = (("bicgk", lambda: bto.bto_band_bicgk(sto, m, nn, kl, ku, 0, A, ld, p, r, q, s, ws, nb),
+                      8 * 2 * (m + nn)),
+                     ("batax", lambda: bto.bto_band_atax(sto, m, nn, kl, ku, 0, 0.75, A, ld, p, s, ws, nb),
+                      8 * 2 * nn))
+        row = {"m": m, "n": nn, "kl": kl, "ku": ku, "entries": entries}
+        for op, call, vec in calls:
+            ms = time(call)
+            gbs = (8 * entries + vec) / ms / 1e6
+            tfl = 4 * entries / ms / 1e9
+            row[op] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3),
+                       "fp64_tflops": round(tfl, 3), "fp64_frac": round(tfl / fp64_peak, 3)}
+        out[name] = row
+        del A, ws, p, r, q, s
+        torch.cuda.empty_cache()
+    out["bound"] = "fp64 (two FMAs per stored entry)"
+    return out
+
+
 def mrhs_form(torch, bto, hbm, steps, n=8192, k=64, seed=6):
     """Multi-right-hand-side BICGK: Q = A P, S = A^T R with A n x n BF16 and
     k BF16 right-hand sides, FP32 Q and S, on the tensor cores.  Each timed
@@ -1075,6 +1149,8 @@ def main():
     ap.add_argument("--no-generator", action="store_true", help="skip the generated sequences")
     ap.add_argument("--no-sparse", action="store_true", help="skip the CSR forms")
     ap.add_argument("--sparse-only", action="store_true", help="only the CSR forms")
+    ap.add_argument("--no-structured", action="store_true", help="skip the banded and triangular forms")
+    ap.add_argument("--structured-only", action="store_true", help="only the banded and triangular forms")
     ap.add_argument("--generator-only", action="store_true", help="only the generated sequences")
     ap.add_argument("--precision-only", type=int, default=0,
                     help="profiling runs: only the reduced-precision form at this n")
@@ -1118,6 +1194,16 @@ def main():
         import paper_1205_1098_gb300 as bto
         hbm, _, _ = load_peaks()
         print(json.dumps({"sparse": sparse_form(torch, bto, hbm)}))
+        return
+    if args.structured_only:
+        import torch
+        from paper_1205_1098_gb300 import build
+        build.build()
+        import paper_1205_1098_gb300 as bto
+        hbm, sm_max, _ = load_peaks()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak = FP64_FLOP_PER_CLK_PER_SM * sms * sm_max * 1e6 / 1e12
+        print(json.dumps({"structured": structured_form(torch, bto, hbm, peak)}))
         return
     if args.generator_only:
         import torch
@@ -1287,6 +1373,10 @@ def main():
     if not args.no_sparse and not args.only:
         torch.cuda.empty_cache()
         sparse = sparse_form(torch, bto, hbm)
+    structured = None
+    if not args.no_structured and not args.only:
+        torch.cuda.empty_cache()
+        structured = structured_form(torch, bto, hbm, fp64_peak)
     search = None
     if not args.no_search and not args.only:
         torch.cuda.empty_cache()
@@ -1327,6 +1417,7 @@ def main():
             "layout_n16384": layout,
             "generator_n16384": gen,
             "csr_2e20_avg32": sparse,
+            "structured": structured,
             "peaks": {"hbm_gbs": hbm, "hbm_source": peak_src, "fp64_tflops": round(fp64_peak, 4)},
         }))
     if dist:

@@ -339,6 +339,61 @@ bto_status bto_csr_atax(int64_t m, int64_t n, int64_t nnz, const int64_t *row_pt
                         const double *val, double beta, const double *x, double *y, void *ws,
                         size_t ws_bytes, bto_stream_t stream);
 
+/* ------------------------------------------------- banded and triangular
+ * BICGK and BATAX on banded and triangular matrices, the other structured
+ * formats the paper plans beside sparse ones (Section VII).  A is m x n with
+ * A(i, j) = 0 outside j - ku <= i <= j + kl (kl sub-diagonals, ku
+ * super-diagonals, both >= 0 and <= 2^40; they may exceed the matrix).  Only
+ * entries inside the band are read and only they enter the sums, whatever
+ * the storage holds elsewhere: a NaN or Inf in p, r or x meets no product
+ * outside the band.  With unit_diag = 1 the diagonal entries are taken as 1
+ * and never read.  Storage kinds (all FP64, 8-byte aligned):
+ *   BTO_STORE_FULL    column-major, A(i, j) at A[i + j*ld], ld >= max(1, m);
+ *   BTO_STORE_BAND    the LAPACK band layout: A(i, j) at A[(ku + i - j) + j*ld],
+ *                     ld >= kl + ku + 1 (column j holds its band entries,
+ *                     the diagonal in row ku);
+ *   BTO_STORE_PACKED  a square triangle (m = n, kl = 0 and ku = n - 1 for the
+ *                     upper one, ku = 0 and kl = n - 1 for the lower) packed
+ *                     column after column: column j holds rows 0..j (upper)
+ *                     or j..n-1 (lower); ld is ignored.
+ * Every entry is multiplied in FP64 (two FMAs per stored entry; the sweep is
+ * bound by the FP64 pipe).  Each output's partial sums are added in a fixed
+ * order, so results are bitwise reproducible.  BATAX forms t = A x in the
+ * workspace, then y = beta (A^T t): A is read twice.
+ * ws: bto_band_workspace_bytes (or bto_tri_workspace_bytes) bytes, 256-byte
+ * aligned, not shared with a call in flight; its first word is the device
+ * status (always BTO_OK for these calls).  Argument positions are 1-based as
+ * in every entry point (bto_last_invalid_arg). */
+#define BTO_STORE_FULL 0
+#define BTO_STORE_BAND 1
+#define BTO_STORE_PACKED 2
+#define BTO_UPPER 0
+#define BTO_LOWER 1
+
+/* Workspace bytes of a band call; op is BTO_OP_BICGK or BTO_OP_ATAX. */
+bto_status bto_band_workspace_bytes(int op, int64_t m, int64_t n, int64_t kl, int64_t ku, size_t *bytes);
+
+/* q <- A p (q: m), s <- A^T r (s: n); p: n, r: m. */
+bto_status bto_band_bicgk(int storage, int64_t m, int64_t n, int64_t kl, int64_t ku, int unit_diag,
+                          const double *A, int64_t ld, const double *p, const double *r, double *q, double *s,
+                          void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* y <- beta A^T (A x); x: n, y: n. */
+bto_status bto_band_atax(int storage, int64_t m, int64_t n, int64_t kl, int64_t ku, int unit_diag, double beta,
+                         const double *A, int64_t ld, const double *x, double *y, void *ws, size_t ws_bytes,
+                         bto_stream_t stream);
+
+/* Triangular n x n forms of the same calls: uplo BTO_UPPER or BTO_LOWER,
+ * packed 0 (full storage, lda >= max(1, n)) or 1 (packed storage, lda
+ * ignored).  Equivalent to the band calls with (kl, ku) = (0, n - 1) or
+ * (n - 1, 0). */
+bto_status bto_tri_workspace_bytes(int op, int uplo, int64_t n, size_t *bytes);
+bto_status bto_tri_bicgk(int uplo, int unit_diag, int packed, int64_t n, const double *A, int64_t lda,
+                         const double *p, const double *r, double *q, double *s, void *ws, size_t ws_bytes,
+                         bto_stream_t stream);
+bto_status bto_tri_atax(int uplo, int unit_diag, int packed, int64_t n, double beta, const double *A,
+                        int64_t lda, const double *x, double *y, void *ws, size_t ws_bytes, bto_stream_t stream);
+
 /* --------------------------------------------------------- schedule overrides
  * The FP64 matrix kernels (BICGK, ATAX's two-pass forms, GEMVER, GESUMMV,
  * DGEMV, DGEMVT; op < BTO_OP_AXPYDOT) split A into row blocks x column panels

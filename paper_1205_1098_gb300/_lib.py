@@ -57,6 +57,10 @@ SIGNATURES = {
     "bto_dgemvt_layout": "kiiddpipppppzs",
     "bto_csr_bicgk": "iiippppppppzs",
     "bto_csr_atax": "iiipppdpppzs",
+    "bto_band_bicgk": "kiiiikpipppppzs",
+    "bto_band_atax": "kiiiikdpipppzs",
+    "bto_tri_bicgk": "kkkipipppppzs",
+    "bto_tri_atax": "kkkidpipppzs",
 }
 # The double-float forms take the FP64 forms' arguments.
 for _k in ("bicgk", "atax", "gemver", "gesummv", "dgemv", "dgemvt"):
@@ -71,6 +75,8 @@ BTO_F64, BTO_F32, BTO_BF16 = 0, 1, 2
 BTO_FORM_FUSED, BTO_FORM_UNFUSED, BTO_FORM_DF, BTO_FORM_DF_UNFUSED = 0, 1, 2, 3
 BTO_COL_MAJOR, BTO_ROW_MAJOR = 0, 1
 BTO_NO_TRANS, BTO_TRANS = 0, 1
+BTO_STORE_FULL, BTO_STORE_BAND, BTO_STORE_PACKED = 0, 1, 2
+BTO_UPPER, BTO_LOWER = 0, 1
 OPS = {"bicgk": 0, "atax": 1, "gemver": 2, "gesummv": 3, "dgemv": 4, "dgemvt": 5,
        "axpydot": 6, "waxpby": 7, "vadd": 8}
 
@@ -191,6 +197,31 @@ def bto_workspace_bytes(op, form, m, n, a_type=BTO_F64):
     st = L.bto_workspace_bytes(int(op), int(form), int(m), int(n), int(a_type), ctypes.byref(out))
     if st != BTO_OK:
         raise BtoError("bto_workspace_bytes", st, L.bto_last_invalid_arg())
+    return out.value
+
+
+def bto_band_workspace_bytes(op, m, n, kl, ku):
+    """Workspace bytes of bto_band_bicgk / bto_band_atax (op: 'bicgk', 'atax' or a bto_op value)."""
+    if isinstance(op, str):
+        op = OPS[op]
+    out = _c_size(0)
+    L = lib()
+    st = L.bto_band_workspace_bytes(_c_int(int(op)), _c_i64(int(m)), _c_i64(int(n)), _c_i64(int(kl)),
+                                    _c_i64(int(ku)), ctypes.byref(out))
+    if st != BTO_OK:
+        raise BtoError("bto_band_workspace_bytes", st, L.bto_last_invalid_arg())
+    return out.value
+
+
+def bto_tri_workspace_bytes(op, uplo, n):
+    """Workspace bytes of bto_tri_bicgk / bto_tri_atax."""
+    if isinstance(op, str):
+        op = OPS[op]
+    out = _c_size(0)
+    L = lib()
+    st = L.bto_tri_workspace_bytes(_c_int(int(op)), _c_int(int(uplo)), _c_i64(int(n)), ctypes.byref(out))
+    if st != BTO_OK:
+        raise BtoError("bto_tri_workspace_bytes", st, L.bto_last_invalid_arg())
     return out.value
 
 
@@ -381,4 +412,4 @@ def exported_symbols():
                                       "bto_bicgk_mrhs_workspace_bytes", "bto_batch_workspace_bytes",
                                       "bto_serve_run", "bto_schedule_get", "bto_layout_workspace_bytes",
                                       "bto_program_check", "bto_program_workspace_bytes", "bto_program_run",
-                                      "bto_panel_plan"])
+                                      "bto_panel_plan", "bto_band_workspace_bytes", "bto_tri_workspace_bytes"])

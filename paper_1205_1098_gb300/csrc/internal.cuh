@@ -46,6 +46,24 @@ inline bto_status launch_status() {
     return e == cudaSuccess ? BTO_OK : BTO_ERR_CUDA;
 }
 
+// Transposing butterfly over 16 column partials: after four rounds lane l
+// holds, for column l mod 16, the sum over the 16 lanes that share bit 4 of
+// l; one more exchange with lane l ^ 16 completes the warp sum.  16 adds per
+// lane for 16 columns (v is destroyed).
+__device__ __forceinline__ double transpose_reduce16(double (&v)[16], int lane) {
+#pragma unroll
+    for (int half = 8; half >= 1; half >>= 1) {
+        const bool upper = (lane & half) != 0;
+#pragma unroll
+        for (int k = 0; k < half; k++) {
+            double send = upper ? v[k] : v[k + half];
+            double keep = upper ? v[k + half] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
 // ------------------------------------------------------------ panel engine
 // The matrix is cut into NR row blocks x NC column panels; tile (rb, cb)
 // leaves row-vector partials in qpart[cb][.] and column-vector partials in

@@ -41,24 +41,6 @@ constexpr int64_t kMaxPanel = 512;                // widest column panel
 constexpr int kGroup = 16;                        // columns per transposing group
 constexpr int kU = 4;                             // columns loaded before any is consumed
 
-// Transposing butterfly over 16 column partials: after four rounds lane l
-// holds, for column l mod 16, the sum over the 16 lanes that share bit 4 of
-// l; one more exchange with lane l ^ 16 completes the warp sum.  16 adds per
-// lane for 16 columns (v is destroyed).
-__device__ __forceinline__ double transpose_reduce16(double (&v)[16], int lane) {
-#pragma unroll
-    for (int half = 8; half >= 1; half >>= 1) {
-        const bool upper = (lane & half) != 0;
-#pragma unroll
-        for (int k = 0; k < half; k++) {
-            double send = upper ? v[k] : v[k + half];
-            double keep = upper ? v[k + half] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
-        }
-    }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
-}
-
 // Row offset (within a chunk) of the lane's k-th element.
 template <int VEC>
 __device__ __forceinline__ int row_of(int warp, int lane, int k) {

@@ -32,12 +32,10 @@ def store_full(D, kl, ku, ld=None):
     """Column-major full storage (ld >= m) with NaN outside the band."""
     m, n = D.shape
     ld = ld or max(1, m)
-    S = np.full(ld * n, np.nan)
-    for j in range(n):
-        for i in range(m):
-            if j - ku <= i <= j + kl:
-                S[i + j * ld] = D[i, j]
-    return S, ld
+    S = np.full((ld, n), np.nan, order="F")
+    mask = in_band(m, n, kl, ku)
+    S[:m][mask] = D[mask]
+    return S.ravel(order="F"), ld
 
 
 def store_band(D, kl, ku, ld=None):

@@ -842,7 +842,8 @@ def sparse_form(torch, bto, hbm, m=1 << 20, avg=32, reps=7, seed=11):
     row on average (synth.csr: uniform row lengths 0..2 avg, uniform random
     columns), median of `reps` calls after 2 warm-ups.  Algorithmic bytes:
     12 per stored entry (value + int32 column), the row pointers, and each
-    vector read or written once."""
+    vector read or written once (BATAX reads the entries twice; its fraction
+    is over one read)."""
     import synth
     rp, col, val = synth.csr(seed, 70, m, m, avg)
     nnz = len(col)
@@ -851,7 +852,8 @@ def sparse_form(torch, bto, hbm, m=1 << 20, avg=32, reps=7, seed=11):
     p, r, q, s = (torch.empty(m, **f64) for _ in range(4))
     bto.bto_fill_f64(seed, 1, 0, m, 1, 0, p, m, None)
     bto.bto_fill_f64(seed, 2, 0, m, 1, 0, r, m, None)
-    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    nb = bto.bto_csr_workspace_bytes("atax", m, m, nnz)
+    ws = torch.zeros(nb, dtype=torch.uint8, device="cuda")
     st = torch.cuda.current_stream()
 
     def time(call):
@@ -870,8 +872,8 @@ def sparse_form(torch, bto, hbm, m=1 << 20, avg=32, reps=7, seed=11):
     out = {"m": m, "nnz": nnz, "avg_row": avg}
     base = 12 * nnz + 8 * (m + 1)
     for name, call, vec in (
-            ("bicgk", lambda: bto.bto_csr_bicgk(m, m, nnz, d_rp, d_col, d_val, p, r, q, s, ws, 256), 8 * 4 * m),
-            ("batax", lambda: bto.bto_csr_atax(m, m, nnz, d_rp, d_col, d_val, 0.75, p, q, ws, 256), 8 * 2 * m)):
+            ("bicgk", lambda: bto.bto_csr_bicgk(m, m, nnz, d_rp, d_col, d_val, p, r, q, s, ws, nb), 8 * 4 * m),
+            ("batax", lambda: bto.bto_csr_atax(m, m, nnz, d_rp, d_col, d_val, 0.75, p, q, ws, nb), 8 * 2 * m)):
         ms = time(call)
         gbs = (base + vec) / ms / 1e6
         out[name] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3)}

@@ -317,17 +317,21 @@ bto_status bto_program_run(const bto_instr *prog, int count, void *ws, size_t ws
  * m x n with nnz stored entries: row_ptr has m + 1 int64 entries
  * (nondecreasing, row_ptr[0] = 0, row_ptr[m] = nnz), col and val nnz entries
  * (int32 column indices in [0, n), FP64 values; duplicates are summed, order
- * within a row is free).  One sweep over the stored entries: each row's
- * products are summed in a fixed order by a group of lanes (bitwise
- * reproducible), the transposed product is scattered with FP64 atomic adds
- * (reproducible to rounding only).  BATAX forms t_i = A(i,:) x inside the
- * group and scatters beta A(i,:)^T t_i from the same entries, so A is read
- * once and t is never stored.  n <= 2^31 - 1.
- * ws: at least 256 bytes, 256-byte aligned; its first word is the device
- * status (bto_device_status): BTO_ERR_INVALID_VALUE if a row pointer lay
- * outside [0, nnz] or decreased, or a column index outside [0, n) (those
- * entries are skipped, never dereferenced). */
-#define BTO_CSR_WORKSPACE_BYTES 256
+ * within a row is free).  The stored entries are divided evenly among the
+ * lanes (8 consecutive entries each), whatever the row lengths.  Each row's
+ * products are summed in a fixed order (bitwise reproducible); the
+ * transposed product is scattered with FP64 atomic adds (reproducible to
+ * rounding only).  BATAX forms t = A x in the workspace, then scatters
+ * beta t_i A(i, j): the stored entries are read twice.  n <= 2^31 - 1.
+ * ws: bto_csr_workspace_bytes bytes (about 24 bytes per 256 stored entries,
+ * plus 8 m for BATAX), 256-byte aligned; its first word is the device status
+ * (bto_device_status): BTO_ERR_INVALID_VALUE if a row pointer lay outside
+ * [0, nnz] or decreased (the call then sums every row with clamped bounds),
+ * or a column index outside [0, n) (that entry is skipped, never
+ * dereferenced). */
+
+/* Workspace bytes of a CSR call; op is BTO_OP_BICGK or BTO_OP_ATAX. */
+bto_status bto_csr_workspace_bytes(int op, int64_t m, int64_t n, int64_t nnz, size_t *bytes);
 
 /* q <- A p (q: m) ; s <- A^T r (s: n); p: n, r: m. */
 bto_status bto_csr_bicgk(int64_t m, int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,

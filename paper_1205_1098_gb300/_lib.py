@@ -200,6 +200,19 @@ def bto_workspace_bytes(op, form, m, n, a_type=BTO_F64):
     return out.value
 
 
+def bto_csr_workspace_bytes(op, m, n, nnz):
+    """Workspace bytes of bto_csr_bicgk / bto_csr_atax (op: 'bicgk', 'atax' or a bto_op value)."""
+    if isinstance(op, str):
+        op = OPS[op]
+    out = _c_size(0)
+    L = lib()
+    st = L.bto_csr_workspace_bytes(_c_int(int(op)), _c_i64(int(m)), _c_i64(int(n)), _c_i64(int(nnz)),
+                                   ctypes.byref(out))
+    if st != BTO_OK:
+        raise BtoError("bto_csr_workspace_bytes", st, L.bto_last_invalid_arg())
+    return out.value
+
+
 def bto_band_workspace_bytes(op, m, n, kl, ku):
     """Workspace bytes of bto_band_bicgk / bto_band_atax (op: 'bicgk', 'atax' or a bto_op value)."""
     if isinstance(op, str):
@@ -412,4 +425,5 @@ def exported_symbols():
                                       "bto_bicgk_mrhs_workspace_bytes", "bto_batch_workspace_bytes",
                                       "bto_serve_run", "bto_schedule_get", "bto_layout_workspace_bytes",
                                       "bto_program_check", "bto_program_workspace_bytes", "bto_program_run",
-                                      "bto_panel_plan", "bto_band_workspace_bytes", "bto_tri_workspace_bytes"])
+                                      "bto_panel_plan", "bto_band_workspace_bytes", "bto_tri_workspace_bytes",
+                                      "bto_csr_workspace_bytes"])

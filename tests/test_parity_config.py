@@ -109,9 +109,10 @@ def test_csr_2e20_rows():
     pv, rv = synth.vector(seed, 1, m), synth.vector(seed, 2, m)
     d_rp, d_col, d_val = (torch.from_numpy(a).cuda() for a in (rp, col, val))
     q, s, y = Out(m), Out(m), Out(m)
-    wk = torch.zeros(256, dtype=torch.uint8, device="cuda")
-    bto.bto_csr_bicgk(m, m, nnz, d_rp, d_col, d_val, dev(pv), dev(rv), q.ptr(), s.ptr(), wk, 256, None)
-    bto.bto_csr_atax(m, m, nnz, d_rp, d_col, d_val, 0.75, dev(pv), y.ptr(), wk, 256, None)
+    nb = bto.bto_csr_workspace_bytes("atax", m, m, nnz)
+    wk = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    bto.bto_csr_bicgk(m, m, nnz, d_rp, d_col, d_val, dev(pv), dev(rv), q.ptr(), s.ptr(), wk, nb, None)
+    bto.bto_csr_atax(m, m, nnz, d_rp, d_col, d_val, 0.75, dev(pv), y.ptr(), wk, nb, None)
     sync()
     assert int(wk[:4].view(torch.int32).cpu().numpy()[0]) == 0
     qo, so = O.csr_bicgk(m, m, rp, col, val, pv, rv)

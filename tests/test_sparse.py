@@ -99,9 +99,10 @@ def _run_bicgk(m, n, rp, col, val, p, r):
     d = [_dev(rp), _dev(col), _dev(val), _dev(p), _dev(r)]
     q = torch.full((max(m, 1),), np.nan, dtype=torch.float64, device="cuda")
     s = torch.full((max(n, 1),), np.nan, dtype=torch.float64, device="cuda")
-    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    nb = bto.bto_csr_workspace_bytes("bicgk", m, n, len(col))
+    ws = torch.full((nb,), 0xA5, dtype=torch.uint8, device="cuda")
     bto.bto_csr_bicgk(m, n, len(col), d[0], d[1] if len(col) else None, d[2] if len(col) else None,
-                      d[3] if n else None, d[4] if m else None, q if m else None, s if n else None, ws, 256)
+                      d[3] if n else None, d[4] if m else None, q if m else None, s if n else None, ws, nb)
     torch.cuda.synchronize()
     return q.cpu().numpy()[:m], s.cpu().numpy()[:n], ws
 
@@ -140,10 +141,11 @@ def test_csr_atax_matches_oracle(m, n, avg):
     rp, col, val = synth.csr(8, 60, m, n, avg)
     x = synth.vector(8, 1, n)
     y = torch.full((max(n, 1),), np.nan, dtype=torch.float64, device="cuda")
-    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    nb = bto.bto_csr_workspace_bytes("atax", m, n, len(col))
+    ws = torch.full((nb,), 0xA5, dtype=torch.uint8, device="cuda")
     d = [_dev(rp), _dev(col), _dev(val), _dev(x)]
     bto.bto_csr_atax(m, n, len(col), d[0], d[1] if len(col) else None, d[2] if len(col) else None, 0.75,
-                     d[3] if n else None, y if n else None, ws, 256)
+                     d[3] if n else None, y if n else None, ws, nb)
     got = y.cpu().numpy()[:n]
     assert relerr(got, O.csr_atax(m, n, 0.75, rp, col, val, x)) <= TOL64
     assert _status(ws) == _lib.BTO_OK
@@ -176,3 +178,74 @@ def test_csr_bad_indices_are_skipped_and_reported():
     q, s, ws = _run_bicgk(m, n, rp2, col, val, synth.vector(9, 1, n), synth.vector(9, 2, m))
     assert _status(ws) == _lib.BTO_ERR_INVALID_VALUE
     assert np.all(np.isfinite(q)) and np.all(np.isfinite(s))
+
+
+def _structured_csr(lengths, n, seed):
+    """CSR arrays with the given row lengths (columns and values seeded)."""
+    rp = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    nnz = int(rp[-1])
+    col = (synth.u64(seed, 90, np.arange(nnz, dtype=np.uint64)) % np.uint64(n)).astype(np.int32)
+    val = synth.vector(seed, 91, nnz)
+    return rp, col, val
+
+
+# Row lengths that put row ends on lane (8-entry) and unit (256-entry)
+# boundaries, empty rows at those boundaries, in runs and at the end, rows
+# that span many units, and a single row holding everything.
+PATTERNS = {
+    "boundaries": [8, 0, 8, 0, 0, 248, 256, 0, 1, 7, 0, 8, 240, 0, 0, 512, 3, 0, 0],
+    "long_rows": [0, 3, 5000, 0, 1, 2560, 7, 0, 0],
+    "one_row": [12345],
+    "empties_first": [0] * 40 + [300, 0, 5] + [0] * 9,
+    "mixed": list(np.tile([0, 1, 2, 3, 17, 31, 32, 33, 255, 256, 257, 0], 20)),
+}
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name", sorted(PATTERNS))
+def test_csr_row_patterns(name):
+    """Rows crossing lane and unit boundaries, empty rows everywhere, long
+    rows spanning many units: q and t bitwise reproducible and <= 1e-12 vs
+    the oracle; the unaligned-pointer path (val and col one element off a
+    16-byte boundary) gives the same row sums bitwise."""
+    import torch
+    from gpu_util import TOL64, relerr
+    build.build()
+    lengths = PATTERNS[name]
+    m, n = len(lengths), 777
+    rp, col, val = _structured_csr(lengths, n, 12)
+    nnz = len(col)
+    p, r = synth.vector(12, 1, n), synth.vector(12, 2, m)
+    q, s, ws = _run_bicgk(m, n, rp, col, val, p, r)
+    rq, rs = O.csr_bicgk(m, n, rp, col, val, p, r)
+    assert _status(ws) == _lib.BTO_OK
+    assert relerr(q, rq) <= TOL64 and relerr(s, rs) <= TOL64
+    assert np.all(q[np.diff(rp) == 0] == 0.0)
+    # unaligned entry arrays: one element into larger buffers
+    dcol = torch.from_numpy(np.concatenate([[0], col]).astype(np.int32)).cuda()
+    dval = torch.from_numpy(np.concatenate([[0.0], val])).cuda()
+    q2 = torch.full((m,), np.nan, dtype=torch.float64, device="cuda")
+    s2 = torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
+    nb = bto.bto_csr_workspace_bytes("bicgk", m, n, nnz)
+    w2 = torch.full((nb,), 0x5A, dtype=torch.uint8, device="cuda")
+    bto.bto_csr_bicgk(m, n, nnz, _dev(rp), dcol.data_ptr() + 4, dval.data_ptr() + 8, _dev(p), _dev(r), q2, s2,
+                      w2, nb)
+    assert _status(w2) == _lib.BTO_OK
+    assert np.array_equal(q, q2.cpu().numpy())
+    # BATAX on the same pattern
+    y = torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
+    nb = bto.bto_csr_workspace_bytes("atax", m, n, nnz)
+    w3 = torch.full((nb,), 0x5A, dtype=torch.uint8, device="cuda")
+    bto.bto_csr_atax(m, n, nnz, _dev(rp), _dev(col), _dev(val), -1.25, _dev(p), y, w3, nb)
+    assert _status(w3) == _lib.BTO_OK
+    assert relerr(y.cpu().numpy(), O.csr_atax(m, n, -1.25, rp, col, val, p)) <= TOL64
+
+
+def test_csr_workspace_query():
+    build.build()
+    a = bto.bto_csr_workspace_bytes("bicgk", 1000, 1000, 256 * 1000)
+    b = bto.bto_csr_workspace_bytes("atax", 1000, 1000, 256 * 1000)
+    assert a % 256 == 0 and a >= 256 + 3 * 8 * 1000 and b >= a + 8 * 1000
+    assert bto.bto_csr_workspace_bytes("bicgk", 0, 0, 0) >= 256
+    with pytest.raises(bto.BtoError):
+        bto.bto_csr_workspace_bytes("gemver", 1, 1, 1)

@@ -665,7 +665,8 @@ def gemver_small(torch, bto, hbm, reps=30, n=2048):
         ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
         byts = compulsory_bytes("gemver", n, n, 0)
         out[mode] = {"ms": round(ms, 4), "gbs": round(byts / ms / 1e6, 1), "hbm_frac": round(byts / ms / 1e6 / hbm, 3)}
-    out["note"] = "A, B 32 MiB each: warm runs from L2; cold evicts L2 with a 512 MiB write before every call"
+    out["note"] = ("A, B 32 MiB each: warm runs from L2; cold evicts L2 with a 512 MiB write before every call; "
+                   "one cooperative launch (both passes, a bounded grid barrier between them)")
     return out
 
 
@@ -1153,6 +1154,7 @@ def main():
     ap.add_argument("--sparse-only", action="store_true", help="only the CSR forms")
     ap.add_argument("--no-structured", action="store_true", help="skip the banded and triangular forms")
     ap.add_argument("--structured-only", action="store_true", help="only the banded and triangular forms")
+    ap.add_argument("--gemver2048-only", action="store_true", help="only GEMVER at n = 2048")
     ap.add_argument("--generator-only", action="store_true", help="only the generated sequences")
     ap.add_argument("--precision-only", type=int, default=0,
                     help="profiling runs: only the reduced-precision form at this n")
@@ -1196,6 +1198,14 @@ def main():
         import paper_1205_1098_gb300 as bto
         hbm, _, _ = load_peaks()
         print(json.dumps({"sparse": sparse_form(torch, bto, hbm)}))
+        return
+    if args.gemver2048_only:
+        import torch
+        from paper_1205_1098_gb300 import build
+        build.build()
+        import paper_1205_1098_gb300 as bto
+        hbm, _, _ = load_peaks()
+        print(json.dumps({"gemver_n2048": gemver_small(torch, bto, hbm)}))
         return
     if args.structured_only:
         import torch

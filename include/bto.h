@@ -822,6 +822,21 @@ bto_status bto_debug_atax_stall(int64_t m, int64_t n, double beta, const double 
                                 const double *x, double *y, void *ws, size_t ws_bytes,
                                 int64_t stall_band, int timeout_ms, bto_stream_t stream);
 
+/* Fault injection for the grid barrier of the one-launch GEMVER (bto_gemver
+ * takes it for matrices with m n <= 2^23 and max(3 m, 2 n) <= 12800 when the
+ * device allows a cooperative launch).  Runs that form with block
+ * `stall_block` never arriving at the barrier, so every wait expires after
+ * `timeout_ms` (1..10000) milliseconds: the kernel returns without the second
+ * pass, w is unspecified (B and x are complete) and bto_device_status reads
+ * BTO_ERR_TIMEOUT.  No fault is raised on the device.  stall_block < 0 runs
+ * the form normally.  BTO_ERR_UNSUPPORTED when the sizes do not qualify.
+ * ws: at least 256 bytes, 256-byte aligned. */
+bto_status bto_debug_gemver_stall(int64_t m, int64_t n, double alpha, double beta, const double *A, int64_t lda,
+                                  const double *u1, const double *v1, const double *u2, const double *v2,
+                                  const double *y, const double *z, double *B, int64_t ldb, double *x, double *w,
+                                  void *ws, size_t ws_bytes, int stall_block, int timeout_ms,
+                                  bto_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

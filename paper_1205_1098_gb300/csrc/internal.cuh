@@ -101,6 +101,18 @@ struct PanelArgs {
 };
 bto_status launch_panel(int mode, const PanelArgs& a, const PanelPlan& pl, cudaStream_t st);
 
+// True when bto_schedule_set has replaced the automatic schedule of (op, form).
+bool schedule_overridden(int op, int form);
+
+// GEMVER in one cooperative launch for matrices whose B stays in L2
+// (gemver_small.cu).  gemver_small returns BTO_ERR_UNSUPPORTED, having
+// launched nothing, when the grid cannot be made co-resident.
+bool gemver_small_ok(int64_t m, int64_t n, const DeviceInfo& d);
+bto_status gemver_small(int64_t m, int64_t n, double alpha, double beta, const double* A, int64_t lda,
+                        const double* u1, const double* v1, const double* u2, const double* v2, const double* y,
+                        const double* z, double* B, int64_t ldb, double* x, double* w, void* ws,
+                        const DeviceInfo& d, int stall_block, unsigned long long timeout_ns, cudaStream_t st);
+
 // out[i] = a1 * sum_k P1[k*ld1 + i] (+ a2 * sum_k P2[k*ld2 + i]) (+ b * v[i])
 struct CombineJob {
     double* out; int64_t len;

@@ -338,6 +338,13 @@ static bto_status run_gemver(int form, int64_t m, int64_t n, double alpha, doubl
         if (form == BTO_FORM_DF && ws_layout(BTO_OP_GEMVER, BTO_FORM_FUSED, m, n, BTO_F64, d, &L) != BTO_OK)
             return BTO_ERR_CUDA;
     }
+    // Matrices whose B stays in L2: both passes in one launch (unless a
+    // schedule override asks for the panel engine's tiles).
+    if (gemver_small_ok(m, n, d) && !schedule_overridden(BTO_OP_GEMVER, BTO_FORM_FUSED)) {
+        const bto_status e = gemver_small(m, n, alpha, beta, A, lda, u1, v1, u2, v2, y, z, B, ldb, x, w, ws, d, -1, 0,
+                                          st);
+        if (e != BTO_ERR_UNSUPPORTED) return e;
+    }
     const PanelPlan pl = panel_plan(m, n, d.sms, BTO_OP_GEMVER, BTO_FORM_FUSED);
     PanelArgs a{};
     a.m = m; a.n = n; a.A = A; a.lda = lda; a.Bout = B; a.ldb = ldb;
@@ -413,4 +420,29 @@ extern "C" bto_status bto_gemver_df(int64_t m, int64_t n, double alpha, double b
                                     double* x, double* w, void* ws, size_t ws_bytes, bto_stream_t stream) {
     return run_gemver(BTO_FORM_DF, m, n, alpha, beta, A, lda, u1, v1, u2, v2, y, z, B, ldb, x, w, ws,
                       ws_bytes, stream);
+}
+
+// Fault injection for the bounded grid barrier of the one-launch GEMVER:
+// block `stall_block` never arrives, so every block's wait expires after
+// `timeout_ms` and the status word reads BTO_ERR_TIMEOUT.
+extern "C" bto_status bto_debug_gemver_stall(int64_t m, int64_t n, double alpha, double beta, const double* A,
+                                             int64_t lda, const double* u1, const double* v1, const double* u2,
+                                             const double* v2, const double* y, const double* z, double* B,
+                                             int64_t ldb, double* x, double* w, void* ws, size_t ws_bytes,
+                                             int stall_block, int timeout_ms, bto_stream_t stream) {
+    clear_invalid_arg();
+    Check c;
+    c.size(1, m); c.size(2, n);
+    c.ptr(5, A, true); c.ld(6, lda, m);
+    c.ptr(7, u1, true); c.ptr(8, v1, true); c.ptr(9, u2, true); c.ptr(10, v2, true);
+    c.ptr(11, y, true); c.ptr(12, z, true); c.ptr(13, B, true); c.ld(14, ldb, m);
+    c.ptr(15, x, true); c.ptr(16, w, true);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < WS_HEADER) c.fail(17, BTO_ERR_WORKSPACE);
+    if (timeout_ms < 1 || timeout_ms > 10000) c.fail(20);
+    if (!c.ok()) return c.finish();
+    DeviceInfo d;
+    if (!device_info(&d)) return BTO_ERR_CUDA;
+    if (!gemver_small_ok(m, n, d)) return BTO_ERR_UNSUPPORTED;
+    return gemver_small(m, n, alpha, beta, A, lda, u1, v1, u2, v2, y, z, B, ldb, x, w, ws, d, stall_block,
+                        (unsigned long long)timeout_ms * 1000000ull, (cudaStream_t)stream);
 }

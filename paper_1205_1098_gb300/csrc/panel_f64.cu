@@ -544,6 +544,12 @@ bto_status launch_combine(const CombineJob* jobs, int njobs, cudaStream_t st) {
     return launch_status();
 }
 
+bool schedule_overridden(int op, int form) {
+    if (op < BTO_OP_BICGK || op > BTO_OP_DGEMVT || form < BTO_FORM_FUSED || form > BTO_FORM_UNFUSED) return false;
+    return g_sched[op][form][0].load(std::memory_order_relaxed) != 0 ||
+           g_sched[op][form][1].load(std::memory_order_relaxed) != 0;
+}
+
 }  // namespace bto
 
 using namespace bto;

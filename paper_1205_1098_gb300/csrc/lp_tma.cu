@@ -62,13 +62,16 @@ template <typename TA, int BPS> struct LpStages {
     static constexpr int value = BPS == 2 ? 5 : Cfg<TA>::S;
 };
 
+// nvec column vectors of the tile: s (hi, lo) and p, plus v1 and v2 in
+// GEMVER's first pass (5); 3 otherwise.
 template <typename TA, int BPS>
-size_t tma_smem(int64_t tcmax) {
+size_t tma_smem(int64_t tcmax, int nvec) {
     return LpStages<TA, BPS>::value * stage_bytes<TA>()     // ring
            + 2 * LpStages<TA, BPS>::value * sizeof(uint64_t)   // full, empty
            + 2 * kConsumerWarps * kBoxR * sizeof(float)      // q reduction (hi, lo)
-           + 5 * (size_t)tcmax * sizeof(float) + 128;        // s (hi, lo), p, v1, v2 of the tile
+           + (size_t)nvec * (size_t)tcmax * sizeof(float) + 128;
 }
+constexpr int lp_nvec(int mode) { return mode == LP_G1 ? 5 : 3; }
 
 template <typename TA>
 constexpr int box_cols() { return Cfg<TA>::BoxC; }
@@ -394,7 +397,7 @@ EncodeFn encode_fn() {
 template <typename TA, int MODE, int BPS>
 bto_status launch_t(const CUtensorMap& map, const LpArgs& a, int grid, cudaStream_t st) {
     auto k = lp_tma_kernel<TA, MODE, BPS>;
-    const size_t smem = tma_smem<TA, BPS>(a.tcmax);
+    const size_t smem = tma_smem<TA, BPS>(a.tcmax, lp_nvec(MODE));
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return BTO_ERR_CUDA;
     k<<<grid, kThreadsT, smem, st>>>(map, a);
@@ -426,12 +429,43 @@ PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type, int bps) {
     if (m <= 0 || n <= 0) return pl;
     const int64_t G = (int64_t)sms * bps, cu = lp_col_unit(a_type);
     const int64_t cunits = ceil_div(n, cu), runits = ceil_div(m, kBoxR);
-    const int64_t NC = std::min<int64_t>(G, cunits);
-    const int64_t NR = std::max<int64_t>(1, std::min<int64_t>(G / NC, runits));
-    pl.NC = (int)NC;
-    pl.NR = (int)NR;
-    pl.TCmax = ceil_div(cunits, NC) * cu;
-    pl.ntiles = NR * NC;
+    // At most one tile per block: NR row blocks x NC column panels with
+    // NR NC <= G.  The busiest block does (widest panel) x (tallest row
+    // block) units of 256 rows x cu columns; column panels leave NC x m row
+    // partials and row blocks NR x n column partials (FP32 pairs) that are
+    // written and read again.  Take the split with the least of
+    //   busiest block's units x (1 + partial bytes / matrix bytes)
+    // among those whose panel vectors fit the block's shared memory (one
+    // block per SM: 227 KB and GEMVER's five vectors; two: 113 KB each and
+    // three).  With one row block the panels of 1024 BF16 units over 304
+    // blocks were 3 or 4 units wide: a quarter of the blocks worked 19% longer
+    // than the mean.
+    const bool bf = a_type == BTO_BF16;
+    auto fits = [&](int64_t tc) {
+        const size_t smem = bf ? (bps == 2 ? tma_smem<__nv_bfloat16, 2>(tc, 3) : tma_smem<__nv_bfloat16, 1>(tc, 5))
+                               : (bps == 2 ? tma_smem<float, 2>(tc, 3) : tma_smem<float, 1>(tc, 5));
+        return smem <= (bps == 2 ? (size_t)115712 : (size_t)232448);
+    };
+    const double abytes = (double)m * (double)n * (bf ? 2.0 : 4.0);
+    int64_t bestNR = 0, bestNC = 0;
+    double best = 0.0;
+    for (int64_t NR = 1; NR <= std::min<int64_t>(G, runits); NR++) {
+        const int64_t NC = std::min<int64_t>(cunits, G / NR);
+        if (NC < 1) break;
+        const int64_t wu = ceil_div(cunits, NC), hc = ceil_div(runits, NR);
+        if (!fits(wu * cu)) continue;
+        const double pbytes = 2.0 * 8.0 * ((double)NC * (double)m + (double)NR * (double)n);
+        const double cost = (double)(wu * hc) * (1.0 + pbytes / abytes);
+        if (bestNR == 0 || cost < best) { best = cost; bestNR = NR; bestNC = NC; }
+    }
+    if (bestNR == 0) {          // no split fits (not reached for n >= 1): one row block
+        bestNC = std::min<int64_t>(G, cunits);
+        bestNR = std::max<int64_t>(1, std::min<int64_t>(G / bestNC, runits));
+    }
+    pl.NC = (int)bestNC;
+    pl.NR = (int)bestNR;
+    pl.TCmax = ceil_div(cunits, bestNC) * cu;
+    pl.ntiles = bestNR * bestNC;
     pl.grid = (int)G;
     return pl;
 }

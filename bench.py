@@ -611,13 +611,19 @@ def precision_form(torch, bto, hbm, steps, n=32768):
                 byts = 3 * es * m * n + 4 * (4 * m + 4 * n)
                 Bcols = B.view(n, m)[torch.from_numpy(rows).cuda()].cpu().numpy()
                 Bc = Bcols.astype(np.float64) if t == "f32" else synth.bf16_bits_to_f64(Bcols.view(np.uint16))
-                xh = x.cpu().numpy()[rows]
+                xall = x.cpu().numpy().astype(np.float64)
+                xh = xall[rows]
                 xref = 1.2 * (Bc @ g32["y"].astype(np.float64)) + g32["z"][rows].astype(np.float64)
+                # w on sampled rows, from the returned B (those rows, every column) and x
+                Brows = B.view(n, m)[:, torch.from_numpy(rows).cuda()].cpu().numpy().T
+                Br = Brows.astype(np.float64) if t == "f32" else synth.bf16_bits_to_f64(Brows.view(np.uint16))
+                wref = 1.5 * (Br @ xall)
+                wh = w.cpu().numpy()[rows]
                 Bx64 = (C64 + np.outer(gv["u1"], gv["v1"][rows]) + np.outer(gv["u2"], gv["v2"][rows]))
                 x64 = 1.2 * (Bx64.T @ gv["y"]) + gv["z"][rows]
                 res["gemver"] = {"ms": round(ms, 4), "gbs": round(byts / ms / 1e6, 1),
                                  "hbm_frac": round(byts / ms / 1e6 / hbm, 3),
-                                 "err_vs_stored": {"x": rel(xh, xref)},
+                                 "err_vs_stored": {"x": rel(xh, xref), "w": rel(wh, wref)},
                                  "err_vs_fp64_data": {"B": rel(Bc, Bx64.T), "x": rel(xh, x64)}}
                 del B, wsb
             del A

@@ -66,7 +66,7 @@ constexpr int kStages = 5;
 constexpr size_t kStageBytes = (size_t)kBoxR * kBoxC * sizeof(double);   // 32 KB
 constexpr int kGS = 4;                        // stages per butterfly group (8 columns per warp)
 constexpr int kMaxRowVecs = 3;                // u1, u2, y in GEMVER's first pass
-constexpr int kMaxPanel = 512;                // widest column panel (shared-memory vectors)
+constexpr int kMaxPanel = 1024;               // widest column panel (shared-memory vectors)
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 using df::split_words;
@@ -566,14 +566,34 @@ PanelPlan df_plan(int64_t m, int64_t n, int sms) {
     if (m <= 0 || n <= 0) return pl;
     const int64_t G = sms, cu = kBoxC;
     const int64_t cunits = ceil_div(n, cu), runits = ceil_div(m, kBoxR);
-    // At least one panel per block, and panels no wider than kMaxPanel columns
-    // (their vectors live in shared memory).
-    const int64_t NC = std::max<int64_t>(std::min<int64_t>(G, cunits), ceil_div(cunits, kMaxPanel / kBoxC));
-    const int64_t NR = std::max<int64_t>(1, std::min<int64_t>(G / NC, runits));
-    pl.NC = (int)NC;
-    pl.NR = (int)NR;
-    pl.TCmax = ceil_div(cunits, NC) * cu;
-    pl.ntiles = NR * NC;
+    // NR row blocks x NC column panels, panels no wider than kMaxPanel columns
+    // (their vectors live in shared memory).  With at most one tile per
+    // block, take the split with the least busiest-block work (widest panel x
+    // tallest row block, in 256 x 16 units) times one plus the bytes of FP64
+    // partials written and read again (NC x m and NR x n) over the matrix
+    // bytes.  Wider matrices than one tile per block allows take panels of
+    // kMaxPanel columns, several per block.
+    const int64_t wmax = kMaxPanel / kBoxC;
+    const double abytes = 8.0 * (double)m * (double)n;
+    int64_t bestNR = 0, bestNC = 0;
+    double best = 0.0;
+    for (int64_t NR = 1; NR <= std::min<int64_t>(G, runits); NR++) {
+        const int64_t NC = std::min<int64_t>(cunits, G / NR);
+        if (NC < 1) break;
+        const int64_t wu = ceil_div(cunits, NC), hc = ceil_div(runits, NR);
+        if (wu > wmax) continue;
+        const double pbytes = 2.0 * 8.0 * ((double)NC * (double)m + (double)NR * (double)n);
+        const double cost = (double)(wu * hc) * (1.0 + pbytes / abytes);
+        if (bestNR == 0 || cost < best) { best = cost; bestNR = NR; bestNC = NC; }
+    }
+    if (bestNR == 0) {
+        bestNC = std::max<int64_t>(std::min<int64_t>(G, cunits), ceil_div(cunits, wmax));
+        bestNR = std::max<int64_t>(1, std::min<int64_t>(G / bestNC, runits));
+    }
+    pl.NC = (int)bestNC;
+    pl.NR = (int)bestNR;
+    pl.TCmax = ceil_div(cunits, bestNC) * cu;
+    pl.ntiles = bestNR * bestNC;
     pl.grid = (int)std::min<int64_t>(G, pl.ntiles);
     return pl;
 }

@@ -555,7 +555,8 @@ typedef struct bto_serve_res {
     double admit;        /* seconds after the start: launched (-1: never)                  */
     double done;         /* seconds after the start: completion observed (-1: never)       */
     int64_t out[3];      /* arena byte offsets: outputs 0 and 1 (as bto_batch_desc.out),     */
-                         /* GEMVER's B (n x n, ld n, storage type); -1 where none           */
+                         /* GEMVER's B (n x n in A's storage type, leading dimension n     */
+                         /* rounded up to a multiple of 8); -1 where none                   */
     int32_t status;      /* BTO_OK, the device status of its launch, or BTO_ERR_BUDGET     */
     int32_t direct;      /* 1: served alone by a bto_*_ex entry point                      */
 } bto_serve_res;

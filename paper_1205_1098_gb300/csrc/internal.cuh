@@ -143,7 +143,11 @@ inline int lp_blocks_per_sm(int op, int a_type) {
     return ((a_type == BTO_BF16 && (op == BTO_OP_BICGK || op == BTO_OP_ATAX || op == BTO_OP_GESUMMV)) ||
             (a_type == BTO_F32 && op == BTO_OP_BICGK)) ? 2 : 1;
 }
-PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type, int bps = 1);
+// balanced: the split of the TMA-fed sweeps (every sweep of the call can
+// take that path, see lp_tma_ok); otherwise the load-instruction kernel's.
+PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type, int bps = 1, bool balanced = false);
+// A matrix the TMA-fed sweep can copy (16-byte base and column stride).
+bool lp_tma_ok(int a_type, const void* A, int64_t lda, int64_t m, int64_t n);
 
 // TMA path of the batched form (batched_tma.cu): instances whose matrices
 // suit the tensor memory accelerator, as tiles through the reduced-precision

@@ -421,7 +421,12 @@ bool encode_tmap_2d(CUtensorMap* map, CUtensorMapDataType dtype, size_t esize, c
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type, int bps) {
+bool lp_tma_ok(int a_type, const void* A, int64_t lda, int64_t m, int64_t n) {
+    const size_t es = a_type == BTO_F32 ? 4 : 2;
+    return m <= INT32_MAX && n <= INT32_MAX && aligned16(A) && ((size_t)lda * es) % 16 == 0;
+}
+
+PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type, int bps, bool balanced) {
     PanelPlan pl;
     pl.bps = bps;
     pl.ldq = round_up(m > 0 ? m : 1, 32);
@@ -429,7 +434,22 @@ PanelPlan lp_plan(int64_t m, int64_t n, int sms, int a_type, int bps) {
     if (m <= 0 || n <= 0) return pl;
     const int64_t G = (int64_t)sms * bps, cu = lp_col_unit(a_type);
     const int64_t cunits = ceil_div(n, cu), runits = ceil_div(m, kBoxR);
-    // At most one tile per block: NR row blocks x NC column panels with
+    if (!balanced) {
+        // The load-instruction kernel (operands the tensor memory accelerator
+        // cannot copy): one panel per block, row blocks only to fill the
+        // grid.  Its per-warp column partials live in shared memory for the
+        // whole panel, so the wide panels below cost it occupancy (GEMVER
+        // with an unaligned B measured 1.6 to 3.6 times slower with them).
+        const int64_t NC = std::min<int64_t>(G, cunits);
+        const int64_t NR = std::max<int64_t>(1, std::min<int64_t>(G / NC, runits));
+        pl.NC = (int)NC;
+        pl.NR = (int)NR;
+        pl.TCmax = ceil_div(cunits, NC) * cu;
+        pl.ntiles = NR * NC;
+        pl.grid = (int)G;
+        return pl;
+    }
+    // TMA-fed sweeps.  At most one tile per block: NR row blocks x NC column panels with
     // NR NC <= G.  The busiest block does (widest panel) x (tallest row
     // block) units of 256 rows x cu columns; column panels leave NC x m row
     // partials and row blocks NR x n column partials (FP32 pairs) that are

@@ -28,8 +28,15 @@ bto_status ws_layout(int op, int form, int64_t m, int64_t n, int a_type, const D
         return BTO_ERR_UNSUPPORTED;
     WsLayout L;
     size_t cur = WS_HEADER;
-    const PanelPlan pl = a_type == BTO_F64 ? panel_plan(m, n, d.sms, op, form)
-                                           : lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(op, a_type));
+    PanelPlan pl = a_type == BTO_F64 ? panel_plan(m, n, d.sms, op, form)
+                                     : lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(op, a_type), false);
+    if (a_type != BTO_F64) {
+        // Room for the partials of either split (the call picks one by the
+        // operands' alignment).
+        const PanelPlan pb = lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(op, a_type), true);
+        pl.NC = std::max(pl.NC, pb.NC);
+        pl.NR = std::max(pl.NR, pb.NR);
+    }
     const size_t qp = (size_t)pl.NC * pl.ldq * sizeof(double);
     const size_t sp = (size_t)pl.NR * pl.lds * sizeof(double);
     switch (op) {

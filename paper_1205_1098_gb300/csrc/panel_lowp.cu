@@ -349,7 +349,8 @@ extern "C" bto_status bto_bicgk_ex(int64_t m, int64_t n, int a_type, const void*
     }
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(BTO_OP_BICGK, a_type));
+    const PanelPlan pl = lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(BTO_OP_BICGK, a_type),
+                                 lp_tma_ok(a_type, A, lda, m, n));
     char* w = static_cast<char*>(ws);
     if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
     LpArgs a{};
@@ -398,7 +399,9 @@ extern "C" bto_status bto_gemver_ex(int64_t m, int64_t n, float alpha, float bet
     }
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = lp_plan(m, n, d.sms, a_type);
+    // Both passes take the TMA path only when A and B both suit it.
+    const PanelPlan pl = lp_plan(m, n, d.sms, a_type, 1,
+                                 lp_tma_ok(a_type, A, lda, m, n) && lp_tma_ok(a_type, B, ldb, m, n));
     char* wk = static_cast<char*>(ws);
     if (cudaMemsetAsync(wk, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
     LpArgs a{};
@@ -445,7 +448,8 @@ extern "C" bto_status bto_atax_ex(int64_t m, int64_t n, float beta, int a_type, 
     }
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(BTO_OP_ATAX, a_type));
+    const PanelPlan pl = lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(BTO_OP_ATAX, a_type),
+                                 lp_tma_ok(a_type, A, lda, m, n));
     char* w = static_cast<char*>(ws);
     if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
     if (n == 0) return BTO_OK;
@@ -489,7 +493,8 @@ extern "C" bto_status bto_gesummv_ex(int64_t m, int64_t n, float alpha, float be
     }
     if (!c.ok()) return c.finish();
     cudaStream_t st = (cudaStream_t)stream;
-    const PanelPlan pl = lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(BTO_OP_GESUMMV, a_type));
+    const PanelPlan pl = lp_plan(m, n, d.sms, a_type, lp_blocks_per_sm(BTO_OP_GESUMMV, a_type),
+                                 lp_tma_ok(a_type, A, lda, m, n) && lp_tma_ok(a_type, B, ldb, m, n));
     char* w = static_cast<char*>(ws);
     if (cudaMemsetAsync(w, 0, sizeof(int), st) != cudaSuccess) return BTO_ERR_CUDA;
     LpArgs a{};

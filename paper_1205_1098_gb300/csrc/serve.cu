@@ -160,13 +160,19 @@ class Server {
         b->on = false;
     }
 
+    // Leading dimension of GEMVER's B: n rounded up to 8 elements, so that its
+    // columns start on 16-byte boundaries and both passes run TMA-fed (with
+    // ld n, most n sent them to the load-instruction kernel, 3 to 10 times
+    // slower at n >= 1500).
+    static int64_t b_ld(int64_t n) { return (n + 7) / 8 * 8; }
+
     // Output vectors (and GEMVER's B) of request i.
     bool take_outputs(int64_t i) {
         const bto_serve_req& r = rq_[i];
         Blocks& bl = blocks_[i];
         for (int k = 0; k < n_outputs(r.op); k++)
             if (!take((size_t)r.n * sizeof(float), &bl.out[k])) { give_outputs(i); return false; }
-        if (r.op == BTO_OP_GEMVER && !take((size_t)r.n * r.n * esize(r.a_type), &bl.out[2])) {
+        if (r.op == BTO_OP_GEMVER && !take((size_t)r.n * b_ld(r.n) * esize(r.a_type), &bl.out[2])) {
             give_outputs(i);
             return false;
         }
@@ -290,7 +296,7 @@ class Server {
         d.beta = c_.beta;
         d.A = c_.A[tix(r.a_type)][0];
         if (r.op == BTO_OP_GESUMMV) d.B = const_cast<void*>(c_.A[tix(r.a_type)][1]);
-        if (r.op == BTO_OP_GEMVER) { d.B = at(bl.out[2]); d.ldb = r.n; }
+        if (r.op == BTO_OP_GEMVER) { d.B = at(bl.out[2]); d.ldb = b_ld(r.n); }
         for (int k = 0; k < n_inputs(r.op); k++) d.in[k] = c_.vec[k];
         for (int k = 0; k < n_outputs(r.op); k++) d.out[k] = static_cast<float*>(at(bl.out[k]));
         return d;
@@ -309,7 +315,7 @@ class Server {
                 return bto_bicgk_ex(n, n, r.a_type, A, ld, v[0], v[1], o0, static_cast<float*>(at(bl.out[1])), ws, wsb, s);
             case BTO_OP_GEMVER:
                 return bto_gemver_ex(n, n, c_.alpha, c_.beta, r.a_type, A, ld, v[0], v[1], v[2], v[3], v[4], v[5],
-                                     at(bl.out[2]), n, o0, static_cast<float*>(at(bl.out[1])), ws, wsb, s);
+                                     at(bl.out[2]), b_ld(n), o0, static_cast<float*>(at(bl.out[1])), ws, wsb, s);
             case BTO_OP_ATAX:
                 return bto_atax_ex(n, n, c_.beta, r.a_type, A, ld, v[0], o0, ws, wsb, s);
             default:

@@ -143,7 +143,10 @@ class Server:
                 n = r["n"]
                 d["out"] = [self._view(x.out[k], n, torch.float32) for k in range(2) if x.out[k] >= 0]
                 if r["op"] == "gemver":
-                    d["B"] = self._view(x.out[2], n * n, torch.float32 if r["dtype"] == "f32" else torch.int16)
+                    # n columns of leading dimension n rounded up to 8, returned as n x n
+                    ldb = (n + 7) // 8 * 8
+                    Bs = self._view(x.out[2], n * ldb, torch.float32 if r["dtype"] == "f32" else torch.int16)
+                    d["B"] = Bs.view(n, ldb)[:, :n].contiguous().view(-1)
             done.append(d)
         wall = stats.wall_s
         lat = np.array([d["done"] - d["t"] for d in done]) if done else np.zeros(1)

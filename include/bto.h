@@ -722,9 +722,9 @@ bto_status bto_unfused_vadd(int64_t n, const double *w, const double *y, const d
  *     Normwise relative error against exact FP64 arithmetic: about 1e-14 on
  *     ordinary data (the FP64 form's contract is 1e-12); integer-valued data
  *     below 2^24 in magnitude give exact results, as in the FP64 form.
- *   - GEMVER's B is hi + lo rounded once to FP64: within 2^-45 relative of
- *     the exact A + u1 v1^T + u2 v2^T (the FP64 form rounds twice); x and w
- *     are computed from that B.
+ *   - GEMVER's B is formed with the FP64 form's two FMAs per element
+ *     (the same bits as bto_gemver's B); x and w are double-float sums over
+ *     that B.
  *   - FP32's exponent range: values below 2^-127 in magnitude count as zero
  *     and products below about 2^-100 lose low-order bits, an absolute error
  *     below 2^-126 times the other factor per element (the underflow term of

@@ -42,9 +42,10 @@
 // overflows, so either makes the chunk's results non-finite.  Chunk results
 // are checked for finiteness; a 256-row chunk of a tile that fails is
 // recomputed in FP64 from the matrix in global memory, so those inputs get
-// plain FP64 semantics.  In GEMVER's first pass a lane whose B values come
-// out non-finite forms its B elements in FP64 from then on (the matrix may
-// be overwritten in place), and the chunk's column sums are recomputed in
+// plain FP64 semantics.  GEMVER's first pass forms B with two FP64 FMAs per
+// element (the FP64 form's formula: its B, bit for bit), which leaves one
+// FP64 instruction stream beside the FP32 work of the sums; B's column sums
+// are double-float, and a chunk whose sums fail the check is recomputed in
 // FP64 from the stored B.
 //
 // Every mbarrier wait is bounded by %globaltimer (2 s) and a shared abort
@@ -146,8 +147,6 @@ __device__ __forceinline__ void butterfly8(float (&h)[8], float (&l)[8], int lan
 // Sum over the lane's 8 rows of a * v for one column: a as packed row pairs
 // (AH, AL), v as packed row pairs (VH, its negation NVH, VL).  Returns the
 // double-float sum (sh, sl).
-// NEG_LO: AL holds the negated low parts (-a_lo).
-template <bool NEG_LO = false>
 __device__ __forceinline__ void col_partial(const float2 (&AH)[4], const float2 (&AL)[4], const float2 (&VH)[4],
                                             const float2 (&NVH)[4], const float2 (&VL)[4], float& sh, float& sl) {
     float2 Pn[4], Lx[4];
@@ -155,7 +154,7 @@ __device__ __forceinline__ void col_partial(const float2 (&AH)[4], const float2 
     for (int h = 0; h < 4; h++) {
         Pn[h] = mul2(AH[h], NVH[h]);                          // -(a_hi v_hi)
         const float2 E = fma2(AH[h], VH[h], Pn[h]);           // its rounding error, exact
-        Lx[h] = fma2(AL[h], NEG_LO ? NVH[h] : VH[h], fma2(AH[h], VL[h], E));    // + cross terms
+        Lx[h] = fma2(AL[h], VH[h], fma2(AH[h], VL[h], E));    // + cross terms
     }
     float2 s01, e01, s23, e23, s, e;
     two_sum2(Pn[0], Pn[1], s01, e01);
@@ -264,16 +263,20 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
         const int ncols = (int)(c1 - c0);
         const int ncols_u = (ncols + kBoxC - 1) / kBoxC * kBoxC;
 
-        // Column vectors of the tile, split once (zero beyond the matrix).
+        // Column vectors of the tile, split once (zero beyond the matrix);
+        // GEMVER's v1 and v2 stay FP64 (B is formed with FP64 FMAs), in the
+        // space of the split parts.
+        double* v1d = reinterpret_cast<double*>(vph);
+        double* v2d = reinterpret_cast<double*>(v2h);
         for (int k = tid; k < ncols_u; k += kCT) {
             if (HAS_S) sacc[k] = 0.0;
-            if (HAS_Q || MODE == DF_G1) {
-                const double v = k < ncols ? __ldg((MODE == DF_G1 ? a.v1 : a.p) + c0 + k) : 0.0;
+            if (HAS_Q) {
+                const double v = k < ncols ? __ldg(a.p + c0 + k) : 0.0;
                 split_vec(v, vph[k], vpl[k]);
             }
             if (MODE == DF_G1) {
-                const double v = k < ncols ? __ldg(a.v2 + c0 + k) : 0.0;
-                split_vec(v, v2h[k], v2l[k]);
+                v1d[k] = k < ncols ? __ldg(a.v1 + c0 + k) : 0.0;
+                v2d[k] = k < ncols ? __ldg(a.v2 + c0 + k) : 0.0;
             }
         }
         // Row vectors of the tile's first chunk.
@@ -303,7 +306,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
 
             // The lane's rows: pair h holds rows R0 + 64h + 2 lane + {0, 1}.
             float2 RH[4], NRH[4], RL[4];         // r (or y) parts
-            float2 U1H[4], U1L[4], U2H[4], U2L[4];
+            double2 U1[4], U2[4];                // GEMVER's u1, u2 (FP64)
             const double* rv = rowv + (size_t)rbuf * kMaxRowVecs * kBoxR;
 #pragma unroll
             for (int h = 0; h < 4; h++) {
@@ -316,16 +319,10 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                     RH[h] = f2(hx, hy); NRH[h] = f2(-hx, -hy); RL[h] = f2(lx, ly);
                 }
                 if (MODE == DF_G1) {
-                    float hx, lx, hy, ly;
-                    split_vec(rv[row], hx, lx);
-                    split_vec(rv[row + 1], hy, ly);
-                    U1H[h] = f2(hx, hy); U1L[h] = f2(lx, ly);
-                    split_vec(rv[kBoxR + row], hx, lx);
-                    split_vec(rv[kBoxR + row + 1], hy, ly);
-                    U2H[h] = f2(hx, hy); U2L[h] = f2(lx, ly);
+                    U1[h] = make_double2(rv[row], rv[row + 1]);
+                    U2[h] = make_double2(rv[kBoxR + row], rv[kBoxR + row + 1]);
                 }
             }
-            bool lbad = false;               // GEMVER: this lane forms its B in FP64
             float2 QH[4], QL[4], QH2[4], QL2[4];
 #pragma unroll
             for (int h = 0; h < 4; h++) {
@@ -360,7 +357,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
 #pragma unroll
                                 for (int h = 0; h < 4; h++) {
                                     D[h] = col[h * 32 + lane];
-                                    split_pair(D[h], AH[h], AL[h]);
+                                    if (MODE != DF_G1) split_pair(D[h], AH[h], AL[h]);
                                 }
                                 if (HAS_Q) {
                                     const float p_h = vph[lc], p_l = vpl[lc];
@@ -387,47 +384,18 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                                 if (MODE == DF_QS || MODE == DF_S)
                                     col_partial(AH, AL, RH, NRH, RL, sh[2 * gs + cc], sl[2 * gs + cc]);
                                 if (MODE == DF_G1) {
-                                    // B = A + u1 v1^T + u2 v2^T in double-float, stored in FP64.
-                                    const float w1h = vph[lc], w1l = vpl[lc], w2h = v2h[lc], w2l = v2l[lc];
-                                    const float2 V1H = f2(w1h, w1h), NV1H = f2(-w1h, -w1h), V1L = f2(w1l, w1l);
-                                    const float2 V2H = f2(w2h, w2h), NV2H = f2(-w2h, -w2h), V2L = f2(w2l, w2l);
-                                    float2 BH[4], NBL[4];    // hi and negated lo of B
-#pragma unroll
-                                    for (int h = 0; h < 4; h++) {
-                                        const float2 P1n = mul2(U1H[h], NV1H);
-                                        const float2 E1 = fma2(U1H[h], V1H, P1n);
-                                        const float2 P2n = mul2(U2H[h], NV2H);
-                                        const float2 E2 = fma2(U2H[h], V2H, P2n);
-                                        float2 L = fma2(U1L[h], V1H, fma2(U1H[h], V1L, add2(E1, E2)));
-                                        L = fma2(U2L[h], V2H, fma2(U2H[h], V2L, L));
-                                        float2 s1, e1, s2, e2;
-                                        two_sum_n(AH[h], P1n, s1, e1);
-                                        two_sum_n(s1, P2n, s2, e2);
-                                        const float2 low = add2(add2(AL[h], L), add2(e1, e2));
-                                        BH[h] = add2(s2, low);
-                                        NBL[h] = rsub2(low, rsub2(s2, BH[h]));    // (BH - s2) - low
-                                    }
-                                    // Anything out of FP32's range (a huge or non-finite
-                                    // input, an overflow) shows as a non-finite hi part:
-                                    // from here on the lane forms B in FP64.
-                                    const float2 ck = add2(add2(BH[0], BH[1]), add2(BH[2], BH[3]));
-                                    lbad = lbad || !isfinite(ck.x + ck.y);
+                                    // B = (A + u1 v1^T) + u2 v2^T with two FP64 FMAs per
+                                    // element (the FP64 form's formula, so the same bits),
+                                    // stored, then split for the double-float column sum.
+                                    const double v1j = v1d[lc], v2j = v2d[lc];
                                     const int64_t col_g = cs + c;
                                     double* bcol = a.Bout + col_g * a.ldbo;
+                                    float2 BH[4], BL[4];
 #pragma unroll
                                     for (int h = 0; h < 4; h++) {
                                         const int64_t i0 = R0 + 64 * h + 2 * lane;
-                                        double b0, b1;
-                                        if (!lbad) {
-                                            b0 = df::pair_to_f64(BH[h].x, NBL[h].x);
-                                            b1 = df::pair_to_f64(BH[h].y, NBL[h].y);
-                                        } else {
-                                            // FP64 for the whole lane once anything it holds is out of range.
-                                            const double v1j = col_g < c1 ? __ldg(a.v1 + col_g) : 0.0;
-                                            const double v2j = col_g < c1 ? __ldg(a.v2 + col_g) : 0.0;
-                                            b0 = i0 < r1 ? fma(__ldg(a.u2 + i0), v2j, fma(__ldg(a.u1 + i0), v1j, D[h].x)) : 0.0;
-                                            b1 = i0 + 1 < r1 ? fma(__ldg(a.u2 + i0 + 1), v2j, fma(__ldg(a.u1 + i0 + 1), v1j, D[h].y)) : 0.0;
-                                        }
+                                        const double b0 = fma(U2[h].x, v2j, fma(U1[h].x, v1j, D[h].x));
+                                        const double b1 = fma(U2[h].y, v2j, fma(U1[h].y, v1j, D[h].y));
                                         if (col_g < c1) {
                                             if (i0 + 1 < r1) {
                                                 *reinterpret_cast<double2*>(bcol + i0) = make_double2(b0, b1);
@@ -435,8 +403,9 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                                                 bcol[i0] = b0;
                                             }
                                         }
+                                        split_pair(make_double2(b0, b1), BH[h], BL[h]);
                                     }
-                                    col_partial<true>(BH, NBL, RH, NRH, RL, sh[2 * gs + cc], sl[2 * gs + cc]);
+                                    col_partial(BH, BL, RH, NRH, RL, sh[2 * gs + cc], sl[2 * gs + cc]);
                                 }
                             }
                             __syncwarp();
@@ -460,7 +429,6 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
 
             // ---- chunk end: rows of q, check, write or recompute in FP64
             const int fl = (int)(chunk & 1);
-            if (lbad) s_badp[fl] = 1;
             double qv = 0.0, qv2 = 0.0;
             if (MODE == DF_QS || MODE == DF_Q) {
 #pragma unroll

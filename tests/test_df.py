@@ -65,9 +65,10 @@ def test_df_matrix_kernel(kernel, shape, form):
     m, n, lda = shape
     res = MATRIX_RUNNERS[kernel](m, n, lda, synth.KIND_UNIFORM, form=form)
     if kernel == "gemver":
-        # B: hi + lo rounded once (47 bits of A kept): within 2^-45 per element.
+        # B: formed by FP64 FMAs (the FP64 form's B), a few ulps from the
+        # oracle's twice-rounded sums.
         g, o = res.pop("B")
-        assert relerr(g, o) <= 1e-13
+        assert relerr(g, o) <= 1e-15
     _check(res)
 
 
@@ -215,6 +216,17 @@ def test_df_gemver_in_place(case):
     _compare_special(Bg, Bo, tol=1e-13)
     _compare_special(d[5].cpu().numpy(), xo)
     _compare_special(w.host(), wo)
+    # B is formed by the FP64 form's two FMAs per element: the same bits as bto_gemver's.
+    dA2 = dev(A)
+    d2 = [dev(v) for v in vecs]
+    B64 = torch.empty(1100 * n, dtype=torch.float64, device="cuda")
+    x64, w64 = Out(n), Out(m)
+    wk2, nb2 = ws("gemver", 0, m, n)
+    bto.bto_gemver(m, n, 1.5, 1.2, p(dA2), 1100, *[p(t) for t in d2], p(B64), 1100, x64.ptr(), w64.ptr(),
+                   p(wk2), nb2, None)
+    sync()
+    B64h = B64.cpu().numpy().reshape(n, 1100).T[:m]
+    assert np.array_equal(Bg, B64h, equal_nan=True)
 
 
 def test_df_zero_data_gives_exact_zeros():

@@ -20,10 +20,9 @@ N = 16384
 SEED = 1
 NSAMP = 48
 FORMS = ["fused", "df"]
-# GEMVER's B: the FP64 form rounds A + u1 v1^T + u2 v2^T twice like the
-# oracle (a few ulps apart); the double-float form keeps 47 bits of A and
-# rounds its hi + lo sum once (within 2^-45 relative per element).
-B_TOL = {"fused": 1e-15, "df": 1e-13}
+# GEMVER's B: both forms compute A + u1 v1^T + u2 v2^T with two FP64 FMAs
+# per element (the oracle rounds twice without contraction: a few ulps apart).
+B_TOL = {"fused": 1e-15, "df": 1e-15}
 
 
 @pytest.fixture(scope="module")

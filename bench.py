@@ -1036,6 +1036,7 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3, tile=0):
     ops = np.where(synth.vector(seed, 501, count) < 0, 0, 2)
     descs = (bto.BatchDesc * count)()
     keep = []
+    outs = []
     f32 = dict(dtype=torch.float32, device="cuda")
     nbytes = 0
     for i in range(count):
@@ -1054,17 +1055,21 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3, tile=0):
             bto.bto_fill_f32(seed, 1000 * i + 1 + k, 0, ln, 1, 0, t, ln, None)
             keep.append(t)
             d.in_[k] = t.data_ptr()
+        o = []
         for k, ln in enumerate([m, n] if op == 0 else [n, m]):
             t = torch.empty(ln, **f32)
             keep.append(t)
             d.out[k] = t.data_ptr()
+            o.append(t)
         if op == 2:
             B = torch.empty(lda * n, **f32)
             keep.append(B)
             d.B = B.data_ptr()
+            o.append(B)
             nbytes += 3 * 4 * m * n + 4 * (4 * m + 4 * n)
         else:
             nbytes += 4 * m * n + 4 * (2 * m + 2 * n)
+        outs.append(o)
     torch.cuda.synchronize()
     if tile:
         best, cand_ms = tile, {}           # profiling runs: a fixed panel width, no tuner
@@ -1094,7 +1099,29 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3, tile=0):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     status = bto.bto_device_status(ws)
+    # Sampled accuracy: FP64 products (numpy) on the stored FP32 values; GEMVER's x and w from the
+    # returned B (x with the returned B, w with the returned B and x).
+    f32h = lambda a64: synth.to_f32(a64).astype(np.float64)
+    rel = lambda a, b: float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+    errs = {"bicgk": [], "gemver": []}
+    for i in np.unique(np.linspace(0, count - 1, 32).astype(np.int64)):
+        m, n, op = int(sizes[2 * i]), int(sizes[2 * i + 1]), int(ops[i])
+        lda = (m + 3) // 4 * 4
+        vin = [f32h(synth.vector(seed, 1000 * int(i) + 1 + k, ln))
+               for k, ln in enumerate([n, m] if op == 0 else [m, n, m, n, m, n])]
+        got = [t.cpu().numpy().astype(np.float64) for t in outs[i]]
+        if op == 0:
+            A64 = f32h(synth.matrix(seed, 1000 * int(i), m, n))
+            errs["bicgk"].append(max(rel(got[0], A64 @ vin[0]), rel(got[1], A64.T @ vin[1])))
+        else:
+            Bret = got[2][:lda * n].reshape(n, lda).T[:m]
+            errs["gemver"].append(max(rel(got[0], 1.25 * (Bret.T @ vin[4]) + vin[5]),
+                                      rel(got[1], 1.5 * (Bret @ got[0]))))
+    sampled = {"instances": sum(len(v) for v in errs.values()),
+               "max_err": {k: (float(max(v)) if v else None) for k, v in errs.items()},
+               "reference": "FP64 products (numpy) on the stored FP32 values; GEMVER's x and w from the returned B"}
     return {"instances": count, "ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
+            "sampled_err": sampled,
             "hbm_frac": round(nbytes / ms / 1e6 / hbm, 3), "compulsory_bytes": nbytes,
             "tile_cols": best, "tuner_ms": {str(k): round(v, 4) for k, v in cand_ms.items()},
             "status": status, "launch": "CUDA graph of bto_batch_run (TMA-path sweeps and combines; fallback kernel idle)",
@@ -1117,7 +1144,46 @@ def serving_form(torch, duration=10.0, rate=20000.0, seed=4, runs_n=3):
     out = dict(runs[-1])
     out["runs"] = [{k: r[k] for k in ("p50_ms", "p99_ms", "mean_ms", "gbs", "loop", "p99_ms_by_second")}
                    for r in runs]
+    out["sampled_err"] = serving_errors(srv, make_trace(seed + 2, rate, 0.0, nmax=4096, count=200), seed)
     return out
+
+
+def serving_errors(srv, trace, seed, nsamp=24):
+    """Accuracy of served requests: a short trace (n up to 4096) served with
+    its outputs kept; every k-th request's outputs against FP64 products
+    (numpy) on the stored operands (the leading n x n blocks of the resident
+    matrices, dequantized; GEMVER's x and w from the returned B)."""
+    import synth
+    from paper_1205_1098_gb300.serve import ALPHA, BETA
+    stats, done = srv.run(trace, keep_results=True)
+    rel = lambda a, b: float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+    errs = {}
+    for r in done[::max(1, len(done) // nsamp)]:
+        n, op, t = r["n"], r["op"], r["dtype"]
+        code = 1 if t == "f32" else 2
+
+        def block(aid):
+            A = synth.matrix_cols(seed, aid, 8192, 8192, np.arange(n))[:n]
+            return synth.to_f32(A).astype(np.float64) if t == "f32" else synth.bf16_bits_to_f64(synth.to_bf16_bits(A))
+        v = [synth.to_f32(synth.vector(seed, 100 + k, 8192))[:n].astype(np.float64) for k in range(6)]
+        got = [o.cpu().numpy().astype(np.float64) for o in r["out"]]
+        if op == "gemver":
+            Bb = r["B"].cpu().numpy()
+            Bret = (Bb.astype(np.float64) if t == "f32" else synth.bf16_bits_to_f64(Bb.view(np.uint16))).reshape(n, n).T
+            xr = BETA * (Bret.T @ v[4]) + v[5]
+            e = max(rel(got[0], xr), rel(got[1], ALPHA * (Bret @ xr)))
+        else:
+            A = block(10 * code)
+            if op == "bicgk":
+                e = max(rel(got[0], A @ v[0]), rel(got[1], A.T @ v[1]))
+            elif op == "atax":
+                e = rel(got[0], BETA * (A.T @ (A @ v[0])))
+            else:
+                e = rel(got[0], ALPHA * (A @ v[0]) + BETA * (block(10 * code + 1) @ v[0]))
+        errs.setdefault("%s_%s" % (op, t), []).append(e)
+    return {"requests": sum(len(x) for x in errs.values()), "status_ok": bool(stats["status_ok"]),
+            "max_err": {k: max(x) for k, x in sorted(errs.items())},
+            "reference": "FP64 products (numpy) on the stored operands; GEMVER's x and w from the returned B"}
 
 
 def _rounded(d):

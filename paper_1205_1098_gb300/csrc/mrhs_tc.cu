@@ -301,13 +301,19 @@ mrhs_tma_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ 
                 const uint32_t aR = smem_u32(sR + (v & 1) * bk);
                 const uint32_t aP = smem_u32(sP + c * bk);
                 const uint32_t tS = tm + (uint32_t)(c * k), tQ = tm + (uint32_t)(kSub * k + qb * k);
+                // The descriptors of the eight K steps differ only in the start
+                // address (bits 0-13, in 16-byte units; shared-memory addresses
+                // stay below 2^18, so the field never carries): form each base
+                // once and add the steps' offsets.
+                const uint64_t dS0 = sdesc(aA, 16, 1024, 2), dQ0 = sdesc(aA, kTileBytes / 2, 1024, 2);
+                const uint64_t dR0 = sdesc(aR, 16, 1024, 2), dP0 = sdesc(aP, 16, 1024, 2);
+                const uint64_t bh = (uint64_t)(bk / 2) >> 4;
 #pragma unroll
                 for (int ks = 0; ks < kTile / 16; ks++) {
-                    const uint32_t kA = (uint32_t)((ks >> 2) * (kTileBytes / 2) + (ks & 3) * 32);
-                    const uint32_t kB = (uint32_t)((ks >> 2) * (bk / 2) + (ks & 3) * 32);
-                    mma(tS, sdesc(aA + kA, 16, 1024, 2), sdesc(aR + kB, 16, 1024, 2), idS, (!sf || ks > 0) ? 1u : 0u);
-                    mma(tQ, sdesc(aA + ks * 2048, kTileBytes / 2, 1024, 2), sdesc(aP + kB, 16, 1024, 2), idQ,
-                        (c > 0 || ks > 0) ? 1u : 0u);
+                    const uint64_t oA = (uint64_t)(((ks >> 2) * (kTileBytes / 2) + (ks & 3) * 32) >> 4);
+                    const uint64_t oB = (uint64_t)(ks >> 2) * bh + (uint64_t)((ks & 3) * 2);
+                    mma(tS, dS0 + oA, dR0 + oB, idS, (!sf || ks > 0) ? 1u : 0u);
+                    mma(tQ, dQ0 + (uint64_t)(ks * 128), dP0 + oB, idQ, (c > 0 || ks > 0) ? 1u : 0u);
                 }
                 mma_commit(&empty[s]);
                 if (c == kSub - 1) mma_commit(&qfull[qb]);

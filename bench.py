@@ -399,20 +399,27 @@ def e2e_steps(torch, bto, steps, warmup, m, n, N):
     # Copies overlap the kernels: inputs go host->device on their own stream in
     # the order the kernels need them, each kernel waits for its own inputs
     # only, and results go back on a third stream as soon as they exist
-    # (GEMVER's 2 GiB B while the other matrix kernels run).  A step starts
-    # after the previous one has finished, so no buffer is reused early.
+    # (GEMVER's 2 GiB B while the other matrix kernels run).  A step's inputs
+    # are copied once the previous step's kernels are done with the input
+    # buffers, so they overlap the previous step's read-back (the link carries
+    # both directions at once); a kernel group overwrites its outputs only
+    # after the previous step has read them back.
     sC = torch.cuda.current_stream()
     sH = torch.cuda.Stream()
     sD = torch.cuda.Stream()
+    prev = {}
 
     def rec(stream):
         e = torch.cuda.Event()
         e.record(stream)
         return e
 
+    def after_readback(group):
+        if group in prev:
+            sC.wait_event(prev[group])
+
     def step():
         sH.wait_stream(sC)
-        sH.wait_stream(sD)
         with torch.cuda.stream(sH):
             for k, t in hbig.items():
                 suite.big[k].copy_(t, non_blocking=True)
@@ -424,6 +431,7 @@ def e2e_steps(torch, bto, steps, warmup, m, n, N):
             suite.B2.copy_(hB, non_blocking=True)
             e_b = rec(sH)
         sC.wait_event(e_big)
+        after_readback("vector")
         for k in ("axpydot", "waxpby", "vadd"):
             suite.call(k, 0)
         sD.wait_event(rec(sC))
@@ -431,13 +439,17 @@ def e2e_steps(torch, bto, steps, warmup, m, n, N):
             for k, t in outs_big_h.items():
                 t.copy_(suite.big[k], non_blocking=True)
             outs_h["r"].copy_(suite.r, non_blocking=True)
+        prev["vector"] = rec(sD)
         sC.wait_event(e_a)
+        after_readback("gemver")
         suite.call("gemver", 0)
         sD.wait_event(rec(sC))
         with torch.cuda.stream(sD):
             hBout.copy_(suite.Bout, non_blocking=True)
             for k in ("gx", "gw"):
                 outs_h[k].copy_(suite.vec[k], non_blocking=True)
+        prev["gemver"] = rec(sD)
+        after_readback("matrix")
         for k in ("bicgk", "atax", "dgemv", "dgemvt"):
             suite.call(k, 0)
         sC.wait_event(e_b)
@@ -447,6 +459,7 @@ def e2e_steps(torch, bto, steps, warmup, m, n, N):
             for k, t in outs_h.items():
                 if k not in ("r", "gx", "gw"):
                     t.copy_(suite.vec[k], non_blocking=True)
+        prev["matrix"] = rec(sD)
 
     st = sC
     for _ in range(warmup):

@@ -758,7 +758,13 @@ bool make_plan(int count, const bto_batch_desc* descs, int tile_cols, Plan* P, i
     H.off_desc = region((size_t)count * sizeof(bto_batch_desc));
     H.off_info = region((size_t)count * sizeof(InstInfo));
     H.off_items = region(P->items.size() * sizeof(Item));
-    if (!bt_plan_empty(P->bt)) cur = (size_t)bt_plan_layout_records(P->bt, (int64_t)cur);
+    if (!bt_plan_empty(P->bt)) {
+        // The TMA sweep runs one block per SM (bt_launch): its items are
+        // ordered for that grid.
+        DeviceInfo dinf;
+        const int G = device_info(&dinf) ? dinf.sms : 0;
+        cur = (size_t)bt_plan_layout_records(P->bt, (int64_t)cur, G);
+    }
     H.counters_bytes = (int64_t)(count + kQueues) * sizeof(unsigned);
     H.off_counters = region((size_t)H.counters_bytes);
     H.off_qpart = region((size_t)std::max<int64_t>(qsize, 1) * sizeof(float2));

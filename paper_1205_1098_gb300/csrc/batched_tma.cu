@@ -26,6 +26,7 @@
 #include "lp_math.cuh"
 #include "tma.cuh"
 #include <algorithm>
+#include <queue>
 #include <cstring>
 #include <vector>
 
@@ -43,6 +44,8 @@ constexpr int kStagesT = 12;                    // ring stages (16 KB each)
 constexpr int kMaxTw = 512;                     // widest tile (columns)
 constexpr int kRowsPerTile = 2048;              // tallest tile (rows)
 constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr double kItemCost = 40000.0;           // an item's fixed work, in matrix elements
+constexpr double kChunkCost = 2500.0;           // a 256-row chunk's reductions, in matrix elements
 
 template <typename TA> struct Cfg {
     static constexpr int BoxC = sizeof(TA) == 2 ? 32 : 16;   // 16 KB boxes
@@ -432,6 +435,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) bt_sweep(char* ws, int stage) {
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
         asm volatile("cp.async.wait_group 1;" ::: "memory");   // this item's copies are in
+        if (it.mode < 0) continue;                               // a slot the plan left empty
         sm.sp = vbuf + buf * 3 * kMaxTw;
         sm.sv1 = sm.sp + kMaxTw;
         sm.sv2 = sm.sv1 + kMaxTw;
@@ -565,7 +569,11 @@ bool bt_plan_add(BtPlan* P, const bto_batch_desc& d) {
         rec.t_off = (p_is_t || r_is_t) ? t_off : -1;
         if (p_is_t) rec.it.p = nullptr;
         if (r_is_t) rec.it.r = nullptr;
-        rec.cost = w * (double)(rec.it.r1 - rec.it.r0) * (double)(rec.it.c1 - rec.it.c0);
+        // Elements streamed (weighted: GEMVER's first pass also writes B), plus
+        // each item's fixed work (its vectors, partial writes) and each
+        // 256-row chunk's reductions, in the same units.
+        rec.cost = w * (double)(rec.it.r1 - rec.it.r0) * (double)(rec.it.c1 - rec.it.c0) + kItemCost +
+                   kChunkCost * (double)ceil_div(rec.it.r1 - rec.it.r0, kBoxR);
         rec.type = type;
         rec.stage = stage;
         if (rec.it.r1 > rec.it.r0 && rec.it.c1 > rec.it.c0) P->items.push_back(rec);
@@ -620,8 +628,8 @@ bool bt_plan_add(BtPlan* P, const bto_batch_desc& d) {
 
 // Assigns the regions of the plan's records (part of the uploaded image) from
 // `cur` on and returns the new end; sorts the items (stage, storage type,
-// decreasing size) and counts them.
-int64_t bt_plan_layout_records(BtPlan* P, int64_t cur) {
+// decreasing size), orders each group for a grid of G blocks and counts them.
+int64_t bt_plan_layout_records(BtPlan* P, int64_t cur, int G) {
     auto region = [&](int64_t bytes) { const int64_t at = cur; cur += round_up(std::max<int64_t>(bytes, 1), 256); return at; };
     // Items sorted by stage, storage type, then decreasing cost (ties: order of addition).
     std::stable_sort(P->items.begin(), P->items.end(), [](const BtPlan::ItemRec& a, const BtPlan::ItemRec& b) {
@@ -629,6 +637,45 @@ int64_t bt_plan_layout_records(BtPlan* P, int64_t cur) {
         if (a.type != b.type) return a.type < b.type;
         return a.cost > b.cost;
     });
+    // Block b of the sweep takes slots b, b + G, b + 2G, ... of its group.  A
+    // group of more than G items is assigned longest-processing-time first
+    // (each item, in decreasing cost, to the least loaded block; ties to the
+    // lower block) and laid out so that the walk gives every block its list;
+    // slots past the end of a shorter list hold a no-op item (mode -1).
+    if (G > 0) {
+        std::vector<BtPlan::ItemRec> out;
+        out.reserve(P->items.size());
+        size_t i = 0;
+        while (i < P->items.size()) {
+            size_t j = i;
+            while (j < P->items.size() && P->items[j].stage == P->items[i].stage && P->items[j].type == P->items[i].type) j++;
+            if ((int64_t)(j - i) <= G) {
+                out.insert(out.end(), P->items.begin() + i, P->items.begin() + j);
+            } else {
+                std::vector<std::vector<size_t>> lists(G);
+                using Load = std::pair<double, int>;
+                std::priority_queue<Load, std::vector<Load>, std::greater<Load>> least;
+                for (int b = 0; b < G; b++) least.push(Load(0.0, b));
+                for (size_t k = i; k < j; k++) {
+                    const Load l = least.top();
+                    least.pop();
+                    lists[l.second].push_back(k);
+                    least.push(Load(l.first + P->items[k].cost, l.second));
+                }
+                size_t K = 0;
+                for (const auto& l : lists) K = std::max(K, l.size());
+                BtPlan::ItemRec pad{};
+                pad.it.mode = -1;
+                pad.q_off = pad.s_off = pad.t_off = -1;
+                pad.stage = P->items[i].stage;
+                pad.type = P->items[i].type;
+                for (size_t k = 0; k < K; k++)
+                    for (int b = 0; b < G; b++) out.push_back(k < lists[b].size() ? P->items[lists[b][k]] : pad);
+            }
+            i = j;
+        }
+        P->items.swap(out);
+    }
     for (int s = 0; s < 2; s++) {
         for (int t = 0; t < 2; t++) P->nitems[s][t] = 0;
         P->ncomb[s] = 0;

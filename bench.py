@@ -1112,6 +1112,7 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3, tile=0):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     status = bto.bto_device_status(ws)
+    one = bto.bto_batch_one_launch(ws)
     # Sampled accuracy: FP64 products (numpy) on the stored FP32 values; GEMVER's x and w from the
     # returned B (x with the returned B, w with the returned B and x).
     f32h = lambda a64: synth.to_f32(a64).astype(np.float64)
@@ -1137,7 +1138,10 @@ def batched_form(torch, bto, hbm, steps, count=4096, seed=3, tile=0):
             "sampled_err": sampled,
             "hbm_frac": round(nbytes / ms / 1e6 / hbm, 3), "compulsory_bytes": nbytes,
             "tile_cols": best, "tuner_ms": {str(k): round(v, 4) for k, v in cand_ms.items()},
-            "status": status, "launch": "CUDA graph of bto_batch_run (TMA-path sweeps and combines; fallback kernel idle)",
+            "status": status,
+            "launch": ("CUDA graph of bto_batch_run: one cooperative launch (both stages' TMA sweeps and combines, "
+                       "bounded grid barriers)" if one else
+                       "CUDA graph of bto_batch_run (TMA-path sweeps and combines; fallback kernels)"),
             "layout": "column-major, leading dimension rounded up to a multiple of 4 floats"}
 
 

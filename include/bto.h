@@ -506,16 +506,29 @@ bto_status bto_batch_workspace_bytes(int count, const bto_batch_desc *descs, int
 bto_status bto_batch_prepare(int count, const bto_batch_desc *descs, int tile_cols, void *ws,
                              size_t ws_bytes, bto_stream_t stream);
 
-/* Runs a prepared batch on `stream` (a reset kernel and the persistent kernel). */
+/* Runs a prepared batch on `stream`.  When every instance suits the tensor
+ * memory accelerator (16-byte aligned matrices and leading dimensions) and
+ * all share one storage type, and the device launches cooperatively, the
+ * whole batch is one cooperative launch of one block per SM: both stages'
+ * sweeps and fixed-order combines, separated by bounded grid barriers (a
+ * timeout leaves BTO_ERR_TIMEOUT in the status word; prepare the workspace
+ * again before the next run).  Otherwise a reset kernel, the persistent
+ * kernels of the load-instruction queues and the tensor-memory sweeps and
+ * combines of each stage.  The results are the same either way. */
 bto_status bto_batch_run(void *ws, size_t ws_bytes, bto_stream_t stream);
+
+/* Whether bto_batch_run takes the one-launch form for the workspace ws (as
+ * last prepared by bto_batch_prepare): *one = 1 or 0.  No device work. */
+bto_status bto_batch_one_launch(const void *ws, int *one);
 
 /* Plans and launches a batch in one call: the plan is copied into ws
  * (status word and counters zeroed, so no reset kernel runs) through
  * `staging` when it is pinned host memory of at least the plan's size (the
  * caller keeps it unchanged until the stream has passed the copy), else
- * through a pageable copy that the call waits for; then only the kernels of
- * the non-empty queues are launched, each grid no larger than its items, so
- * that a small batch leaves the other SMs to other streams.  Same results as
+ * through a pageable copy that the call waits for; then the one-launch form
+ * when it applies (as for bto_batch_run), else only the kernels of the
+ * non-empty queues, each grid no larger than its items, so that a small batch
+ * leaves the other SMs to other streams.  Same results as
  * bto_batch_prepare + bto_batch_run.  Not for graph capture when staging is
  * NULL (the call waits). */
 bto_status bto_batch_submit(int count, const bto_batch_desc *descs, int tile_cols, void *ws,

@@ -115,6 +115,8 @@ def lib():
         L.bto_workspace_bytes.restype = _c_int
         L.bto_device_status.argtypes = [_c_ptr, _c_ptr, ctypes.POINTER(_c_int)]
         L.bto_device_status.restype = _c_int
+        L.bto_batch_one_launch.argtypes = [_c_ptr, ctypes.POINTER(_c_int)]
+        L.bto_batch_one_launch.restype = _c_int
         L.bto_bicgk_mrhs_workspace_bytes.argtypes = [_c_i64, _c_i64, _c_i64, ctypes.POINTER(_c_size)]
         L.bto_bicgk_mrhs_workspace_bytes.restype = _c_int
         _LIB = L
@@ -351,6 +353,16 @@ def bto_device_status(ws, stream=None):
     if st != BTO_OK:
         raise BtoError("bto_device_status", st, L.bto_last_invalid_arg())
     return out.value
+
+
+def bto_batch_one_launch(ws):
+    """True when bto_batch_run takes the one-launch form for workspace ws."""
+    out = _c_int(0)
+    L = lib()
+    st = L.bto_batch_one_launch(_ptr(ws), ctypes.byref(out))
+    if st != BTO_OK:
+        raise BtoError("bto_batch_one_launch", st, L.bto_last_invalid_arg())
+    return out.value == 1
 
 
 class BatchDesc(ctypes.Structure):

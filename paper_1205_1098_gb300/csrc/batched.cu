@@ -26,6 +26,8 @@
 #include "check.cuh"
 #include "lp_math.cuh"
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 #include <cstring>
 #include <vector>
 
@@ -811,8 +813,35 @@ void write_image(const Plan& P, char* img, bool counters, char* ws) {
     if (!P.items.empty()) std::memcpy(img + P.h.off_items, P.items.data(), P.items.size() * sizeof(Item));
 }
 
+// The one-launch form (bt_fused) runs a prepared workspace when every instance
+// takes the TMA path with one storage type and the device launches
+// cooperatively: its storage type, or -1.
+int fused_type(const Plan& P) {
+    if (!P.items.empty() || bt_plan_empty(P.bt)) return -1;
+    DeviceInfo dinf;
+    if (!device_info(&dinf) || !dinf.coop) return -1;
+    return bt_fused_type(P.bt);
+}
+
+// Workspaces prepared for the one-launch form, with their storage type, so
+// that bto_batch_run (which sees only the workspace) takes it.
+std::mutex g_fused_mu;
+std::unordered_map<const void*, int> g_fused_ws;
+
+void note_fused(const void* ws, int type) {
+    std::lock_guard<std::mutex> lock(g_fused_mu);
+    if (type >= 0) g_fused_ws[ws] = type;
+    else g_fused_ws.erase(ws);
+}
+
+int fused_of(const void* ws) {
+    std::lock_guard<std::mutex> lock(g_fused_mu);
+    const auto it = g_fused_ws.find(ws);
+    return it == g_fused_ws.end() ? -1 : it->second;
+}
+
 bto_status submit_plan(const Plan& P, void* ws, size_t ws_bytes, void* staging, size_t staging_bytes,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool allow_fused) {
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < (size_t)P.h.total) return BTO_ERR_WORKSPACE;
     DeviceInfo dinf;
     if (!device_info(&dinf)) return BTO_ERR_CUDA;
@@ -830,9 +859,14 @@ bto_status submit_plan(const Plan& P, void* ws, size_t ws_bytes, void* staging, 
         if (cudaMemcpyAsync(ws, img.data(), nb, cudaMemcpyHostToDevice, st) != cudaSuccess) return BTO_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return BTO_ERR_CUDA;
     }
+    char* w = static_cast<char*>(ws);
+    // The workspace now holds this plan: a later bto_batch_run takes its form.
+    const int ft = allow_fused ? fused_type(P) : -1;
+    note_fused(ws, ft);
+    if (ft >= 0) return bt_launch_fused(w, ft, st);
     // Only the queues that hold items, each grid no larger than its items:
     // a small batch leaves the other SMs to work on other streams.
-    char* w = static_cast<char*>(ws);
+
     const int64_t full = (int64_t)dinf.sms * occ;
     for (int q = 0; q < kQueues; q++) {
         const int64_t ni = P.h.qstart[q + 1] - P.h.qstart[q];
@@ -871,7 +905,9 @@ size_t batch_plan_image_bytes(const BatchPlan* b) { return image_bytes(b->p, tru
 
 bto_status batch_plan_submit(const BatchPlan* b, void* ws, size_t ws_bytes, void* staging, size_t staging_bytes,
                              cudaStream_t st) {
-    return submit_plan(b->p, ws, ws_bytes, staging, staging_bytes, st);
+    // The serving loop: its slots run side by side, so no cooperative launch
+    // that would hold every SM.
+    return submit_plan(b->p, ws, ws_bytes, staging, staging_bytes, st, false);
 }
 
 }  // namespace bto
@@ -915,6 +951,7 @@ extern "C" bto_status bto_batch_prepare(int count, const bto_batch_desc* descs, 
         return BTO_ERR_CUDA;
     // The host image is released on return: wait for the copy to leave it.
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return BTO_ERR_CUDA;
+    note_fused(ws, fused_type(P));
     return BTO_OK;
 }
 
@@ -928,6 +965,9 @@ extern "C" bto_status bto_batch_run(void* ws, size_t ws_bytes, bto_stream_t stre
     if (occ == 0) return BTO_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     char* w = static_cast<char*>(ws);
+    // A workspace prepared for the one-launch form: that launch alone.
+    const int ft = fused_of(ws);
+    if (ft >= 0) return bt_launch_fused(w, ft, st);
     const int grid = dinf.sms * occ;
     batch_reset_kernel<<<1, 256, 0, st>>>(w);
     if (cudaGetLastError() != cudaSuccess) return BTO_ERR_CUDA;
@@ -942,6 +982,14 @@ extern "C" bto_status bto_batch_run(void* ws, size_t ws_bytes, bto_stream_t stre
     return bt_launch(w, nullptr, st);
 }
 
+extern "C" bto_status bto_batch_one_launch(const void* ws, int* one) {
+    clear_invalid_arg();
+    if (!ws) { set_invalid_arg(1); return BTO_ERR_INVALID_VALUE; }
+    if (!one) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
+    *one = fused_of(ws) >= 0 ? 1 : 0;
+    return BTO_OK;
+}
+
 extern "C" bto_status bto_batch_submit(int count, const bto_batch_desc* descs, int tile_cols, void* ws,
                                        size_t ws_bytes, void* staging, size_t staging_bytes,
                                        bto_stream_t stream) {
@@ -953,7 +1001,7 @@ extern "C" bto_status bto_batch_submit(int count, const bto_batch_desc* descs, i
     Plan P;
     int bad = -1;
     if (!make_plan(count, descs, tile_cols, &P, &bad)) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
-    const bto_status e = submit_plan(P, ws, ws_bytes, staging, staging_bytes, (cudaStream_t)stream);
+    const bto_status e = submit_plan(P, ws, ws_bytes, staging, staging_bytes, (cudaStream_t)stream, true);
     if (e == BTO_ERR_WORKSPACE) set_invalid_arg(4);
     return e;
 }

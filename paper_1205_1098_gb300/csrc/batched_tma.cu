@@ -98,6 +98,7 @@ struct BtChunk { int32_t job, start; };   // 256 consecutive outputs of one comb
 
 struct BtHeader {
     int32_t ninst, pad;
+    uint32_t bar_count, bar_gen;   // the one-launch form's grid barrier (zero when uploaded)
     int32_t nitems[2][2];      // [stage][FP32, BF16]
     int32_t ncomb[2];
     int32_t nchunk[2];
@@ -346,10 +347,26 @@ __device__ __forceinline__ void consume(const BtItem& it, const BtInst& in, cons
     named_bar(1, kConsumers);
 }
 
+// Shared memory of the sweep (bt_smem<TA>() bytes), carved once per block.
 template <typename TA>
-__global__ void __launch_bounds__(kThreadsT, 1) bt_sweep(char* ws, int stage) {
-    const BtHeader* bh = bt_header(ws);
-    if (!bh) return;
+__device__ __forceinline__ Smem carve(unsigned char* smraw) {
+    Smem sm;
+    sm.ring = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    sm.full = reinterpret_cast<uint64_t*>(sm.ring + kStagesT * stage_bytes<TA>());
+    sm.empty = sm.full + kStagesT;
+    sm.qred = reinterpret_cast<float*>(sm.empty + kStagesT);
+    sm.shi = sm.qred + 2 * kCW * kBoxR;
+    sm.slo = sm.shi + kMaxTw;
+    return sm;
+}
+
+// One stage's sweep over this block's items of storage type TA: the producer
+// warp copies their boxes through the ring, the consumer warps run them.  The
+// ring's position (g for the producer, slot and ph for the consumers) carries
+// over from one call to the next.
+template <typename TA>
+__device__ __forceinline__ void sweep_stage(char* ws, const BtHeader* bh, int stage, const Smem& sm0,
+                                            volatile int* abortp, long long& g, int& slot, uint32_t& ph) {
     constexpr int T = sizeof(TA) == 2 ? 1 : 0;
     const int nitems = bh->nitems[stage][T];
     if ((int)blockIdx.x >= nitems) return;
@@ -358,55 +375,37 @@ __global__ void __launch_bounds__(kThreadsT, 1) bt_sweep(char* ws, int stage) {
     int* status = reinterpret_cast<int*>(ws);
     constexpr int S = kStagesT;
     constexpr int kBoxC = Cfg<TA>::BoxC;
-    extern __shared__ unsigned char smraw[];
-    Smem sm;
-    sm.ring = reinterpret_cast<unsigned char*>(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    sm.full = reinterpret_cast<uint64_t*>(sm.ring + S * stage_bytes<TA>());
-    sm.empty = sm.full + S;
-    sm.qred = reinterpret_cast<float*>(sm.empty + S);
-    sm.shi = sm.qred + 2 * kCW * kBoxR;
-    sm.slo = sm.shi + kMaxTw;
+    Smem sm = sm0;
     float* vbuf = sm.slo + kMaxTw;      // [2][3][kMaxTw]
-    __shared__ int s_abort_;
-    volatile int* abortp = &s_abort_;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < S; s++) {
-            mbar_init(&sm.full[s], 1);
-            mbar_init(&sm.empty[s], kCW);
-        }
-        *abortp = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
 
     if (warp == kCW) {
         // ---------------- producer: every box of this block's items, in order
         if (lane == 0) {
             TA* ring = reinterpret_cast<TA*>(sm.ring);
-            long long g = 0;
+            const long long g0 = g;
             for (int t = blockIdx.x; t < nitems && !*abortp; t += gridDim.x) {
                 const BtItem it = items[t];
                 const CUtensorMap* map = it.matB ? &insts[it.inst].mapB : &insts[it.inst].mapA;
                 for (int R0 = it.r0; R0 < it.r1 && !*abortp; R0 += kBoxR) {
                     for (int cs = it.c0; cs < it.c1; cs += kBoxC, g++) {
-                        const int slot = (int)(g % S);
-                        if (g >= S && !mbar_wait_bounded(&sm.empty[slot], (uint32_t)(((g / S) - 1) & 1), kWaitNs, abortp)) {
+                        const int slot_ = (int)(g % S);
+                        if (g >= S && !mbar_wait_bounded(&sm.empty[slot_], (uint32_t)(((g / S) - 1) & 1), kWaitNs, abortp)) {
                             atomicExch(status, (int)BTO_ERR_TIMEOUT);
                             *abortp = 1;
                             break;
                         }
-                        mbar_arrive_expect_tx(&sm.full[slot], (uint32_t)stage_bytes<TA>());
-                        tma_load_2d(ring + (size_t)slot * kBoxR * kBoxC, map, R0, cs, &sm.full[slot]);
+                        mbar_arrive_expect_tx(&sm.full[slot_], (uint32_t)stage_bytes<TA>());
+                        tma_load_2d(ring + (size_t)slot_ * kBoxR * kBoxC, map, R0, cs, &sm.full[slot_]);
                     }
                 }
             }
             if (*abortp) {
                 // Wait (bounded) for the copies this thread issued before leaving.
-                const long long first = g > S ? g - S : 0;
+                const long long first = g - S > g0 ? g - S : g0;
                 for (long long h = first; h < g; h++) {
-                    const int slot = (int)(h % S);
-                    mbar_wait_timed(&sm.full[slot], (uint32_t)((h / S) & 1), kWaitNs);
+                    const int slot_ = (int)(h % S);
+                    mbar_wait_timed(&sm.full[slot_], (uint32_t)((h / S) & 1), kWaitNs);
                 }
             }
         }
@@ -416,8 +415,6 @@ __global__ void __launch_bounds__(kThreadsT, 1) bt_sweep(char* ws, int stage) {
     // ---------------- consumers
     // Column vectors go through two buffers: the next item's are copied
     // (cp.async) while this item runs.
-    int slot = 0;
-    uint32_t ph = 0;
     int buf = 0;
     {
         const BtItem first = items[blockIdx.x];
@@ -446,6 +443,37 @@ __global__ void __launch_bounds__(kThreadsT, 1) bt_sweep(char* ws, int stage) {
             default: consume<TA, LP_S>(it, in, sm, slot, ph, abortp, status); break;
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <typename TA>
+__device__ __forceinline__ void init_ring(const Smem& sm, volatile int* abortp) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStagesT; s++) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], kCW);
+        }
+        *abortp = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(kThreadsT, 1) bt_sweep(char* ws, int stage) {
+    const BtHeader* bh = bt_header(ws);
+    if (!bh) return;
+    constexpr int T = sizeof(TA) == 2 ? 1 : 0;
+    if ((int)blockIdx.x >= bh->nitems[stage][T]) return;
+    extern __shared__ unsigned char smraw[];
+    const Smem sm = carve<TA>(smraw);
+    __shared__ int s_abort_;
+    volatile int* abortp = &s_abort_;
+    init_ring<TA>(sm, abortp);
+    long long g = 0;
+    int slot = 0;
+    uint32_t ph = 0;
+    sweep_stage<TA>(ws, bh, stage, sm, abortp, g, slot, ph);
 }
 
 // out[i] = a1 sum_k P[k][i] + a2 sum_k P2[k][i] + b v[i], each partial a
@@ -471,9 +499,11 @@ __device__ __forceinline__ double sum_partials(const float2* P, int64_t ld, int 
     return s;
 }
 
-__global__ void __launch_bounds__(256) bt_combine(const char* ws, int stage) {
-    const BtHeader* bh = bt_header(ws);
-    if (!bh) return;
+// One stage's combine, chunks dealt over the grid, one output per thread of
+// the block's first 256 threads (out[i] = a1 sum_k P[k][i] + a2 sum_k P2[k][i]
+// + b v[i], as described above).
+__device__ __forceinline__ void combine_stage(const char* ws, const BtHeader* bh, int stage) {
+    if (threadIdx.x >= 256) return;
     const int nch = bh->nchunk[stage];
     const BtComb* jobs = reinterpret_cast<const BtComb*>(ws + bh->off_comb[stage]);
     const BtChunk* chunks = reinterpret_cast<const BtChunk*>(ws + bh->off_chunk[stage]);
@@ -488,6 +518,84 @@ __global__ void __launch_bounds__(256) bt_combine(const char* ws, int stage) {
             if (c.v) o = fma(c.b, (double)__ldcg(c.v + i), o);
             c.out[i] = (float)o;
         }
+    }
+}
+
+__global__ void __launch_bounds__(256) bt_combine(const char* ws, int stage) {
+    const BtHeader* bh = bt_header(ws);
+    if (!bh) return;
+    combine_stage(ws, bh, stage);
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier of the one-launch form, bounded (about two seconds of
+// %globaltimer, then BTO_ERR_TIMEOUT in the status word and false).  It resets
+// itself: a block reads the generation before it arrives; the last of the
+// grid to arrive zeroes the count and then advances the generation, which
+// releases the others.  Nothing has to be cleared between runs.
+__device__ __forceinline__ bool grid_sync(BtHeader* bh, int* status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen0 = ld_acquire_gpu(&bh->bar_gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&bh->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            *reinterpret_cast<volatile unsigned*>(&bh->bar_count) = 0u;
+            __threadfence();
+            st_release_gpu(&bh->bar_gen, gen0 + 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_gpu(&bh->bar_gen) == gen0) {
+                if (global_ns() - t0 > kWaitNs) {
+                    atomicExch(status, (int)BTO_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The whole batch in one cooperative launch, when every instance takes the
+// TMA path with storage type TA: stage one's sweep, a grid barrier, its
+// combine, a barrier, stage two's sweep, a barrier, its combine.  The copy
+// ring runs on across the stages.  The status word is cleared by block 0 at
+// the start (a timeout needs seconds of waiting, so no block can have set it).
+template <typename TA>
+__global__ void __launch_bounds__(kThreadsT, 1) bt_fused(char* ws) {
+    BtHeader* bh = const_cast<BtHeader*>(bt_header(ws));
+    if (!bh) return;
+    int* status = reinterpret_cast<int*>(ws);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *status = BTO_OK;
+    extern __shared__ unsigned char smraw[];
+    const Smem sm = carve<TA>(smraw);
+    __shared__ int s_abort_;
+    volatile int* abortp = &s_abort_;
+    init_ring<TA>(sm, abortp);
+    long long g = 0;
+    int slot = 0;
+    uint32_t ph = 0;
+#pragma unroll 1
+    for (int stage = 0; stage < 2; stage++) {
+        sweep_stage<TA>(ws, bh, stage, sm, abortp, g, slot, ph);
+        if (!grid_sync(bh, status)) return;
+        combine_stage(ws, bh, stage);
+        if (stage == 0 && !grid_sync(bh, status)) return;
     }
 }
 
@@ -759,7 +867,9 @@ bool bt_setup() {
     static int done = 0;
     if (!done) {
         if (cudaFuncSetAttribute(bt_sweep<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem<TA>()) !=
-            cudaSuccess) {
+                cudaSuccess ||
+            cudaFuncSetAttribute(bt_fused<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem<TA>()) !=
+                cudaSuccess) {
             cudaGetLastError();
             return false;
         }
@@ -769,6 +879,34 @@ bool bt_setup() {
 }
 
 }  // namespace
+
+// The one-launch form applies when every item has storage type 0 (FP32) or
+// every item type 1 (BF16): returns that type, or -1.
+int bt_fused_type(const BtPlan* P) {
+    const bool f32 = P->nitems[0][0] + P->nitems[1][0] > 0, bf16 = P->nitems[0][1] + P->nitems[1][1] > 0;
+    if (f32 == bf16) return -1;
+    return f32 ? 0 : 1;
+}
+
+// Launches bt_fused<type> cooperatively (one block per SM).
+bto_status bt_launch_fused(char* ws, int type, cudaStream_t st) {
+    DeviceInfo dinf;
+    if (!device_info(&dinf) || !dinf.coop) return BTO_ERR_CUDA;
+    if (!bt_setup<float>() || !bt_setup<__nv_bfloat16>()) return BTO_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(dinf.sms);
+    cfg.blockDim = dim3(kThreadsT);
+    cfg.dynamicSmemBytes = type ? bt_smem<__nv_bfloat16>() : bt_smem<float>();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = type ? cudaLaunchKernelEx(&cfg, bt_fused<__nv_bfloat16>, ws)
+                               : cudaLaunchKernelEx(&cfg, bt_fused<float>, ws);
+    return e == cudaSuccess ? BTO_OK : BTO_ERR_CUDA;
+}
 
 // Launches the TMA path: stage one (both storage types), its combine, stage
 // two, its combine.  With the host plan, only the launches that have work,

@@ -162,6 +162,10 @@ int64_t bt_plan_layout_records(BtPlan* p, int64_t cur, int grid);   // grid: the
 int64_t bt_plan_layout_partials(BtPlan* p, int64_t cur);
 void bt_plan_write(const BtPlan* p, char* img, char* ws);
 bto_status bt_launch(char* ws, const BtPlan* p, cudaStream_t st);
+// The one-launch form (bt_fused): the storage type every TMA item has (0 FP32,
+// 1 BF16), or -1 when both occur; and its cooperative launch.
+int bt_fused_type(const BtPlan* p);
+bto_status bt_launch_fused(char* ws, int type, cudaStream_t st);
 
 // Batched form, planned once and submitted (the serving runtime's path).
 struct BatchPlan;

@@ -199,3 +199,12 @@ def test_schedule_overrides_without_gpu(L):
     finally:
         bto.bto_schedule_set(bto.OPS["gemver"], 1, 0, 0)
     assert bto.bto_schedule_get("gemver", 1) == (0, 0)
+
+
+def test_batch_one_launch_query_without_gpu(L):
+    # No device work: a NULL workspace is argument 1; a workspace nothing was
+    # prepared in runs the multi-launch form.
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_batch_one_launch(None)
+    assert e.value.status == bto.BTO_ERR_INVALID_VALUE and e.value.arg == 1
+    assert bto.bto_batch_one_launch(0x10000) is False

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+import paper_1205_1098_gb300 as bto
 import synth
 from batch_util import Batch, logu_sizes
 from gpu_util import relerr
@@ -136,3 +137,35 @@ def test_batch_tall_and_wide_tma(tile_cols):
     assert one.run(tile_cols) == 0
     for k, (g1, g2) in enumerate(zip(one.result(0), mixed[5])):
         assert np.array_equal(g1, g2, equal_nan=True), k
+
+
+# Every instance FP32 with 16-byte leading dimensions: the whole batch is one
+# cooperative launch (both stages and their combines behind grid barriers).
+ONE = [("bicgk", 1000, 700, 1000), ("gemver", 1300, 900, 1300), ("atax", 800, 1200, 800),
+       ("gesummv", 640, 700, 640), ("bicgk", 4400, 600, 4400), ("gemver", 2100, 1500, 2100),
+       ("atax", 5000, 300, 5000), ("gemver", 4, 4, 4), ("bicgk", 4100, 9, 4100)]
+
+
+@pytest.mark.parametrize("tile_cols", [64, 512])
+def test_batch_one_launch_form(tile_cols):
+    """The one-launch form: taken for a single-type, TMA-suited batch (and not
+    once a BF16 instance joins it); every instance against the oracle; the
+    bits of the multi-launch form for the same instances; graph replay and
+    bto_batch_submit equal to a plain run."""
+    b = Batch(ONE, seed=17)
+    assert b.run(tile_cols) == 0
+    assert bto.bto_batch_one_launch(b.ws)
+    check_batch(b)
+    ref = [b.result(i) for i in range(len(ONE))]
+    mixed = Batch(ONE + [("bicgk", 300, 200, 300, "bf16")], seed=17)
+    assert mixed.run(tile_cols) == 0
+    assert not bto.bto_batch_one_launch(mixed.ws)
+    for i in range(len(ONE)):
+        for k, (g1, g2) in enumerate(zip(mixed.result(i), ref[i])):
+            assert np.array_equal(g1, g2, equal_nan=True), (ONE[i], k)
+    assert b.run(tile_cols, graph=True, reps=3) == 0
+    assert b.submit(tile_cols) == 0
+    assert bto.bto_batch_one_launch(b.ws)
+    for i in range(len(ONE)):
+        for k, (g1, g2) in enumerate(zip(b.result(i), ref[i])):
+            assert np.array_equal(g1, g2, equal_nan=True), (ONE[i], k)

@@ -836,6 +836,16 @@ bto_status bto_debug_atax_stall(int64_t m, int64_t n, double beta, const double 
                                 const double *x, double *y, void *ws, size_t ws_bytes,
                                 int64_t stall_band, int timeout_ms, bto_stream_t stream);
 
+/* Fault injection for the grid barriers of the batched form's one-launch
+ * form (see bto_batch_run; the workspace must have been prepared for it,
+ * else BTO_ERR_UNSUPPORTED).  Runs it with block `stall_block` never
+ * arriving at the barriers, so every wait expires after `timeout_ms`
+ * (1..10000) milliseconds: the outputs are unspecified and
+ * bto_device_status reads BTO_ERR_TIMEOUT; prepare the workspace again before
+ * the next run.  No fault is raised on the device. */
+bto_status bto_debug_batch_stall(void *ws, size_t ws_bytes, int stall_block, int timeout_ms,
+                                 bto_stream_t stream);
+
 /* Fault injection for the grid barrier of the one-launch GEMVER (bto_gemver
  * takes it for matrices with m n <= 2^23 and max(3 m, 2 n) <= 12800 when the
  * device allows a cooperative launch).  Runs that form with block

@@ -39,6 +39,7 @@ SIGNATURES = {
     "bto_fill_f32": "uukiippis",
     "bto_fill_bf16": "uukiippis",
     "bto_debug_atax_stall": "iidpipppziks",
+    "bto_debug_batch_stall": "pzkks",
     "bto_debug_gemver_stall": "iiddpipppppppipppzkks",
     "bto_bicgk_noalloc": "iipipppps",
     "bto_bicgk_ex": "iikpipppppzs",

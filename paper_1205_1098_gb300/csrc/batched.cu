@@ -982,6 +982,21 @@ extern "C" bto_status bto_batch_run(void* ws, size_t ws_bytes, bto_stream_t stre
     return bt_launch(w, nullptr, st);
 }
 
+// Fault injection for tests (bto.h's testing section): the one-launch form
+// of a prepared workspace with block `stall_block` never arriving at the grid
+// barriers, so that every wait expires after `timeout_ms`.
+extern "C" bto_status bto_debug_batch_stall(void* ws, size_t ws_bytes, int stall_block, int timeout_ms,
+                                            bto_stream_t stream) {
+    clear_invalid_arg();
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) { set_invalid_arg(1); return BTO_ERR_INVALID_VALUE; }
+    if (ws_bytes < 1024) { set_invalid_arg(2); return BTO_ERR_WORKSPACE; }
+    if (timeout_ms < 1 || timeout_ms > 10000) { set_invalid_arg(4); return BTO_ERR_INVALID_VALUE; }
+    const int ft = fused_of(ws);
+    if (ft < 0) return BTO_ERR_UNSUPPORTED;
+    return bt_launch_fused(static_cast<char*>(ws), ft, (cudaStream_t)stream, stall_block,
+                           (unsigned long long)timeout_ms * 1000000ull);
+}
+
 extern "C" bto_status bto_batch_one_launch(const void* ws, int* one) {
     clear_invalid_arg();
     if (!ws) { set_invalid_arg(1); return BTO_ERR_INVALID_VALUE; }

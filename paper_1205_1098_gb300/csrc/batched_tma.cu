@@ -541,22 +541,23 @@ __device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
 // itself: a block reads the generation before it arrives; the last of the
 // grid to arrive zeroes the count and then advances the generation, which
 // releases the others.  Nothing has to be cleared between runs.
-__device__ __forceinline__ bool grid_sync(BtHeader* bh, int* status) {
+__device__ __forceinline__ bool grid_sync(BtHeader* bh, int* status, int stall_block, unsigned long long limit_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned gen0 = ld_acquire_gpu(&bh->bar_gen);
         __threadfence();
-        const unsigned arrived = atomicAdd(&bh->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
+        // (stall_block: fault injection for tests, a block that never arrives.)
+        const unsigned arrived = (int)blockIdx.x == stall_block ? 0u : atomicAdd(&bh->bar_count, 1u);
+        if ((int)blockIdx.x != stall_block && arrived == gridDim.x - 1) {
             *reinterpret_cast<volatile unsigned*>(&bh->bar_count) = 0u;
             __threadfence();
             st_release_gpu(&bh->bar_gen, gen0 + 1u);
         } else {
             const unsigned long long t0 = global_ns();
             while (ld_acquire_gpu(&bh->bar_gen) == gen0) {
-                if (global_ns() - t0 > kWaitNs) {
+                if (global_ns() - t0 > limit_ns) {
                     atomicExch(status, (int)BTO_ERR_TIMEOUT);
                     ok = 0;
                     break;
@@ -577,7 +578,7 @@ __device__ __forceinline__ bool grid_sync(BtHeader* bh, int* status) {
 // ring runs on across the stages.  The status word is cleared by block 0 at
 // the start (a timeout needs seconds of waiting, so no block can have set it).
 template <typename TA>
-__global__ void __launch_bounds__(kThreadsT, 1) bt_fused(char* ws) {
+__global__ void __launch_bounds__(kThreadsT, 1) bt_fused(char* ws, int stall_block, unsigned long long limit_ns) {
     BtHeader* bh = const_cast<BtHeader*>(bt_header(ws));
     if (!bh) return;
     int* status = reinterpret_cast<int*>(ws);
@@ -593,9 +594,9 @@ __global__ void __launch_bounds__(kThreadsT, 1) bt_fused(char* ws) {
 #pragma unroll 1
     for (int stage = 0; stage < 2; stage++) {
         sweep_stage<TA>(ws, bh, stage, sm, abortp, g, slot, ph);
-        if (!grid_sync(bh, status)) return;
+        if (!grid_sync(bh, status, stall_block, limit_ns)) return;
         combine_stage(ws, bh, stage);
-        if (stage == 0 && !grid_sync(bh, status)) return;
+        if (stage == 0 && !grid_sync(bh, status, stall_block, limit_ns)) return;
     }
 }
 
@@ -889,7 +890,7 @@ int bt_fused_type(const BtPlan* P) {
 }
 
 // Launches bt_fused<type> cooperatively (one block per SM).
-bto_status bt_launch_fused(char* ws, int type, cudaStream_t st) {
+bto_status bt_launch_fused(char* ws, int type, cudaStream_t st, int stall_block, unsigned long long limit_ns) {
     DeviceInfo dinf;
     if (!device_info(&dinf) || !dinf.coop) return BTO_ERR_CUDA;
     if (!bt_setup<float>() || !bt_setup<__nv_bfloat16>()) return BTO_ERR_CUDA;
@@ -903,8 +904,8 @@ bto_status bt_launch_fused(char* ws, int type, cudaStream_t st) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = type ? cudaLaunchKernelEx(&cfg, bt_fused<__nv_bfloat16>, ws)
-                               : cudaLaunchKernelEx(&cfg, bt_fused<float>, ws);
+    const cudaError_t e = type ? cudaLaunchKernelEx(&cfg, bt_fused<__nv_bfloat16>, ws, stall_block, limit_ns)
+                               : cudaLaunchKernelEx(&cfg, bt_fused<float>, ws, stall_block, limit_ns);
     return e == cudaSuccess ? BTO_OK : BTO_ERR_CUDA;
 }
 

@@ -165,7 +165,8 @@ bto_status bt_launch(char* ws, const BtPlan* p, cudaStream_t st);
 // The one-launch form (bt_fused): the storage type every TMA item has (0 FP32,
 // 1 BF16), or -1 when both occur; and its cooperative launch.
 int bt_fused_type(const BtPlan* p);
-bto_status bt_launch_fused(char* ws, int type, cudaStream_t st);
+bto_status bt_launch_fused(char* ws, int type, cudaStream_t st, int stall_block = -1,
+                           unsigned long long limit_ns = 2000000000ull);
 
 // Batched form, planned once and submitted (the serving runtime's path).
 struct BatchPlan;

@@ -169,3 +169,19 @@ def test_batch_one_launch_form(tile_cols):
     for i in range(len(ONE)):
         for k, (g1, g2) in enumerate(zip(b.result(i), ref[i])):
             assert np.array_equal(g1, g2, equal_nan=True), (ONE[i], k)
+
+
+def test_batch_one_launch_barrier_times_out_and_context_survives():
+    """A block that never arrives at the one-launch form's grid barrier: every
+    wait expires into the status word (no device fault); after preparing the
+    workspace again, a run succeeds with the usual results."""
+    b = Batch(ONE[:4], seed=19)
+    assert b.run(128) == 0 and bto.bto_batch_one_launch(b.ws)
+    ref = [b.result(i) for i in range(4)]
+    nb = bto.bto_batch_workspace_bytes(b.descs, 128)
+    bto.bto_debug_batch_stall(b.ws, nb, 3, 50, None)
+    assert bto.bto_device_status(b.ws) == bto.BTO_ERR_TIMEOUT
+    assert b.run(128) == 0
+    for i in range(4):
+        for k, (g1, g2) in enumerate(zip(b.result(i), ref[i])):
+            assert np.array_equal(g1, g2, equal_nan=True), (ONE[i], k)

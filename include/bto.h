@@ -475,8 +475,9 @@ bto_status bto_gesummv_ex(int64_t m, int64_t n, float alpha, float beta, int a_t
  * Use: bto_batch_workspace_bytes -> bto_batch_prepare (host: builds the work
  * list and copies it into ws, waiting for that copy) -> bto_batch_run, as
  * often as wanted while the descriptors' buffers stay valid.  bto_batch_run
- * only enqueues two kernels and performs no host synchronisation, so it may
- * be recorded into a CUDA graph.  Calls sharing a ws must be ordered.
+ * only enqueues kernels (one cooperative launch, or the few of the
+ * multi-launch form) and performs no host synchronisation, so it may be
+ * recorded into a CUDA graph.  Calls sharing a ws must be ordered.
  * tile_cols: width of the column panels each work item covers (16..1024, a
  * multiple of 16; 0 picks 128).  Second-stage items (GEMVER's w, ATAX's y)
  * wait for their instance's first stage with a bounded wait (about 2 s); a

@@ -203,12 +203,13 @@ __device__ __forceinline__ void consume(const BtItem& it, const BtInst& in, cons
             for (int gs = 0; gs < GS; gs++) {
                 const int64_t cs = gbase + (int64_t)gs * kBoxC;
                 if (cs < c1) {
-                    bool have = true;
-                    if (!*abortp && !mbar_wait_bounded(&sm.full[slot], ph, kWaitNs, abortp)) {
+                    // A stage that completed holds valid data even after an abort; once
+                    // the producer has stopped, the wait sees the flag on its first spin.
+                    const bool have = mbar_wait_bounded(&sm.full[slot], ph, kWaitNs, abortp);
+                    if (!have) {
                         if (lane == 0) atomicExch(status, (int)BTO_ERR_TIMEOUT);
                         *abortp = 1;
                     }
-                    if (*abortp) have = false;
                     const TA* buf = ring + (size_t)slot * kBoxR * kBoxC;
                     const int lc0 = (int)(cs - c0);
 #pragma unroll

@@ -339,12 +339,14 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                     if (cs < c1) {
 #pragma unroll
                         for (int u = 0; u < SPU; u++) {
-                            bool have = true;
-                            if (!*s_abort_p && !mbar_wait_bounded(&full[slot], ph, kWaitNs, s_abort_p)) {
+                            // A stage that completed holds valid data even after an
+                            // abort; once the producer has stopped, the wait sees the
+                            // abort flag on its first spin and returns false.
+                            const bool have = mbar_wait_bounded(&full[slot], ph, kWaitNs, s_abort_p);
+                            if (!have) {
                                 if (lane == 0) atomicExch(a.status, (int)BTO_ERR_TIMEOUT);
                                 *s_abort_p = 1;
                             }
-                            if (*s_abort_p) have = false;
                             const double* buf = ring + (size_t)slot * kBoxR * kBoxC;
                             const int lc0 = (int)(cs - c0);
 #pragma unroll

@@ -102,21 +102,40 @@ __global__ void __launch_bounds__(kGT, 2) gemver_small_kernel(const GsArgs a) {
     double* su2 = sm + m;
     float2* sy = reinterpret_cast<float2*>(sm + 2 * m);   // y as (hi, lo)
     bool ybad = false;
-    for (int64_t i = tid; i < m; i += kGT) {
-        su1[i] = __ldg(a.u1 + i);
-        su2[i] = __ldg(a.u2 + i);
-        const double yv = __ldg(a.y + i);
-        const uint32_t hw = (uint32_t)__double2hiint(yv), lw = (uint32_t)__double2loint(yv);
-        ybad |= df_out_of_range(hw, lw);
-        float h, l;
-        df::split_words(hw, lw, h, l);
-        sy[i] = make_float2(h, l);
+    // Four elements of each vector per thread at a time, their loads issued
+    // together (one round trip to L2 instead of four).
+    for (int64_t i0 = tid; i0 < m; i0 += 4 * kGT) {
+        double u1r[4], u2r[4], yr[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t i = i0 + (int64_t)u * kGT;
+            if (i < m) {
+                u1r[u] = __ldg(a.u1 + i);
+                u2r[u] = __ldg(a.u2 + i);
+                yr[u] = __ldg(a.y + i);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t i = i0 + (int64_t)u * kGT;
+            if (i < m) {
+                su1[i] = u1r[u];
+                su2[i] = u2r[u];
+                const uint32_t hw = (uint32_t)__double2hiint(yr[u]), lw = (uint32_t)__double2loint(yr[u]);
+                ybad |= df_out_of_range(hw, lw);
+                float h, l;
+                df::split_words(hw, lw, h, l);
+                sy[i] = make_float2(h, l);
+            }
+        }
     }
     ybad = __syncthreads_or(ybad) != 0;    // y out of range: every x in FP64
 
-    // ---- pass 1: whole columns per warp
+    // ---- pass 1: whole columns per warp, dealt over the blocks first
+    // (column j to block j mod G), so that every SM gets its share of the
+    // FP64 work when there are fewer columns than warps.
     const int64_t nw = (int64_t)gridDim.x * kGW;
-    for (int64_t j = (int64_t)blockIdx.x * kGW + warp; j < n; j += nw) {
+    for (int64_t j = (int64_t)warp * gridDim.x + blockIdx.x; j < n; j += nw) {
         const double v1j = __ldg(a.v1 + j), v2j = __ldg(a.v2 + j);
         const double* acol = a.A + j * a.lda;     // plain loads: B may overwrite A
         double* bcol = a.B + j * a.ldb;
@@ -132,13 +151,29 @@ __global__ void __launch_bounds__(kGT, 2) gemver_small_kernel(const GsArgs a) {
             const float2 yv = sy[ii];
             df_mac1(sh[k], sl[k], bh, bl, yv.x, yv.y);
         };
+        // Four rows per lane at a time; the next four are loaded before these
+        // are processed (other rows than the ones stored, so in-place B is
+        // safe), which the compiler cannot do across the stores by itself.
         int64_t i = lane;
-        for (; i + 96 < m; i += 128) {
+        if (i + 96 < m) {
             double av[4];
 #pragma unroll
             for (int u = 0; u < 4; u++) av[u] = acol[i + 32 * u];
+            while (true) {
+                const int64_t in = i + 128;
+                const bool more = in + 96 < m;
+                double nx[4];
+                if (more) {
 #pragma unroll
-            for (int u = 0; u < 4; u++) one(i + 32 * u, av[u], u & 1);
+                    for (int u = 0; u < 4; u++) nx[u] = acol[in + 32 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) one(i + 32 * u, av[u], u & 1);
+                i = in;
+                if (!more) break;
+#pragma unroll
+                for (int u = 0; u < 4; u++) av[u] = nx[u];
+            }
         }
         for (; i < m; i += 32) one(i, acol[i], 0);
         df_add1(sh[0], sl[0], sh[1], sl[1]);
@@ -185,14 +220,25 @@ __global__ void __launch_bounds__(kGT, 2) gemver_small_kernel(const GsArgs a) {
     float2* sx = reinterpret_cast<float2*>(sm);    // x as (hi, lo)
     double* sxd = sm + n;                          // and in FP64 (for the fallback)
     bool xbad = false;
-    for (int64_t j = tid; j < n; j += kGT) {
-        const double xv = __ldcg(a.x + j);
-        const uint32_t hw = (uint32_t)__double2hiint(xv), lw = (uint32_t)__double2loint(xv);
-        xbad |= df_out_of_range(hw, lw);
-        float h, l;
-        df::split_words(hw, lw, h, l);
-        sx[j] = make_float2(h, l);
-        sxd[j] = xv;
+    for (int64_t j0 = tid; j0 < n; j0 += 8 * kGT) {
+        double xr[8];                              // eight loads in flight per thread
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int64_t j = j0 + (int64_t)u * kGT;
+            if (j < n) xr[u] = __ldcg(a.x + j);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int64_t j = j0 + (int64_t)u * kGT;
+            if (j < n) {
+                const uint32_t hw = (uint32_t)__double2hiint(xr[u]), lw = (uint32_t)__double2loint(xr[u]);
+                xbad |= df_out_of_range(hw, lw);
+                float h, l;
+                df::split_words(hw, lw, h, l);
+                sx[j] = make_float2(h, l);
+                sxd[j] = xr[u];
+            }
+        }
     }
     xbad = __syncthreads_or(xbad) != 0;
     const int r = tid % kP2Rows, g = tid / kP2Rows;

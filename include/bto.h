@@ -847,6 +847,19 @@ bto_status bto_debug_atax_stall(int64_t m, int64_t n, double beta, const double 
 bto_status bto_debug_batch_stall(void *ws, size_t ws_bytes, int stall_block, int timeout_ms,
                                  bto_stream_t stream);
 
+/* Fault injection for the ring waits of the double-float sweeps.  Runs
+ * bto_bicgk_df, except that in block `stall_block` (>= 0; a block of the
+ * sweep's grid) the producer stops after filling the ring once, so that
+ * block's consumer waits expire after `timeout_ms` (1..10000) milliseconds
+ * instead of about two seconds: q and s are unspecified and
+ * bto_device_status reads BTO_ERR_TIMEOUT when that block had more than one
+ * ring fill (five stages of 256 x 16) of work.  The next call clears the
+ * status word.  No fault is raised on the device.  BTO_ERR_UNSUPPORTED when
+ * the sizes or layout send the call to the FP64 form. */
+bto_status bto_debug_df_stall(int64_t m, int64_t n, const double *A, int64_t lda, const double *p,
+                              const double *r, double *q, double *s, void *ws, size_t ws_bytes,
+                              int stall_block, int timeout_ms, bto_stream_t stream);
+
 /* Fault injection for the grid barrier of the one-launch GEMVER (bto_gemver
  * takes it for matrices with m n <= 2^23 and max(3 m, 2 n) <= 12800 when the
  * device allows a cooperative launch).  Runs that form with block

@@ -220,17 +220,22 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
         // ---------------- producer
         if (lane == 0) {
             long long g = 0;
-            for (int64_t t = blockIdx.x; t < a.ntiles && !*s_abort_p; t += gridDim.x) {
+            bool stop = false;       // testing only: see DfArgs::stall_block
+            for (int64_t t = blockIdx.x; t < a.ntiles && !*s_abort_p && !stop; t += gridDim.x) {
                 const int64_t tt = a.reverse ? (a.ntiles - 1 - t) : t;
                 const int64_t cb = tt / a.NR, rb = tt % a.NR;
                 const int64_t c0 = lp_col_at(a.n, a.NC, cb, kBoxC), c1 = lp_col_at(a.n, a.NC, cb + 1, kBoxC);
                 const int64_t r0 = lp_row_at(a.m, a.NR, rb), r1 = lp_row_at(a.m, a.NR, rb + 1);
-                for (int64_t R0 = r0; R0 < r1 && !*s_abort_p; R0 += kBoxR) {
-                    for (int64_t cs = c0; cs < c1 && !*s_abort_p; cs += kBoxC) {
+                for (int64_t R0 = r0; R0 < r1 && !*s_abort_p && !stop; R0 += kBoxR) {
+                    for (int64_t cs = c0; cs < c1 && !*s_abort_p && !stop; cs += kBoxC) {
                         for (int u = 0; u < SPU; u++, g++) {
+                            if ((int)blockIdx.x == a.stall_block && g >= kStages) {
+                                stop = true;
+                                break;
+                            }
                             const int slot = (int)(g % kStages);
                             if (g >= kStages &&
-                                !mbar_wait_bounded(&empty[slot], (uint32_t)(((g / kStages) - 1) & 1), kWaitNs, s_abort_p)) {
+                                !mbar_wait_bounded(&empty[slot], (uint32_t)(((g / kStages) - 1) & 1), a.wait_ns, s_abort_p)) {
                                 atomicExch(a.status, (int)BTO_ERR_TIMEOUT);
                                 *s_abort_p = 1;
                                 break;
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                     }
                 }
             }
-            if (*s_abort_p) {
+            if (*s_abort_p || stop) {
                 // Wait (bounded) for the copies this thread issued before leaving.
                 const long long first = g > kStages ? g - kStages : 0;
                 for (long long h = first; h < g; h++) mbar_wait_timed(&full[(int)(h % kStages)], (uint32_t)((h / kStages) & 1), kWaitNs);
@@ -342,7 +347,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) df_kernel(const __grid_constant_
                             // A stage that completed holds valid data even after an
                             // abort; once the producer has stopped, the wait sees the
                             // abort flag on its first spin and returns false.
-                            const bool have = mbar_wait_bounded(&full[slot], ph, kWaitNs, s_abort_p);
+                            const bool have = mbar_wait_bounded(&full[slot], ph, a.wait_ns, s_abort_p);
                             if (!have) {
                                 if (lane == 0) atomicExch(a.status, (int)BTO_ERR_TIMEOUT);
                                 *s_abort_p = 1;
@@ -615,6 +620,8 @@ DfArgs df_args(int64_t m, int64_t n, const double* A, int64_t lda, const PanelPl
     a.ldq = pl.ldq; a.lds = pl.lds; a.tcmax = pl.TCmax;
     a.NR = pl.NR; a.NC = pl.NC; a.ntiles = pl.ntiles;
     a.status = static_cast<int*>(ws);
+    a.wait_ns = kWaitNs;
+    a.stall_block = -1;
     return a;
 }
 

@@ -227,6 +227,8 @@ struct DfArgs {
     int64_t ldq, lds, tcmax;
     int NR, NC; int64_t ntiles; int reverse;
     int* status;                       // device status word (timeouts of bounded waits)
+    unsigned long long wait_ns;        // limit of each ring wait (df_args: 2 s)
+    int stall_block;                   // testing: this block's producer stops after one ring fill (-1: none)
 };
 PanelPlan df_plan(int64_t m, int64_t n, int sms);
 // True when the matrices suit the tensor-map copies the sweep is built on

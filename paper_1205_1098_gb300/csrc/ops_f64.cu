@@ -113,9 +113,13 @@ bool df_ready(int form, int mode, const DfArgs& a, cudaStream_t st, bto_status* 
 
 }  // namespace
 
+// stall_block >= 0 (testing): the double-float sweep's producer in that block
+// stops after one ring fill and the ring waits give up after wait_ns; the
+// call is then BTO_ERR_UNSUPPORTED unless that sweep runs.
 static bto_status run_bicgk(int form, int64_t m, int64_t n, const double* A, int64_t lda,
                             const double* p, const double* r, double* q, double* s,
-                            void* ws, size_t ws_bytes, bto_stream_t stream) {
+                            void* ws, size_t ws_bytes, bto_stream_t stream, int stall_block = -1,
+                            unsigned long long wait_ns = 0) {
     clear_invalid_arg();
     Check c;
     c.size(1, m); c.size(2, n);
@@ -137,6 +141,10 @@ static bto_status run_bicgk(int form, int64_t m, int64_t n, const double* A, int
         const PanelPlan dp = df_plan(m, n, d.sms);
         DfArgs a = df_args(m, n, A, lda, dp, ws);
         a.p = p; a.r = r; a.qpart = wsd(ws, L.off[0]); a.spart = wsd(ws, L.off[1]);
+        if (stall_block >= 0) {
+            a.stall_block = stall_block;
+            a.wait_ns = wait_ns;
+        }
         bto_status e;
         if (df_ready(form, DF_QS, a, st, &e)) {
             if (e != BTO_OK || (e = df_launch(DF_QS, a, dp, st)) != BTO_OK) return e;
@@ -145,6 +153,7 @@ static bto_status run_bicgk(int form, int64_t m, int64_t n, const double* A, int
             j[1] = {s, n, a.spart, dp.lds, dp.NR, 1.0, nullptr, 0, 0, 0.0, nullptr, 0.0};
             return launch_combine(j, 2, st);
         }
+        if (stall_block >= 0) return BTO_ERR_UNSUPPORTED;
         if (form == BTO_FORM_DF && ws_layout(BTO_OP_BICGK, BTO_FORM_FUSED, m, n, BTO_F64, d, &L) != BTO_OK)
             return BTO_ERR_CUDA;
     }
@@ -383,6 +392,18 @@ extern "C" bto_status bto_bicgk_df(int64_t m, int64_t n, const double* A, int64_
                                    const double* r, double* q, double* s, void* ws, size_t ws_bytes,
                                    bto_stream_t stream) {
     return run_bicgk(BTO_FORM_DF, m, n, A, lda, p, r, q, s, ws, ws_bytes, stream);
+}
+// Fault injection for tests (declared in bto.h's testing section): the
+// double-float BICGK with block `stall_block`'s producer stopping after one
+// ring fill, so its consumers' waits expire after `timeout_ms`.
+extern "C" bto_status bto_debug_df_stall(int64_t m, int64_t n, const double* A, int64_t lda, const double* p,
+                                         const double* r, double* q, double* s, void* ws, size_t ws_bytes,
+                                         int stall_block, int timeout_ms, bto_stream_t stream) {
+    clear_invalid_arg();
+    if (stall_block < 0) { set_invalid_arg(11); return BTO_ERR_INVALID_VALUE; }
+    if (timeout_ms < 1 || timeout_ms > 10000) { set_invalid_arg(12); return BTO_ERR_INVALID_VALUE; }
+    return run_bicgk(BTO_FORM_DF, m, n, A, lda, p, r, q, s, ws, ws_bytes, stream, stall_block,
+                     (unsigned long long)timeout_ms * 1000000ull);
 }
 extern "C" bto_status bto_dgemv(int64_t m, int64_t n, double alpha, const double* A, int64_t lda,
                                 const double* x, double beta, const double* y, double* z, void* ws,

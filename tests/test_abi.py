@@ -91,6 +91,13 @@ def test_validation_without_gpu(L):
     with pytest.raises(bto.BtoError) as e:
         bto.bto_fill_f64(0, 0, 7, 4, 4, 0, 4096, 4, 0)
     assert e.value.arg == 3
+    # The ring-wait fault injection takes a block index and a limit of 1..10000 ms.
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_debug_df_stall(8, 4, 4096, 8, 4096, 8192, 12288, 16384, 0, 0, -1, 50, 0)
+    assert e.value.status == _lib.BTO_ERR_INVALID_VALUE and e.value.arg == 11
+    with pytest.raises(bto.BtoError) as e:
+        bto.bto_debug_df_stall(8, 4, 4096, 8, 4096, 8192, 12288, 16384, 0, 0, 0, 0, 0)
+    assert e.value.arg == 12
 
 
 def test_mrhs_validation_without_gpu(L):

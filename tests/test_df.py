@@ -270,3 +270,27 @@ def test_df_workspace_too_small_is_rejected():
     with pytest.raises(bto.BtoError) as e:
         bto.bto_bicgk_df(m, n, p(A), m, p(v), p(v), q.ptr(), s.ptr(), p(wk), nb - 8, None)
     assert e.value.status == bto.BTO_ERR_WORKSPACE and e.value.arg == 9
+
+
+def test_df_ring_wait_expires_into_the_status_word():
+    # Block 0's producer stops after one ring fill (its first tile has nine
+    # stages here), so that block's consumer waits run out after 50 ms: the
+    # status word reads BTO_ERR_TIMEOUT and the context stays usable.  The next
+    # ordinary call clears the status and matches the oracle.  (An even
+    # leading dimension, so that the double-float sweep takes the call.)
+    m, n = 3000, 1778
+    A = synth.matrix(23, 0, m, n)
+    pv, rv = synth.vector(23, 1, n), synth.vector(23, 2, m)
+    dA, dpv, drv = dev(A), dev(pv), dev(rv)
+    q, s = Out(m), Out(n)
+    w, nb = ws("bicgk", bto.BTO_FORM_DF, m, n)
+    args = (m, n, p(dA), m, p(dpv), p(drv), q.ptr(), s.ptr(), p(w), nb)
+    bto.bto_debug_df_stall(*args, 0, 50, None)
+    sync()
+    assert bto.bto_device_status(p(w)) == bto.BTO_ERR_TIMEOUT
+    bto.bto_bicgk_df(*args, None)
+    sync()
+    assert bto.bto_device_status(p(w)) == 0
+    qo, so = O.bicgk(m, n, A, pv, rv)
+    assert relerr(q.host(), qo) < TOL64
+    assert relerr(s.host(), so) < TOL64

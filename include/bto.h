@@ -847,6 +847,15 @@ bto_status bto_debug_atax_stall(int64_t m, int64_t n, double beta, const double 
 bto_status bto_debug_batch_stall(void *ws, size_t ws_bytes, int stall_block, int timeout_ms,
                                  bto_stream_t stream);
 
+/* The batched sweep's assignment of one list of work items to the `grid`
+ * (1..65536) blocks of its launch, computed on the host as bto_batch_prepare
+ * does for a list longer than the grid: items in decreasing cost (count >=
+ * 0 costs, each >= 0 and none above the one before it, else
+ * BTO_ERR_INVALID_VALUE, argument 2), each to the block with the least cost
+ * so far, ties to the lower block (longest processing time first).  Writes
+ * block[k] in [0, grid) for every item.  No device work. */
+bto_status bto_debug_lpt(int64_t count, const double *cost, int grid, int32_t *block);
+
 /* Fault injection for the ring waits of the double-float sweeps.  Runs
  * bto_bicgk_df, except that in block `stall_block` (>= 0; a block of the
  * sweep's grid) the producer stops after filling the ring once, so that

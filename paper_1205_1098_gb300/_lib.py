@@ -42,6 +42,7 @@ SIGNATURES = {
     "bto_debug_batch_stall": "pzkks",
     "bto_debug_gemver_stall": "iiddpipppppppipppzkks",
     "bto_debug_df_stall": "iipipppppzkks",
+    "bto_debug_lpt": "ipkp",
     "bto_bicgk_noalloc": "iipipppps",
     "bto_bicgk_ex": "iikpipppppzs",
     "bto_gemver_ex": "iiffkpipppppppipppzs",

@@ -914,6 +914,20 @@ bto_status batch_plan_submit(const BatchPlan* b, void* ws, size_t ws_bytes, void
 
 using namespace bto;
 
+// Testing (declared in bto.h's testing section): the batched sweep's
+// assignment of a list of items to the blocks of a grid, on the host.
+extern "C" bto_status bto_debug_lpt(int64_t count, const double* cost, int grid, int32_t* block) {
+    clear_invalid_arg();
+    if (count < 0) { set_invalid_arg(1); return BTO_ERR_INVALID_VALUE; }
+    if (count > 0 && !cost) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
+    for (int64_t k = 0; k < count; k++)
+        if (!(cost[k] >= 0.0) || (k > 0 && cost[k] > cost[k - 1])) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
+    if (grid < 1 || grid > 65536) { set_invalid_arg(3); return BTO_ERR_INVALID_VALUE; }
+    if (count > 0 && !block) { set_invalid_arg(4); return BTO_ERR_INVALID_VALUE; }
+    if (count > 0) lpt_blocks(cost, count, grid, block);
+    return BTO_OK;
+}
+
 extern "C" bto_status bto_batch_workspace_bytes(int count, const bto_batch_desc* descs, int tile_cols,
                                                 size_t* bytes) {
     clear_invalid_arg();

@@ -739,6 +739,29 @@ bool bt_plan_add(BtPlan* P, const bto_batch_desc& d) {
 // Assigns the regions of the plan's records (part of the uploaded image) from
 // `cur` on and returns the new end; sorts the items (stage, storage type,
 // decreasing size), orders each group for a grid of G blocks and counts them.
+// Longest-processing-time assignment (Graham): items 0..count-1, in
+// decreasing cost, each to the least loaded of G blocks, ties to the lower
+// block; lists[b] receives block b's items in order.
+static void lpt_assign(const double* cost, size_t count, int G, std::vector<std::vector<size_t>>& lists) {
+    lists.assign((size_t)G, {});
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> least;
+    for (int b = 0; b < G; b++) least.push(Load(0.0, b));
+    for (size_t k = 0; k < count; k++) {
+        const Load l = least.top();
+        least.pop();
+        lists[(size_t)l.second].push_back(k);
+        least.push(Load(l.first + cost[k], l.second));
+    }
+}
+
+void lpt_blocks(const double* cost, int64_t count, int G, int32_t* block) {
+    std::vector<std::vector<size_t>> lists;
+    lpt_assign(cost, (size_t)count, G, lists);
+    for (int b = 0; b < G; b++)
+        for (size_t k : lists[(size_t)b]) block[k] = b;
+}
+
 int64_t bt_plan_layout_records(BtPlan* P, int64_t cur, int G) {
     auto region = [&](int64_t bytes) { const int64_t at = cur; cur += round_up(std::max<int64_t>(bytes, 1), 256); return at; };
     // Items sorted by stage, storage type, then decreasing cost (ties: order of addition).
@@ -762,16 +785,10 @@ int64_t bt_plan_layout_records(BtPlan* P, int64_t cur, int G) {
             if ((int64_t)(j - i) <= G) {
                 out.insert(out.end(), P->items.begin() + i, P->items.begin() + j);
             } else {
-                std::vector<std::vector<size_t>> lists(G);
-                using Load = std::pair<double, int>;
-                std::priority_queue<Load, std::vector<Load>, std::greater<Load>> least;
-                for (int b = 0; b < G; b++) least.push(Load(0.0, b));
-                for (size_t k = i; k < j; k++) {
-                    const Load l = least.top();
-                    least.pop();
-                    lists[l.second].push_back(k);
-                    least.push(Load(l.first + P->items[k].cost, l.second));
-                }
+                std::vector<double> cost(j - i);
+                for (size_t k = i; k < j; k++) cost[k - i] = P->items[k].cost;
+                std::vector<std::vector<size_t>> lists;
+                lpt_assign(cost.data(), cost.size(), G, lists);
                 size_t K = 0;
                 for (const auto& l : lists) K = std::max(K, l.size());
                 BtPlan::ItemRec pad{};
@@ -780,7 +797,7 @@ int64_t bt_plan_layout_records(BtPlan* P, int64_t cur, int G) {
                 pad.stage = P->items[i].stage;
                 pad.type = P->items[i].type;
                 for (size_t k = 0; k < K; k++)
-                    for (int b = 0; b < G; b++) out.push_back(k < lists[b].size() ? P->items[lists[b][k]] : pad);
+                    for (int b = 0; b < G; b++) out.push_back(k < lists[b].size() ? P->items[i + lists[b][k]] : pad);
             }
             i = j;
         }

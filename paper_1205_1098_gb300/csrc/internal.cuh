@@ -159,6 +159,10 @@ void bt_plan_reset(BtPlan* p, int tile_cols);
 bool bt_plan_empty(const BtPlan* p);
 bool bt_plan_add(BtPlan* p, const bto_batch_desc& d);
 int64_t bt_plan_layout_records(BtPlan* p, int64_t cur, int grid);   // grid: the sweep's blocks (#SMs)
+// The assignment the layout uses for a (stage, type) list longer than the
+// grid: block[k] for items of the given costs (decreasing), longest
+// processing time first, ties to the lower block.
+void lpt_blocks(const double* cost, int64_t count, int grid, int32_t* block);
 int64_t bt_plan_layout_partials(BtPlan* p, int64_t cur);
 void bt_plan_write(const BtPlan* p, char* img, char* ws);
 bto_status bt_launch(char* ws, const BtPlan* p, cudaStream_t st);

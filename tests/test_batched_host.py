@@ -2,7 +2,11 @@
 validates every descriptor (op, storage type, sizes, leading dimensions,
 operands each op needs) and the panel width before anything touches a
 device, and sizes the workspace of valid batches.  Descriptors carry
-made-up aligned addresses; nothing is dereferenced on the host."""
+made-up aligned addresses; nothing is dereferenced on the host.  The
+sweep's assignment of work items to blocks (longest processing time first)
+is checked through bto_debug_lpt: a hand-worked example, equal items, and
+Graham's list-scheduling bound on uneven lists."""
+import numpy as np
 import pytest
 
 import paper_1205_1098_gb300 as bto
@@ -92,3 +96,52 @@ def test_panel_width_validation(tile, ok):
         with pytest.raises(bto.BtoError) as e:
             bto.bto_batch_workspace_bytes(descs, tile)
         assert e.value.arg == 3
+
+
+# ---- the sweep's assignment of work items to blocks (bto_debug_lpt)
+def _lpt(cost, grid):
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    block = np.full(len(cost), -1, dtype=np.int32)
+    bto.bto_debug_lpt(len(cost), cost.ctypes.data, grid, block.ctypes.data)
+    return block
+
+
+def test_lpt_hand_worked_example():
+    # Costs 9, 7, 6, 5, 4, 3, 1 over three blocks, worked by hand: 9, 7 and 6
+    # open the blocks; 5 joins the least loaded (block 2: 6 -> 11); 4 joins
+    # block 1 (7 -> 11); 3 joins block 0 (9 -> 12); 1 finds blocks 1 and 2
+    # tied at 11 and takes the lower (block 1 -> 12).  Loads 12, 12, 11.
+    assert _lpt([9, 7, 6, 5, 4, 3, 1], 3).tolist() == [0, 1, 2, 2, 1, 0, 1]
+
+
+def test_lpt_equal_items_are_dealt_round_robin():
+    assert np.array_equal(_lpt(np.full(1000, 2.5), 152), np.arange(1000) % 152)
+
+
+def test_lpt_short_lists_take_one_block_each():
+    assert _lpt([5.0, 4.0, 1.0], 8).tolist() == [0, 1, 2]
+    assert _lpt([], 8).tolist() == []
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lpt_balance_bound(seed):
+    # Each item goes to the least loaded block, so the busiest block exceeds
+    # the least busy one by at most the largest item, and the mean by at most
+    # (1 - 1/G) of it (Graham's bound for list scheduling).
+    rng = np.random.default_rng(seed)
+    cost = np.sort(np.exp(rng.uniform(np.log(1e3), np.log(4e6), 4096)))[::-1]
+    G = 152
+    block = _lpt(cost, G)
+    assert block.min() >= 0 and block.max() < G
+    load = np.bincount(block, weights=cost, minlength=G)
+    assert load.max() - load.min() <= cost.max() * (1 + 1e-12)
+    assert load.max() <= load.sum() / G + (1 - 1 / G) * cost.max() * (1 + 1e-12)
+
+
+def test_lpt_validation():
+    with pytest.raises(bto.BtoError) as e:
+        _lpt([1.0, 2.0], 4)          # not in decreasing order
+    assert e.value.status == _lib.BTO_ERR_INVALID_VALUE and e.value.arg == 2
+    with pytest.raises(bto.BtoError) as e:
+        _lpt([2.0, 1.0], 0)
+    assert e.value.arg == 3

@@ -416,7 +416,12 @@ bto_status bto_schedule_get(int op, int form, int *panels, int *row_blocks);
 /* The tile plan the FP64 matrix kernels use for `op` in `form` on an m x n
  * matrix with `sms` multiprocessors (overrides included): writes the number
  * of row blocks and column panels.  Host only; touches no device.  ATAX's
- * fused group-band kernel has its own plan; this is its two-pass plan. */
+ * fused group-band kernel has its own plan; this is its two-pass plan.  The
+ * double-float forms (BTO_FORM_DF, BTO_FORM_DF_UNFUSED) share one plan for
+ * every op: panels of at most 1024 columns, at most one tile per
+ * multiprocessor where that allows, chosen by the least busiest-block work
+ * (256 x 16 units) times one plus the partial-sum bytes over the matrix
+ * bytes. */
 bto_status bto_panel_plan(int op, int form, int64_t m, int64_t n, int sms, int *row_blocks, int *panels);
 
 /* ------------------------------------------- reduced-precision storage form

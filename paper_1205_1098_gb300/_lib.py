@@ -321,7 +321,7 @@ def bto_bicgk_mrhs_workspace_bytes(m, n, k):
 
 
 def bto_panel_plan(op, form, m, n, sms):
-    """(row_blocks, panels) of the FP64 tile plan (host only)."""
+    """(row_blocks, panels) of the tile plan of the FP64 or double-float forms (host only)."""
     if isinstance(op, str):
         op = OPS[op]
     a, b = _c_int(0), _c_int(0)

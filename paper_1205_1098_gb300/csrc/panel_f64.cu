@@ -569,13 +569,13 @@ extern "C" bto_status bto_panel_plan(int op, int form, int64_t m, int64_t n, int
                                      int* panels) {
     clear_invalid_arg();
     if (op < BTO_OP_BICGK || op > BTO_OP_DGEMVT) { set_invalid_arg(1); return BTO_ERR_INVALID_VALUE; }
-    if (form != BTO_FORM_FUSED && form != BTO_FORM_UNFUSED) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
+    if (form < BTO_FORM_FUSED || form > BTO_FORM_DF_UNFUSED) { set_invalid_arg(2); return BTO_ERR_INVALID_VALUE; }
     if (m < 0) { set_invalid_arg(3); return BTO_ERR_INVALID_VALUE; }
     if (n < 0) { set_invalid_arg(4); return BTO_ERR_INVALID_VALUE; }
     if (sms < 1 || sms > 4096) { set_invalid_arg(5); return BTO_ERR_INVALID_VALUE; }
     if (!row_blocks) { set_invalid_arg(6); return BTO_ERR_INVALID_VALUE; }
     if (!panels) { set_invalid_arg(7); return BTO_ERR_INVALID_VALUE; }
-    const PanelPlan pl = panel_plan(m, n, sms, op, form);
+    const PanelPlan pl = form >= BTO_FORM_DF ? df_plan(m, n, sms) : panel_plan(m, n, sms, op, form);
     *row_blocks = pl.NR;
     *panels = pl.NC;
     return BTO_OK;

@@ -5,7 +5,9 @@ fused GEMVER takes one chunk per row block (the schedule search's finding);
 large problems get about two tiles per multiprocessor; overrides are
 clamped as documented; and the documented limit of the no-allocation BICGK
 (every square n up to 3427 on 152 multiprocessors fits its 4 MiB scratch)
-holds."""
+holds.  The double-float forms' plan: panels of at most 1024 columns, at
+most one tile per multiprocessor where that allows, one plan for every op,
+and 8 x 19 tiles at the benchmarked n = 16384 on 152 multiprocessors."""
 import itertools
 
 import pytest
@@ -97,7 +99,29 @@ def test_noalloc_limit_holds():
 
 def test_plan_query_validation():
     for args, pos in ((("bicgk", 0, -1, 4, 152), 3), (("bicgk", 0, 4, -1, 152), 4), (("bicgk", 0, 4, 4, 0), 5),
-                      ((9, 0, 4, 4, 152), 1), (("bicgk", 2, 4, 4, 152), 2)):
+                      ((9, 0, 4, 4, 152), 1), (("bicgk", 4, 4, 4, 152), 2)):
         with pytest.raises(bto.BtoError) as e:
             bto.bto_panel_plan(*args)
         assert e.value.arg == pos
+
+
+DF_FORMS = (2, 3)   # BTO_FORM_DF, BTO_FORM_DF_UNFUSED
+
+
+@pytest.mark.parametrize("sms", [152, 148, 16])
+def test_df_plans_cover_the_matrix(sms):
+    for op, form, m, n in itertools.product(OPS, DF_FORMS, SIZES, SIZES):
+        nr, nc = bto.bto_panel_plan(op, form, m, n, sms)
+        cu, ru = ceil_div(n, 16), ceil_div(m, 256)           # 16-column and 256-row units
+        assert 1 <= nc <= cu and 1 <= nr <= ru, (op, form, m, n, nr, nc)
+        assert ceil_div(cu, nc) * 16 <= 1024, (op, form, m, n, nr, nc)
+        if ceil_div(cu, 64) <= sms:
+            assert nr * nc <= sms, (op, form, m, n, nr, nc)   # at most one tile per block
+        assert (nr, nc) == bto.bto_panel_plan("bicgk", 2, m, n, sms)
+
+
+def test_df_plan_at_the_benchmarked_size():
+    # n = 16384 on 152 multiprocessors: 8 row blocks of 2048 rows and 19
+    # panels of at most 54 units of 16 columns.
+    assert bto.bto_panel_plan("bicgk", 2, 16384, 16384, 152) == (8, 19)
+    assert bto.bto_panel_plan("gemver", 3, 16384, 16384, 152) == (8, 19)
